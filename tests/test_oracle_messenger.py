@@ -1,0 +1,218 @@
+"""Pins of the oracle's messenger iteration (Eqs. 3-4), chi^2 monitor and
+cooling controller (Sect. 3) against what the paper and the mathematics fix."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense as D
+from oracle import oracle as O
+from paper_1211_0585_gb300 import inputs as I
+
+
+def tiny_problem(nside, lmax, seed, masked=True, homogeneous=False, noise=2e-4):
+    rng = np.random.default_rng(seed)
+    z, phi = I.pixel_centres(nside)
+    npix = z.size
+    cl = np.zeros(lmax + 1)
+    l = np.arange(2, lmax + 1)
+    cl[2:] = 1.0 / (l * (l + 1.0))
+    var = np.full(npix, noise) if homogeneous else noise * (1 + 3 * rng.random(npix))
+    mask = np.ones(npix, np.uint8)
+    if masked:
+        mask = (np.abs(z) > 0.3).astype(np.uint8)
+    alm = I.draw_alm(cl, rng)
+    d = O.alm2map(nside, lmax, alm) + rng.standard_normal(npix) * np.sqrt(var)
+    return cl, var, mask, d, z, phi
+
+
+def dense_setup(nside, lmax, cl, var, mask, z, phi, lam):
+    npix = z.size
+    omega = 4 * math.pi / npix
+    tau = O.messenger_tau(var, mask)
+    w = O.inverse_noise(var, mask)
+    Y = D.synthesis_matrix(z, phi, lmax)
+    Yd = D.adjoint_matrix(Y, lmax, npix)
+    f_dof = O.harmonic_filter(lam, tau, omega, cl)[D.dof_l(lmax)]
+    a_pix = O.pixel_gain(lam, tau, w)
+    return Y, Yd, f_dof, a_pix, w, tau, omega
+
+
+def test_pixel_gain_solves_eq3():
+    """t from a_p equals the solution of (Nbar^-1 + (lambda T)^-1) t = Nbar^-1 d + (lambda T)^-1 s."""
+    rng = np.random.default_rng(0)
+    tau = 0.7
+    sig2 = tau * (1 + 5 * rng.random(100))
+    sig2[0] = tau * (1 + 1e-9)
+    d, s = rng.standard_normal(100), rng.standard_normal(100)
+    for lam in (1.0, 3.0, 1e4):
+        nbar = sig2 - tau
+        t_direct = (d / nbar + s / (lam * tau)) / (1 / nbar + 1 / (lam * tau))
+        a = O.pixel_gain(lam, tau, 1 / sig2)
+        assert np.allclose(s + a * (d - s), t_direct, rtol=1e-7, atol=1e-9)
+    # masked pixel (N^-1 = 0): t = s; pixel at the minimum variance with lambda = 1: t = d
+    assert O.pixel_gain(5.0, tau, 0.0) == 0.0
+    assert O.pixel_gain(1.0, tau, 1 / tau) == pytest.approx(1.0)
+
+
+def test_harmonic_filter_solves_eq4():
+    """s from f_l equals the solution of (S^-1 + (lambda T)^-1) s = (lambda T)^-1 t with T = tau Omega."""
+    cl = np.array([0.0, 0.0, 1.0, 0.3, 1e-5])
+    tau, omega = 0.2, 0.01
+    for lam in (1.0, 40.0):
+        f = O.harmonic_filter(lam, tau, omega, cl)
+        T = lam * tau * omega
+        good = cl > 0
+        direct = (1 / T) / (1 / cl[good] + 1 / T)
+        assert np.allclose(f[good], direct, rtol=1e-14)
+        assert np.all(f[~good] == 0.0)
+
+
+@pytest.mark.parametrize("lam", [1.0, 50.0])
+def test_closed_form_full_sky_homogeneous(lam):
+    """Full sky, homogeneous noise sigma^2 = tau: a_p = 1 so t = d, and after
+    one iteration s_lm = C_l / (C_l + lambda tau Omega) d_lm (d_lm from the
+    dense scipy adjoint); at lambda = 1 this is C_l / (C_l + N_l) d_lm."""
+    nside, lmax = 8, 16
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, 1, masked=False, homogeneous=True)
+    npix = z.size
+    tau, omega = var[0], 4 * math.pi / npix
+    res = O.solve(nside, lmax, cl, var, mask, d, schedule=[(lam, lmax, 1)])
+    Y = D.synthesis_matrix(z, phi, lmax)
+    dlm = D.unpack(D.adjoint_matrix(Y, lmax, npix) @ d, lmax)
+    ls = O.l_of_index(lmax)
+    expect = np.where(cl[ls] > 0, cl[ls] / (cl[ls] + lam * tau * omega), 0.0) * dlm
+    assert np.allclose(res.alm, expect, rtol=0, atol=1e-13 * np.abs(expect).max())
+
+
+@pytest.mark.parametrize("nside,lmax,lam,seed", [(4, 8, 1.0, 2), (4, 8, 25.0, 3), (8, 16, 1.0, 4)])
+def test_k_step_iterates_match_dense_recursion(nside, lmax, lam, seed):
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, seed)
+    Y, Yd, f_dof, a_pix, w, tau, omega = dense_setup(nside, lmax, cl, var, mask, z, phi, lam)
+    G, b = D.affine_map(Y, Yd, a_pix, f_dof, d)
+    x = np.zeros(G.shape[0])
+    seen = []
+    O.solve(nside, lmax, cl, var, mask, d, schedule=[(lam, lmax, 6)],
+            callback=lambda k, rec, s: seen.append(D.pack(s, lmax)))
+    for k in range(6):
+        x = G @ x + b
+        assert np.allclose(seen[k], x, rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+def test_band_limited_step_matches_dense():
+    """With lmax_SHT < lmax only l <= lmax_SHT take part, the rest stay zero."""
+    nside, lmax, lsht, lam = 4, 10, 6, 4.0
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, 9)
+    Y, Yd, f_dof, a_pix, w, tau, omega = dense_setup(nside, lsht, cl[:lsht + 1], var, mask, z, phi, lam)
+    G, b = D.affine_map(Y, Yd, a_pix, f_dof, d)
+    res = O.solve(nside, lmax, cl, var, mask, d, schedule=[(lam, lsht, 3)])
+    x = np.zeros(G.shape[0])
+    for _ in range(3):
+        x = G @ x + b
+    got = res.alm
+    assert np.allclose(D.pack(O.truncate_alm(got, lmax, lsht), lsht), x, atol=1e-13 * np.abs(x).max())
+    ls = O.l_of_index(lmax)
+    assert np.all(got[ls > lsht] == 0)
+
+
+@pytest.mark.parametrize("nside,lmax,lam", [(4, 8, 1.0), (8, 16, 1.0), (8, 12, 7.0)])
+def test_converges_to_dense_wiener_filter(nside, lmax, lam):
+    """Sect. 2: the iteration converges exponentially and unconditionally to
+    the Wiener filter; at lambda = 1 the limit is the direct dense solution
+    of Eq. 2 in this discretisation, and at lambda > 1 the Wiener filter with
+    noise N + (lambda - 1) T (which reduces to Eq. 2 at lambda = 1)."""
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, 21, noise=1e-2)
+    Y, Yd, f_dof, a_pix, w, tau, omega = dense_setup(nside, lmax, cl, var, mask, z, phi, lam)
+    G, b = D.affine_map(Y, Yd, a_pix, f_dof, d)
+    rho = D.spectral_radius(G)
+    assert rho < 1.0
+    w_lam = np.where(w > 0, 1.0 / (1.0 / np.where(w > 0, w, 1.0) + (lam - 1.0) * tau), 0.0)
+    xwf = D.posterior_wf(Y, w_lam, cl[D.dof_l(lmax)], D.dof_weight(lmax), d)
+    assert np.linalg.norm(D.fixed_point(G, b) - xwf) <= 1e-10 * np.linalg.norm(xwf)
+    n = int(math.ceil(math.log(1e-13) / math.log(rho))) + 20
+    res = O.solve(nside, lmax, cl, var, mask, d, schedule=[(lam, lmax, n)])
+    assert O.rel_l2(res.alm, D.unpack(xwf, lmax), lmax) < 1e-10
+    # geometric decay of the increments at rate ~rho
+    inc = np.array([h["rel_incr"] for h in res.history])
+    k = min(60, n // 2)
+    assert inc[2 * k] <= inc[k] * (rho ** k) * 10 + 1e-15
+
+
+def test_chi2_matches_dense():
+    nside, lmax, lam = 4, 8, 3.0
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, 5)
+    Y, Yd, f_dof, a_pix, w, tau, omega = dense_setup(nside, lmax, cl, var, mask, z, phi, lam)
+    wgt, cl_dof = D.dof_weight(lmax), cl[D.dof_l(lmax)]
+    G, b = D.affine_map(Y, Yd, a_pix, f_dof, d)
+    res = O.solve(nside, lmax, cl, var, mask, d, schedule=[(lam, lmax, 4)])
+    x = np.zeros(G.shape[0])
+    for k in range(4):
+        # step k reports the chi^2 of its input state
+        assert res.history[k]["chi2"] == pytest.approx(D.chi2(x, Y, w, d, cl_dof, wgt), rel=1e-12)
+        nl = np.where(w > 0, 1 / np.where(w > 0, w, 1) + (lam - 1) * tau, np.inf)
+        r = d - Y @ x
+        chi2l = np.sum(wgt * x * x / np.where(cl_dof > 0, cl_dof, np.inf)) + np.sum(np.where(w > 0, r * r / nl, 0))
+        assert res.history[k]["chi2_lambda"] == pytest.approx(chi2l, rel=1e-12)
+        x = G @ x + b
+
+
+@pytest.mark.parametrize("nside,lmax", [(8, 16), (16, 32)])
+def test_chi2_lambda_monotone_within_level(nside, lmax):
+    """At fixed lambda the chi^2 with N replaced by N + (lambda - 1) T never
+    increases: Eqs. 3 and 4 are block minimisations of a joint functional
+    whose minimum over t is that chi^2."""
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, 8)
+    for lam in (1.0, 30.0, 3000.0):
+        res = O.solve(nside, lmax, cl, var, mask, d, schedule=[(lam, lmax, 80)])
+        c = np.array([h["chi2_lambda"] for h in res.history])
+        assert np.all(np.diff(c) <= 1e-12 * c[1:]), np.diff(c).max()
+        assert c[-1] < c[1]
+
+
+def test_statistical_chi2():
+    """For data drawn from the model, the Wiener-filter chi^2 per observed
+    pixel is 1 +- sqrt(2 / n_obs) (the paper reaches 0.996 on WMAP data)."""
+    nside, lmax = 16, 32
+    p = I.wmap_problem(seed=3, nside=nside, lmax=lmax, ndisc=20, fwhm_arcmin=60.0)
+    var = p.noise_var / 400.0
+    rng = np.random.default_rng(4)
+    d = O.alm2map(nside, lmax, p.alm_true) + rng.standard_normal(p.npix) * np.sqrt(var)
+    res = O.solve(nside, lmax, p.cl, var, p.mask, d, O.Options(tol=1e-8, max_iter=5000))
+    assert res.converged
+    n_obs = int(p.mask.sum())
+    chi2 = res.history[-1]["chi2"]
+    assert abs(chi2 / n_obs - 1.0) < 4 * math.sqrt(2.0 / n_obs)
+
+
+def test_cooling_schedule_shape():
+    """lambda starts at C_20 / (tau Omega) (O(1e4) for the small case, as in
+    the paper's Fig. 2), never increases, ends at 1; while lambda > 1 the
+    band limit is min(lmax, l_iter + 100)."""
+    p = I.small_problem(seed=2, nside=16, lmax=40)
+    d = p.data(O.alm2map(p.nside, p.lmax, p.alm_true))
+    res = O.solve(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d,
+                  O.Options(tol=1e-7, max_iter=400, lmax_margin=5))
+    lams = [h["lam"] for h in res.history]
+    tau = O.messenger_tau(p.noise_var, p.mask)
+    omega = 4 * math.pi / p.npix
+    assert lams[0] == pytest.approx(p.cl[20] / (tau * omega))
+    assert 1e3 < lams[0] < 1e5
+    assert all(b <= a for a, b in zip(lams, lams[1:]))
+    assert lams[-1] == 1.0
+    for h in res.history:
+        if h["lam"] > 1:
+            assert h["lsht"] in (25, 40)
+        else:
+            assert h["lsht"] == 40
+
+
+def test_cooled_solve_reaches_wiener_filter():
+    """The cooled solve ends at lambda = 1 on the Eq. 2 solution (dense)."""
+    nside, lmax = 8, 16
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, 17, noise=6e-3)
+    Y, Yd, f_dof, a_pix, w, tau, omega = dense_setup(nside, lmax, cl, var, mask, z, phi, 1.0)
+    xwf = D.posterior_wf(Y, w, cl[D.dof_l(lmax)], D.dof_weight(lmax), d)
+    res = O.solve(nside, lmax, cl, var, mask, d, O.Options(tol=1e-12, max_iter=20000, l_iter0=4, lmax_margin=4))
+    assert res.converged and res.history[-1]["lam"] == 1.0
+    assert len(O.schedule_of(res)) >= 2
+    assert O.rel_l2(res.alm, D.unpack(xwf, lmax), lmax) < 1e-8
