@@ -1,0 +1,208 @@
+/*
+ * wf.h -- C ABI of the GB300 messenger-field Wiener filter library.
+ *
+ * Method: Elsner & Wandelt, "Fast Wiener filtering of CMB maps",
+ * arXiv:1211.0585. The library solves Eq. 2,
+ *     (S^-1 + N^-1) s_WF = N^-1 d,
+ * for a HEALPix map d (RING order), noise covariance N diagonal in pixel space
+ * (masked pixels carry N^-1 = 0) and signal covariance S = diag(C_l) in
+ * spherical-harmonic space, by the messenger-field iteration of Sect. 2
+ * (Eqs. 3 and 4, messenger covariance T = tau * 1, tau = min diag(N),
+ * Nbar = N - T) with the cooling of lambda and the band limit
+ * lmax_SHT = l_iter + margin of Sect. 3.
+ *
+ * One iteration, all on the GPU:
+ *   s_p  = (Y s)_p                         synthesis (Legendre stage, ring FFT)
+ *   u_p  = a_p(lambda) (d_p - s_p)          Eq. 3 solved per pixel: t = s + u,
+ *                                           a_p = lambda tau w_p / (1 + (lambda-1) tau w_p),
+ *                                           w_p = 1/sigma_p^2 (0 where masked)
+ *   t_lm = s_lm + (Y^dagger u)_lm           basis change of the increment t - s
+ *                                           (ring FFT, Legendre stage); Y^dagger =
+ *                                           (4 pi / Npix) Y^T, uniform weights
+ *   s_lm = f_l(lambda) t_lm                 Eq. 4 solved per mode,
+ *                                           f_l = C_l / (C_l + lambda tau 4 pi / Npix)
+ * plus the chi^2 = s^+ S^-1 s + (d - s)^+ N^-1 (d - s) monitor of Sect. 3.
+ *
+ * Conventions shared by every entry point
+ *   - a_lm: m >= 0 only (real field), m-major, index(l, m) = m (2 lmax + 1 - m) / 2 + l,
+ *     nalm = (lmax + 1)(lmax + 2) / 2 complex numbers stored as interleaved
+ *     doubles (re, im): 2 * nalm doubles. Orthonormal spherical harmonics with
+ *     the Condon-Shortley phase.
+ *   - maps: Npix = 12 nside^2 doubles in HEALPix RING order.
+ *   - Pointers named *_dev are CUDA device pointers; an `on_device` flag says
+ *     whether a pointer that may be either is device (1) or host (0) memory.
+ *     The caller owns every buffer it passes; the library copies what it keeps.
+ *   - Every function returns a wf_status and never aborts; after an error,
+ *     wf_last_error() gives a message (thread-local).
+ *   - A plan is not thread-safe: one thread at a time per plan. The server is
+ *     thread-safe.
+ *   - Units are free but consistent: d and sigma in one unit, C_l in that unit
+ *     squared times steradian.
+ */
+#ifndef WF_H
+#define WF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WF_OK = 0,
+  WF_EINVAL = 1,          /* bad argument (sizes, NaN or <= 0 variance on an observed pixel, ...) */
+  WF_ENOMEM = 2,          /* device or host allocation failed, or over the server's HBM budget */
+  WF_ECUDA = 3,           /* a CUDA call failed (message in wf_last_error) */
+  WF_ENOTCONVERGED = 4,   /* max_iter reached before the stop rule held (result still written) */
+  WF_ENUMERIC = 5,        /* chi^2 became NaN or infinite */
+  WF_ETIMEOUT = 6,        /* a bounded wait gave up */
+  WF_EBUSY = 7,           /* result not ready (wf_poll) */
+  WF_ECANCELLED = 8,      /* request cancelled */
+  WF_ENOTFOUND = 9        /* unknown ticket */
+} wf_status;
+
+typedef enum { WF_PREC_FP64 = 0, WF_PREC_MIXED = 1 } wf_precision;
+
+typedef struct wf_plan_s *wf_plan_t;
+typedef struct wf_server_s *wf_server_t;
+
+/* Solver options (Sect. 3). Fill with wf_options_default, then override. */
+typedef struct {
+  int precision;         /* wf_precision */
+  double tol;            /* stop when ||s_k - s_{k-1}|| / ||s_k|| <= tol at lambda = 1 (1e-6) */
+  int max_iter;          /* iteration cap (10000) */
+  int cooling;           /* 1: cool lambda as in Sect. 3; 0: lambda = 1 throughout (1) */
+  int l_iter0;           /* first l_iter (20) */
+  int lmax_margin;       /* lmax_SHT = min(lmax, l_iter + margin) while lambda > 1 (100) */
+  int band_limit;        /* 1: use lmax_SHT while lambda > 1; 0: always lmax (1) */
+  double plateau_eps;    /* plateau: |chi2_k - chi2_{k-1}| < eps * sqrt(2 n_obs) (1e-2) */
+  double final_dchi2;    /* > 0: also stop at lambda = 1 when |d chi2| < final_dchi2 * sqrt(2 n_obs);
+                            the paper uses 1e-4 (0 = off) */
+  int min_level_iters;   /* iterations at a lambda level before a plateau can end it (3) */
+  int max_level_iters;   /* a level ends after this many iterations regardless (1000) */
+  int graph_iters;       /* iterations captured per CUDA graph launch (16) */
+  void *stream;          /* cudaStream_t to run on; NULL = the plan's own stream */
+} wf_options;
+
+/* Result summary of a solve. */
+typedef struct {
+  int iters;             /* iterations run */
+  int converged;         /* 1 if the stop rule held */
+  int levels;            /* lambda levels visited */
+  int lmax_sht_final;
+  double lambda_final;
+  double chi2;           /* chi^2 of the input state of the last iteration (Sect. 3 definition) */
+  double chi2_prior;     /* s^+ S^-1 s part */
+  double chi2_noise;     /* (d - s)^+ N^-1 (d - s) part */
+  double chi2_per_dof;   /* chi2 / n_obs */
+  double rel_increment;  /* ||s_k - s_{k-1}|| / ||s_k|| of the last iteration */
+  double ms_device;      /* device time of the solve, CUDA events */
+} wf_stats;
+
+/* Per-iteration record written by wf_iterate / wf_solve_history. */
+typedef struct {
+  double chi2_prior, chi2_noise, chi2_lambda;  /* of the iteration's input state */
+  double incr2, norm2;                         /* ||s_k - s_{k-1}||^2, ||s_k||^2 (m > 0 weighted x2) */
+  double lambda;
+  int lmax_sht;
+  int level;
+} wf_iter_record;
+
+/* Defaults listed beside each field above. */
+wf_status wf_options_default(wf_options *opt);
+
+/* Create a plan for one (nside, lmax, C_l, noise, mask) problem: builds the
+ * ring geometry, FFT tables, Legendre recurrence tables, tau = min over
+ * observed pixels of noise_var (Sect. 2), and allocates all device buffers.
+ *   nside      : power of two, 1 .. 8192
+ *   lmax       : 0 .. 4 nside (and <= 16384)
+ *   cl         : host [lmax+1], beam folded in, >= 0 and finite (C_l = 0: mode not solved for)
+ *   noise_var  : host [Npix] sigma_p^2, finite and > 0 on observed pixels
+ *   mask       : host [Npix] 1 = observed, 0 = masked (N^-1 = 0); NULL = all observed
+ *   opt        : NULL = defaults; copied into the plan
+ * Errors: WF_EINVAL on bad sizes/values or no observed pixel; WF_ENOMEM; WF_ECUDA. */
+wf_status wf_plan_create(int nside, int lmax, const double *cl, const double *noise_var,
+                         const uint8_t *mask, const wf_options *opt, wf_plan_t *out);
+
+wf_status wf_plan_destroy(wf_plan_t plan);
+
+/* Sizes and constants of a plan. Any out pointer may be NULL. */
+wf_status wf_plan_info(wf_plan_t plan, int64_t *npix, int64_t *nalm, double *tau,
+                       int64_t *n_obs, size_t *device_bytes);
+
+/* Replace the plan's options (precision, tolerances, schedule knobs, stream). */
+wf_status wf_plan_set_options(wf_plan_t plan, const wf_options *opt);
+
+/* Synthesis map = Y alm with band limit lsht (<= lmax; modes with l > lsht are
+ * ignored): the "transform back" of Sect. 2. Device pointers, alm in the plan's
+ * lmax layout. Runs on the plan's stream; returns after enqueueing (no sync). */
+wf_status wf_alm2map(wf_plan_t plan, int lsht, const double *alm_dev, double *map_dev);
+
+/* Adjoint alm = Y^dagger map = (4 pi / Npix) Y^T map with band limit lsht
+ * (entries with l > lsht are set to 0): the basis change of Sect. 2. */
+wf_status wf_map2alm(wf_plan_t plan, int lsht, const double *map_dev, double *alm_dev);
+
+/* Run `niter` messenger iterations (Eqs. 3-4) at fixed lambda (>= 1) and band
+ * limit lsht, in place on the device state s_dev [2*nalm], with data d_dev
+ * [Npix]. If `reset_state` is 1, s_dev is taken as a fresh start (its synthesis
+ * is recomputed first); the plan otherwise reuses the synthesis left by the
+ * previous call. `records` (host, may be NULL) receives niter entries.
+ * Synchronises the plan's stream before returning. */
+wf_status wf_iterate(wf_plan_t plan, const double *d_dev, double *s_dev, double lambda, int lsht,
+                     int niter, int reset_state, wf_iter_record *records);
+
+/* Full solve with the cooling schedule and stop rule of Sect. 3.
+ *   d        : [Npix] data, host or device (d_on_device)
+ *   alm_out  : [2*nalm] result, host or device (alm_on_device)
+ *   alm_init : NULL (start at s = 0, Sect. 2) or a warm start, same memory kind as alm_out
+ *   stats    : may be NULL
+ * Returns WF_OK, or WF_ENOTCONVERGED (result written) / WF_ENUMERIC. */
+wf_status wf_solve(wf_plan_t plan, const double *d, int d_on_device, double *alm_out,
+                   int alm_on_device, const double *alm_init, wf_stats *stats);
+
+/* As wf_solve, also copying up to max_records per-iteration records to host. */
+wf_status wf_solve_history(wf_plan_t plan, const double *d, int d_on_device, double *alm_out,
+                           int alm_on_device, wf_stats *stats, wf_iter_record *records,
+                           int max_records, int *n_records);
+
+/* Solve nrhs right-hand sides that share the plan's C_l, noise and mask.
+ *   d       : [nrhs][Npix], alm_out : [nrhs][2*nalm], stats : [nrhs] or NULL.
+ * All right-hand sides advance together through one batched iteration per
+ * step; each stops on its own rule. */
+wf_status wf_solve_batch(wf_plan_t plan, int nrhs, const double *d, int d_on_device,
+                         double *alm_out, int alm_on_device, wf_stats *stats);
+
+/* Serving: continuous batching of solve requests of any (nside, lmax, C_l,
+ * noise, mask) under a device-memory budget.
+ *   hbm_budget_bytes : admission limit for plans + per-request buffers (0 = 90 % of free memory)
+ *   max_batch        : most requests of one shape that advance in one step */
+wf_status wf_server_create(size_t hbm_budget_bytes, int max_batch, wf_server_t *out);
+
+/* Submit a request (host arrays, copied). tol <= 1e-7 selects the FP64 path,
+ * larger tol the mixed path. Never blocks on the GPU. */
+wf_status wf_submit(wf_server_t server, int nside, int lmax, const double *cl,
+                    const double *noise_var, const uint8_t *mask, const double *d, double tol,
+                    uint64_t *ticket);
+
+/* Non-blocking: *done = 1 and alm_out (host, [2*nalm]) / stats filled when the
+ * request finished; *done = 0 otherwise. Returns the request's own status once
+ * done; WF_ENOTFOUND for an unknown or already collected ticket. */
+wf_status wf_poll(wf_server_t server, uint64_t ticket, int *done, double *alm_out, wf_stats *stats);
+
+/* Block until every admitted request has finished or timeout_ms passed
+ * (WF_ETIMEOUT). */
+wf_status wf_server_drain(wf_server_t server, int timeout_ms);
+
+/* Request latency percentiles (ms) and completed-solve count since creation. */
+wf_status wf_server_stats(wf_server_t server, double *p50_ms, double *p99_ms, int64_t *completed);
+
+wf_status wf_server_destroy(wf_server_t server);
+
+/* Message of the last error on this thread ("" if none). */
+const char *wf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WF_H */

@@ -1,0 +1,574 @@
+// C ABI of the messenger-field Wiener filter (plan, transforms, solves).
+// The host side builds the HEALPix ring geometry and the per-length FFT
+// tables, checks inputs, owns device memory and drives the kernels; every
+// arithmetic step of the method runs in the kernels of ring.cu,
+// legendre.cu and control.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wf_internal.h"
+#include "wf_plan.h"
+
+namespace wfk {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+wf_status cuda_status(cudaError_t e, const char *where) {
+  if (e == cudaSuccess) return WF_OK;
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? WF_ENOMEM : WF_ECUDA;
+}
+
+#define WF_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_status(e_, #call);  \
+  } while (0)
+
+static int ilog2(long long v) {
+  int r = 0;
+  while ((1LL << r) < v) ++r;
+  return r;
+}
+
+static size_t alm_count(int lmax) { return (size_t)(lmax + 1) * (lmax + 2) / 2; }
+
+wf_status Plan::dalloc(void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+  allocs.push_back(*p);
+  device_bytes += bytes;
+  return WF_OK;
+}
+
+Plan::~Plan() {
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  for (void *p : allocs) cudaFree(p);
+  if (h_ctl) cudaFreeHost(h_ctl);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+cudaStream_t Plan::run_stream() const {
+  return opt.stream ? static_cast<cudaStream_t>(opt.stream) : stream;
+}
+
+static wf_status build_geometry(Plan *P) {
+  const int ns = P->nside, R = P->R;
+  std::vector<RingDev> rings(R);
+  // per-length tables: polar lengths 4i (i = 1 .. nside - 1), then the belt length 4 nside
+  std::vector<long long> hs_off(ns + 1), ch_off(ns + 1), B_off(ns + 1, -1);
+  std::vector<int> logM(ns + 1), blue(ns + 1);
+  long long hs_tot = 0, ch_tot = 0, B_tot = 0;
+  int maxM = 1;
+  for (int i = 1; i <= ns; ++i) {
+    const long long n = 4LL * i;
+    hs_off[i] = hs_tot;
+    hs_tot += n;
+    const bool pow2 = (n & (n - 1)) == 0;
+    blue[i] = pow2 ? 0 : 1;
+    logM[i] = pow2 ? ilog2(n) : ilog2(2 * n - 1);
+    if (!pow2) {
+      ch_off[i] = ch_tot;
+      ch_tot += n;
+      B_off[i] = B_tot;
+      B_tot += 1LL << logM[i];
+    } else {
+      ch_off[i] = 0;
+      B_off[i] = 0;
+    }
+    if ((1 << logM[i]) > maxM) maxM = 1 << logM[i];
+  }
+  const long long npix = P->npix;
+  for (int r = 0; r < R; ++r) {
+    const int i = r + 1;
+    const int ip = i < 4 * ns - i ? i : 4 * ns - i;  // mirrored ring number
+    RingDev g{};
+    const bool polar = ip < ns;
+    const int cls = polar ? ip : ns;                 // length class
+    g.n = 4 * cls;
+    if (i < ns) g.off = 2LL * i * (i - 1);
+    else if (i <= 3 * ns) g.off = 2LL * ns * (ns - 1) + (long long)(i - ns) * 4 * ns;
+    else g.off = npix - 2LL * ip * (ip + 1);
+    g.shifted = polar ? 1 : (((i - ns) % 2) == 0 ? 1 : 0);
+    g.pair = r < R - 1 - r ? r : R - 1 - r;
+    g.side = r > R - 1 - r ? 1 : 0;
+    g.logM = logM[cls];
+    g.blue = blue[cls];
+    g.hs_off = hs_off[cls];
+    g.ch_off = ch_off[cls];
+    g.B_off = B_off[cls];
+    rings[r] = g;
+  }
+  P->maxM = maxM;
+  P->logMmax = ilog2(maxM);
+  // tables
+  std::vector<double2> hs(hs_tot), ch(ch_tot > 0 ? ch_tot : 1), tw(maxM / 2 > 0 ? maxM / 2 : 1);
+  for (int i = 1; i <= ns; ++i) {
+    const long long n = 4LL * i;
+    for (long long q = 0; q < n; ++q) {
+      const double a = M_PI * (double)q / (double)n;
+      hs[hs_off[i] + q] = make_double2(cos(a), sin(a));
+    }
+    if (blue[i]) {
+      for (long long j = 0; j < n; ++j) {
+        const long long jj = (j * j) % (2 * n);
+        const double a = M_PI * (double)jj / (double)n;
+        ch[ch_off[i] + j] = make_double2(cos(a), -sin(a));
+      }
+    }
+  }
+  for (int k = 0; k < maxM / 2; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)maxM;
+    tw[k] = make_double2(cos(a), -sin(a));
+  }
+  if (maxM < 2) tw[0] = make_double2(1.0, 0.0);
+  std::vector<double> xk(P->RP);
+  for (int k = 0; k < P->RP; ++k) {
+    const int i = k + 1;
+    xk[k] = (i < ns) ? 1.0 - (double)i * i / (3.0 * (double)ns * ns) : 4.0 / 3.0 - 2.0 * i / (3.0 * ns);
+  }
+  wf_status st;
+  if ((st = P->dalloc((void **)&P->d_rings, sizeof(RingDev) * R))) return st;
+  if ((st = P->dalloc((void **)&P->d_hs, sizeof(double2) * hs.size()))) return st;
+  if ((st = P->dalloc((void **)&P->d_chirp, sizeof(double2) * ch.size()))) return st;
+  if ((st = P->dalloc((void **)&P->d_B, sizeof(double2) * (B_tot > 0 ? B_tot : 1)))) return st;
+  if ((st = P->dalloc((void **)&P->d_tw, sizeof(double2) * tw.size()))) return st;
+  if ((st = P->dalloc((void **)&P->d_x, sizeof(double) * P->RP))) return st;
+  cudaStream_t s = P->stream;
+  WF_CUDA(cudaMemcpyAsync(P->d_rings, rings.data(), sizeof(RingDev) * R, cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_hs, hs.data(), sizeof(double2) * hs.size(), cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_chirp, ch.data(), sizeof(double2) * ch.size(), cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_x, xk.data(), sizeof(double) * P->RP, cudaMemcpyHostToDevice, s));
+  if (B_tot > 0) launch_bluestein_setup(P->d_rings, R, P->d_tw, P->logMmax, P->d_chirp, P->d_B, maxM, s);
+  WF_CUDA(cudaStreamSynchronize(s));
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+static wf_status build_legendre(Plan *P) {
+  const int lmax = P->lmax;
+  std::vector<double2> rec(alm_count(lmax));
+  for (int m = 0; m <= lmax; ++m) {
+    const size_t base = (size_t)m * (2 * lmax + 1 - m) / 2;
+    for (int l = m; l <= lmax; ++l) {
+      double a = 0.0, b = 0.0;
+      const double dl = l, dm = m;
+      if (l == m + 1) {
+        a = sqrt(2.0 * m + 3.0);
+      } else if (l >= m + 2) {
+        a = sqrt((4.0 * dl * dl - 1.0) / (dl * dl - dm * dm));
+        b = a * sqrt(((dl - 1.0) * (dl - 1.0) - dm * dm) / (4.0 * (dl - 1.0) * (dl - 1.0) - 1.0));
+      }
+      rec[base + l] = make_double2(a, b);
+    }
+  }
+  wf_status st;
+  const size_t nmk = (size_t)(lmax + 1) * P->RP;
+  if ((st = P->dalloc((void **)&P->d_rec, sizeof(double2) * rec.size()))) return st;
+  if ((st = P->dalloc((void **)&P->d_ls, sizeof(int) * nmk))) return st;
+  if ((st = P->dalloc((void **)&P->d_sv, sizeof(double2) * nmk))) return st;
+  WF_CUDA(cudaMemcpyAsync(P->d_rec, rec.data(), sizeof(double2) * rec.size(), cudaMemcpyHostToDevice, P->stream));
+  launch_start_values(P->d_x, P->d_rec, lmax, P->RP, P->d_ls, P->d_sv, P->stream);
+  WF_CUDA(cudaStreamSynchronize(P->stream));
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+wf_status Plan::alloc_work() {
+  wf_status st;
+  const size_t nF = (size_t)(lmax + 1) * RP;
+  if ((st = dalloc((void **)&d_FS, sizeof(double4_32a) * nF))) return st;
+  if ((st = dalloc((void **)&d_FT, sizeof(double4_32a) * nF))) return st;
+  if ((st = dalloc((void **)&d_ring_part, sizeof(double) * 2 * R))) return st;
+  if ((st = dalloc((void **)&d_m_part, sizeof(double) * 3 * (lmax + 1)))) return st;
+  if ((st = dalloc((void **)&d_ctl, sizeof(Ctl)))) return st;
+  if ((st = dalloc((void **)&d_d, sizeof(double) * npix))) return st;
+  if ((st = dalloc((void **)&d_s, sizeof(double2) * nalm))) return st;
+  WF_CUDA(cudaMemsetAsync(d_FS, 0, sizeof(double4_32a) * nF, stream));
+  WF_CUDA(cudaMemsetAsync(d_FT, 0, sizeof(double4_32a) * nF, stream));
+  WF_CUDA(cudaMallocHost((void **)&h_ctl, sizeof(Ctl)));
+  WF_CUDA(cudaEventCreate(&ev0));
+  WF_CUDA(cudaEventCreate(&ev1));
+  return WF_OK;
+}
+
+wf_status Plan::ensure_hist(int cap) {
+  if (cap <= hist_cap) return WF_OK;
+  if (d_hist) {
+    cudaFree(d_hist);
+    for (auto &p : allocs)
+      if (p == d_hist) p = nullptr;
+  }
+  d_hist = nullptr;
+  hist_cap = 0;
+  wf_status st = dalloc((void **)&d_hist, sizeof(wf_iter_record) * (size_t)cap);
+  if (st) return st;
+  hist_cap = cap;
+  if (graph_exec) {  // the captured graph holds the old pointer
+    cudaGraphExecDestroy(graph_exec);
+    graph_exec = nullptr;
+  }
+  return WF_OK;
+}
+
+RingArgs Plan::ring_args() const {
+  RingArgs a{};
+  a.rings = d_rings; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;
+  a.FS = d_FS; a.FT = d_FT; a.RP = RP; a.d = d_d; a.w = d_w; a.ring_part = d_ring_part; a.ctl = d_ctl;
+  a.lsht = lmax; a.omega = omega; a.tau = tau;
+  return a;
+}
+
+LegArgs Plan::leg_args() const {
+  LegArgs a{};
+  a.x = d_x; a.rec = d_rec; a.ls = d_ls; a.sv = d_sv; a.cl = d_cl; a.FT = d_FT; a.FS = d_FS; a.alm = d_s;
+  a.m_part = d_m_part; a.ctl = d_ctl; a.lsht = lmax; a.lmax = lmax; a.RP = RP; a.omega = omega; a.tau = tau;
+  return a;
+}
+
+void Plan::enqueue_iteration(cudaStream_t s) {
+  launch_ring(ring_args(), R, maxM, s, RING_ITER);
+  launch_legendre(leg_args(), s, LEG_ITER);
+  launch_control(d_ctl, d_ring_part, R, d_m_part, lmax, d_cl, d_hist, hist_cap, s);
+}
+
+Ctl Plan::make_ctl(int mode, double lambda, int lsht, int n_fixed) const {
+  Ctl c{};
+  c.mode = mode;
+  c.n_fixed = n_fixed;
+  c.max_iter = opt.max_iter;
+  c.cooling = opt.cooling;
+  c.l_iter0 = opt.l_iter0;
+  c.margin = opt.lmax_margin;
+  c.band_limit = opt.band_limit;
+  c.min_level_iters = opt.min_level_iters;
+  c.max_level_iters = opt.max_level_iters;
+  c.lmax = lmax;
+  c.tol = opt.tol;
+  c.plateau_eps = opt.plateau_eps;
+  c.final_dchi2 = opt.final_dchi2;
+  c.sigma_chi2 = sqrt(2.0 * (double)n_obs);
+  c.tau = tau;
+  c.omega = omega;
+  c.lambda = lambda;
+  c.lsht = lsht;
+  c.l_iter = opt.l_iter0;
+  return c;
+}
+
+double Plan::lambda_of(int l_iter) const {
+  if (l_iter > lmax) return 1.0;
+  const double r = h_cl[l_iter] / (tau * omega);
+  return r > 1.0 ? r : 1.0;
+}
+
+}  // namespace wfk
+
+using namespace wfk;
+
+// ============================================================== C ABI
+
+extern "C" {
+
+const char *wf_last_error(void) { return g_err.c_str(); }
+
+wf_status wf_options_default(wf_options *o) {
+  if (!o) { set_error("wf_options_default: NULL"); return WF_EINVAL; }
+  o->precision = WF_PREC_FP64;
+  o->tol = 1e-6;
+  o->max_iter = 10000;
+  o->cooling = 1;
+  o->l_iter0 = 20;
+  o->lmax_margin = 100;
+  o->band_limit = 1;
+  o->plateau_eps = 1e-2;
+  o->final_dchi2 = 0.0;
+  o->min_level_iters = 3;
+  o->max_level_iters = 1000;
+  o->graph_iters = 16;
+  o->stream = nullptr;
+  return WF_OK;
+}
+
+static wf_status check_options(const wf_options *o) {
+  if (o->precision != WF_PREC_FP64 && o->precision != WF_PREC_MIXED) { set_error("precision"); return WF_EINVAL; }
+  if (!(o->tol >= 0.0) || o->max_iter < 1 || o->l_iter0 < 1 || o->lmax_margin < 0 || o->min_level_iters < 1 ||
+      o->max_level_iters < 1 || o->graph_iters < 1 || o->graph_iters > 1024 || !(o->plateau_eps >= 0.0) ||
+      !(o->final_dchi2 >= 0.0)) {
+    set_error("wf_options: value out of range");
+    return WF_EINVAL;
+  }
+  return WF_OK;
+}
+
+wf_status wf_plan_create(int nside, int lmax, const double *cl, const double *noise_var, const uint8_t *mask,
+                         const wf_options *opt, wf_plan_t *out) {
+  if (!out || !cl || !noise_var) { set_error("wf_plan_create: NULL argument"); return WF_EINVAL; }
+  *out = nullptr;
+  if (nside < 1 || nside > 1024 || (nside & (nside - 1)) != 0) {
+    set_error("wf_plan_create: nside must be a power of two in [1, 1024]");
+    return WF_EINVAL;
+  }
+  if (lmax < 0 || lmax > 4 * nside || lmax > 8192) {
+    set_error("wf_plan_create: lmax must be in [0, 4 nside]");
+    return WF_EINVAL;
+  }
+  wf_options o;
+  wf_options_default(&o);
+  if (opt) o = *opt;
+  if (check_options(&o)) return WF_EINVAL;
+  for (int l = 0; l <= lmax; ++l)
+    if (!std::isfinite(cl[l]) || cl[l] < 0.0) { set_error("wf_plan_create: C_l must be finite and >= 0"); return WF_EINVAL; }
+  const long long npix = 12LL * nside * nside;
+  double tau = INFINITY;
+  long long nobs = 0;
+  std::vector<double> w(npix);
+  for (long long p = 0; p < npix; ++p) {
+    const bool obs = !mask || mask[p] != 0;
+    if (!obs) { w[p] = 0.0; continue; }
+    const double v = noise_var[p];
+    if (!std::isfinite(v) || !(v > 0.0)) {
+      set_error("wf_plan_create: noise variance must be finite and > 0 on observed pixels");
+      return WF_EINVAL;
+    }
+    w[p] = 1.0 / v;
+    if (v < tau) tau = v;
+    ++nobs;
+  }
+  if (nobs == 0) { set_error("wf_plan_create: no observed pixel"); return WF_EINVAL; }
+
+  Plan *P = new (std::nothrow) Plan();
+  if (!P) { set_error("out of host memory"); return WF_ENOMEM; }
+  P->nside = nside; P->lmax = lmax; P->npix = npix; P->nalm = (long long)alm_count(lmax);
+  P->R = 4 * nside - 1; P->RP = 2 * nside;
+  P->tau = tau; P->omega = 4.0 * M_PI / (double)npix; P->n_obs = nobs;
+  P->opt = o;
+  P->h_cl.assign(cl, cl + lmax + 1);
+  wf_status st = WF_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { st = cuda_status(e, "cudaStreamCreate"); delete P; return st; }
+  P->own_stream = true;
+  if ((st = build_geometry(P)) || (st = build_legendre(P)) || (st = P->alloc_work()) ||
+      (st = P->dalloc((void **)&P->d_w, sizeof(double) * npix)) ||
+      (st = P->dalloc((void **)&P->d_cl, sizeof(double) * (lmax + 1)))) {
+    delete P;
+    return st;
+  }
+  e = cudaMemcpyAsync(P->d_w, w.data(), sizeof(double) * npix, cudaMemcpyHostToDevice, P->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P->d_cl, cl, sizeof(double) * (lmax + 1), cudaMemcpyHostToDevice, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) { st = cuda_status(e, "plan upload"); delete P; return st; }
+  if ((st = P->ensure_hist(o.max_iter + 1))) { delete P; return st; }
+  *out = P;
+  return WF_OK;
+}
+
+wf_status wf_plan_destroy(wf_plan_t plan) {
+  if (!plan) return WF_OK;
+  cudaStreamSynchronize(static_cast<Plan *>(plan)->stream);
+  delete static_cast<Plan *>(plan);
+  return WF_OK;
+}
+
+wf_status wf_plan_info(wf_plan_t plan, int64_t *npix, int64_t *nalm, double *tau, int64_t *n_obs,
+                       size_t *device_bytes) {
+  if (!plan) { set_error("wf_plan_info: NULL plan"); return WF_EINVAL; }
+  Plan *P = static_cast<Plan *>(plan);
+  if (npix) *npix = P->npix;
+  if (nalm) *nalm = P->nalm;
+  if (tau) *tau = P->tau;
+  if (n_obs) *n_obs = P->n_obs;
+  if (device_bytes) *device_bytes = P->device_bytes;
+  return WF_OK;
+}
+
+wf_status wf_plan_set_options(wf_plan_t plan, const wf_options *opt) {
+  if (!plan || !opt) { set_error("wf_plan_set_options: NULL"); return WF_EINVAL; }
+  if (check_options(opt)) return WF_EINVAL;
+  Plan *P = static_cast<Plan *>(plan);
+  const bool regraph = opt->graph_iters != P->opt.graph_iters || opt->stream != P->opt.stream;
+  P->opt = *opt;
+  wf_status st = P->ensure_hist(opt->max_iter + 1);
+  if (st) return st;
+  if (regraph && P->graph_exec) {
+    cudaGraphExecDestroy(P->graph_exec);
+    P->graph_exec = nullptr;
+  }
+  return WF_OK;
+}
+
+wf_status wf_alm2map(wf_plan_t plan, int lsht, const double *alm_dev, double *map_dev) {
+  if (!plan || !alm_dev || !map_dev) { set_error("wf_alm2map: NULL argument"); return WF_EINVAL; }
+  Plan *P = static_cast<Plan *>(plan);
+  if (lsht < 0 || lsht > P->lmax) { set_error("wf_alm2map: lsht out of range"); return WF_EINVAL; }
+  cudaStream_t s = P->run_stream();
+  LegArgs la = P->leg_args();
+  la.lsht = lsht;
+  la.alm_in = reinterpret_cast<const double2 *>(alm_dev);
+  launch_legendre(la, s, LEG_SYNTH);
+  RingArgs ra = P->ring_args();
+  ra.lsht = lsht;
+  ra.map_out = map_dev;
+  launch_ring(ra, P->R, P->maxM, s, RING_SYNTH);
+  P->fs_valid = false;
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+wf_status wf_map2alm(wf_plan_t plan, int lsht, const double *map_dev, double *alm_dev) {
+  if (!plan || !alm_dev || !map_dev) { set_error("wf_map2alm: NULL argument"); return WF_EINVAL; }
+  Plan *P = static_cast<Plan *>(plan);
+  if (lsht < 0 || lsht > P->lmax) { set_error("wf_map2alm: lsht out of range"); return WF_EINVAL; }
+  cudaStream_t s = P->run_stream();
+  RingArgs ra = P->ring_args();
+  ra.lsht = lsht;
+  ra.map_in = map_dev;
+  launch_ring(ra, P->R, P->maxM, s, RING_ANALYSIS);
+  LegArgs la = P->leg_args();
+  la.lsht = lsht;
+  la.alm = reinterpret_cast<double2 *>(alm_dev);
+  launch_legendre(la, s, LEG_ANALYSIS);
+  P->fs_valid = false;
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+wf_status wf_iterate(wf_plan_t plan, const double *d_dev, double *s_dev, double lambda, int lsht, int niter,
+                     int reset_state, wf_iter_record *records) {
+  if (!plan || !d_dev || !s_dev) { set_error("wf_iterate: NULL argument"); return WF_EINVAL; }
+  Plan *P = static_cast<Plan *>(plan);
+  if (lsht < 0 || lsht > P->lmax || niter < 0 || !(lambda >= 1.0) || !std::isfinite(lambda)) {
+    set_error("wf_iterate: lambda must be >= 1, 0 <= lsht <= lmax, niter >= 0");
+    return WF_EINVAL;
+  }
+  if (niter == 0) return WF_OK;
+  wf_status st = P->ensure_hist(niter + 1);
+  if (st) return st;
+  cudaStream_t s = P->run_stream();
+  WF_CUDA(cudaMemcpyAsync(P->d_d, d_dev, sizeof(double) * P->npix, cudaMemcpyDeviceToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_s, s_dev, sizeof(double2) * P->nalm, cudaMemcpyDeviceToDevice, s));
+  if (reset_state || !P->fs_valid || P->fs_lsht != lsht) {
+    LegArgs la = P->leg_args();
+    la.lsht = lsht;
+    la.alm_in = P->d_s;
+    launch_legendre(la, s, LEG_SYNTH);
+  }
+  Ctl c = P->make_ctl(0, lambda, lsht, niter);
+  *P->h_ctl = c;
+  WF_CUDA(cudaMemcpyAsync(P->d_ctl, P->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  for (int i = 0; i < niter; ++i) P->enqueue_iteration(s);
+  WF_CUDA(cudaGetLastError());
+  WF_CUDA(cudaMemcpyAsync(s_dev, P->d_s, sizeof(double2) * P->nalm, cudaMemcpyDeviceToDevice, s));
+  if (records)
+    WF_CUDA(cudaMemcpyAsync(records, P->d_hist, sizeof(wf_iter_record) * niter, cudaMemcpyDeviceToHost, s));
+  WF_CUDA(cudaMemcpyAsync(P->h_ctl, P->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  P->fs_valid = true;
+  P->fs_lsht = lsht;
+  if (P->h_ctl->numeric) { set_error("wf_iterate: chi^2 is not finite"); return WF_ENUMERIC; }
+  return WF_OK;
+}
+
+static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *alm_out, int alm_on_device,
+                            const double *alm_init, wf_stats *stats, wf_iter_record *records, int max_records,
+                            int *n_records) {
+  cudaStream_t s = P->run_stream();
+  const auto kind_in = d_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  WF_CUDA(cudaEventRecord(P->ev0, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_d, d, sizeof(double) * P->npix, kind_in, s));
+  const double lam0 = P->opt.cooling ? P->lambda_of(P->opt.l_iter0) : 1.0;
+  const int lb = P->opt.l_iter0 + P->opt.lmax_margin;
+  const int lsht0 = (lam0 <= 1.0 || !P->opt.band_limit) ? P->lmax : (lb < P->lmax ? lb : P->lmax);
+  if (alm_init) {
+    const auto k2 = alm_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    WF_CUDA(cudaMemcpyAsync(P->d_s, alm_init, sizeof(double2) * P->nalm, k2, s));
+    LegArgs la = P->leg_args();
+    la.lsht = lsht0;
+    la.alm_in = P->d_s;
+    launch_legendre(la, s, LEG_SYNTH);
+  } else {
+    WF_CUDA(cudaMemsetAsync(P->d_s, 0, sizeof(double2) * P->nalm, s));
+    WF_CUDA(cudaMemsetAsync(P->d_FS, 0, sizeof(double4_32a) * (size_t)(P->lmax + 1) * P->RP, s));
+  }
+  Ctl c = P->make_ctl(1, lam0, lsht0, 0);
+  *P->h_ctl = c;
+  WF_CUDA(cudaMemcpyAsync(P->d_ctl, P->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  // one CUDA graph holds graph_iters iterations; the controller stops the rest early
+  if (!P->graph_exec) {
+    cudaGraph_t g;
+    WF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < P->opt.graph_iters; ++i) P->enqueue_iteration(s);
+    WF_CUDA(cudaStreamEndCapture(s, &g));
+    cudaError_t e = cudaGraphInstantiate(&P->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
+  }
+  const int max_launch = (P->opt.max_iter + P->opt.graph_iters - 1) / P->opt.graph_iters + 1;
+  for (int it = 0; it < max_launch; ++it) {
+    WF_CUDA(cudaGraphLaunch(P->graph_exec, s));
+    WF_CUDA(cudaMemcpyAsync(P->h_ctl, P->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaStreamSynchronize(s));
+    if (P->h_ctl->done) break;
+  }
+  const auto kind_out = alm_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  WF_CUDA(cudaMemcpyAsync(alm_out, P->d_s, sizeof(double2) * P->nalm, kind_out, s));
+  WF_CUDA(cudaEventRecord(P->ev1, s));
+  const Ctl fin = *P->h_ctl;
+  wf_iter_record last{};
+  if (fin.iter > 0)
+    WF_CUDA(cudaMemcpyAsync(&last, P->d_hist + (fin.iter - 1), sizeof(last), cudaMemcpyDeviceToHost, s));
+  int nrec = 0;
+  if (records && max_records > 0) {
+    nrec = fin.iter < max_records ? fin.iter : max_records;
+    if (nrec > 0)
+      WF_CUDA(cudaMemcpyAsync(records, P->d_hist, sizeof(wf_iter_record) * nrec, cudaMemcpyDeviceToHost, s));
+  }
+  WF_CUDA(cudaStreamSynchronize(s));
+  if (n_records) *n_records = nrec;
+  P->fs_valid = false;
+  if (stats) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+    stats->iters = fin.iter;
+    stats->converged = fin.converged;
+    stats->levels = fin.level + 1;
+    stats->lmax_sht_final = fin.lsht;
+    stats->lambda_final = fin.lambda;
+    stats->chi2_prior = last.chi2_prior;
+    stats->chi2_noise = last.chi2_noise;
+    stats->chi2 = last.chi2_prior + last.chi2_noise;
+    stats->chi2_per_dof = stats->chi2 / (double)P->n_obs;
+    stats->rel_increment = fin.last_rel;
+    stats->ms_device = ms;
+  }
+  if (fin.numeric) { set_error("wf_solve: chi^2 is not finite"); return WF_ENUMERIC; }
+  if (!fin.converged) { set_error("wf_solve: max_iter reached before the stop rule"); return WF_ENOTCONVERGED; }
+  return WF_OK;
+}
+
+wf_status wf_solve(wf_plan_t plan, const double *d, int d_on_device, double *alm_out, int alm_on_device,
+                   const double *alm_init, wf_stats *stats) {
+  if (!plan || !d || !alm_out) { set_error("wf_solve: NULL argument"); return WF_EINVAL; }
+  return solve_impl(static_cast<Plan *>(plan), d, d_on_device, alm_out, alm_on_device, alm_init, stats, nullptr, 0,
+                    nullptr);
+}
+
+wf_status wf_solve_history(wf_plan_t plan, const double *d, int d_on_device, double *alm_out, int alm_on_device,
+                           wf_stats *stats, wf_iter_record *records, int max_records, int *n_records) {
+  if (!plan || !d || !alm_out) { set_error("wf_solve_history: NULL argument"); return WF_EINVAL; }
+  return solve_impl(static_cast<Plan *>(plan), d, d_on_device, alm_out, alm_on_device, nullptr, stats, records,
+                    max_records, n_records);
+}
+
+}  // extern "C"

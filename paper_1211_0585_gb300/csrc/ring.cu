@@ -1,0 +1,270 @@
+// Ring stage of the HEALPix spherical harmonic transform pair, FP64.
+//
+// One CTA per ring. A ring of n pixels at azimuths phi_j = phi0 + 2 pi j / n
+// (phi0 = pi / n for shifted rings, 0 otherwise) carries the Fourier
+// coefficients F_m, m = 0 .. lsht, of the Legendre stage. Synthesis folds every
+// frequency -lsht .. lsht onto its residue q = m mod n (m-aliasing on rings
+// shorter than 2 lsht + 1) and applies an inverse DFT of length n; analysis is
+// the forward DFT followed by the same unfolding:
+//     f_j  = sum_q G_q e^{+2 pi i j q / n},  G_q = e^{i q phi0} sum_{m = q mod n} (-1)^{(m-q)/n [shifted]} F_m
+//     T_m  = Omega e^{-i m phi0} sum_j u_j e^{-2 pi i j m / n}
+// (Sect. 2: the basis change between pixel space and harmonic space, here its
+// azimuthal half.) Power-of-two n use an in-place radix-2 FFT in shared
+// memory; other n (polar rings, n = 4i) use Bluestein's chirp-z convolution
+// with a power-of-two size M >= 2n - 1, whose filter spectrum is precomputed
+// per ring length.
+//
+// RING_ITER fuses the pixel-space half of one messenger iteration between the
+// two transforms: s_p = f_p, r_p = d_p - s_p, the chi^2 partials of Sect. 3
+// (sum w r^2 and sum w r^2 / (1 + (lambda - 1) tau w)) and the Eq. 3 increment
+// u_p = t_p - s_p = a_p r_p with a_p = lambda tau w_p / (1 + (lambda - 1) tau w_p).
+#include <cuda_runtime.h>
+
+#include "wf_internal.h"
+
+namespace wfk {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+
+__device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+
+// In-place radix-2 decimation in frequency: natural order in, bit-reversed out.
+// sign < 0: kernel e^{-2 pi i jk / M}; sign > 0: e^{+2 pi i jk / M} (unnormalised).
+__device__ void fft_dif(double2 *buf, int logM, int sign, const double2 *tw, int logMmax) {
+  const int M = 1 << logM;
+  for (int s = logM; s >= 1; --s) {
+    const int half = 1 << (s - 1);
+    const int tsh = logMmax - s;
+    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
+      const int pos = t & (half - 1);
+      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
+      double2 w = tw[pos << tsh];
+      if (sign > 0) w.y = -w.y;
+      const double2 a = buf[i0], b = buf[i1];
+      buf[i0] = cadd(a, b);
+      buf[i1] = cmul(csub(a, b), w);
+    }
+    __syncthreads();
+  }
+}
+
+// In-place radix-2 decimation in time: bit-reversed order in, natural out.
+__device__ void fft_dit(double2 *buf, int logM, int sign, const double2 *tw, int logMmax) {
+  const int M = 1 << logM;
+  for (int s = 1; s <= logM; ++s) {
+    const int half = 1 << (s - 1);
+    const int tsh = logMmax - s;
+    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
+      const int pos = t & (half - 1);
+      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
+      double2 w = tw[pos << tsh];
+      if (sign > 0) w.y = -w.y;
+      const double2 a = buf[i0], b = cmul(buf[i1], w);
+      buf[i0] = cadd(a, b);
+      buf[i1] = csub(a, b);
+    }
+    __syncthreads();
+  }
+}
+
+// Bluestein core: on entry buf[0..n) holds x_j c_j (c_j = e^{-i pi j^2 / n}),
+// buf[n..M) zero; on exit buf[k] (natural order) = sum_j x_j c_j conj(c_{k-j}),
+// so that DFT_n(x)_k = c_k buf[k] for k < n.
+__device__ void bluestein_conv(double2 *buf, int logM, const double2 *Bf, const double2 *tw, int logMmax) {
+  const int M = 1 << logM;
+  fft_dif(buf, logM, -1, tw, logMmax);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) buf[i] = cmul(buf[i], Bf[i]);
+  __syncthreads();
+  fft_dit(buf, logM, +1, tw, logMmax);
+}
+
+// Deterministic block sum of two doubles (fixed tree); result valid in thread 0.
+__device__ void block_sum2(double &a, double &b, double *red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[2 * warp] = a; red[2 * warp + 1] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { sa += red[2 * w2]; sb += red[2 * w2 + 1]; }
+    a = sa; b = sb;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) ring_kernel(const RingArgs A) {
+  extern __shared__ double2 smem[];
+  const int r = blockIdx.x;
+  const RingDev rg = A.rings[r];
+  const int n = rg.n;
+  const int M = 1 << rg.logM;
+  double2 *buf = smem;                          // [M]
+  double *ureal = reinterpret_cast<double *>(smem + M);  // [n]
+  __shared__ double red[64];
+
+  int L = A.lsht;
+  double lam = 1.0;
+  if (MODE == RING_ITER) {
+    if (A.ctl->done) return;
+    L = A.ctl->lsht;
+    lam = A.ctl->lambda;
+  }
+  const double2 *hs = A.hs + rg.hs_off;
+  const double2 *ch = A.chirp + rg.ch_off;
+  const double2 *Bf = A.B + rg.B_off;
+  const int k = rg.pair;
+  const int slot = rg.side;
+
+  if (MODE == RING_SYNTH || MODE == RING_ITER) {
+    // ---- fold F_m onto residues q (m-aliasing) with the half-pixel shift
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+      int j = 0;
+      for (int m = q; m <= L; m += n, ++j) {
+        const double4_32a f4 = A.FS[(size_t)m * A.RP + k];
+        double2 f = slot ? make_double2(f4.z, f4.w) : make_double2(f4.x, f4.y);
+        if (rg.shifted && (j & 1)) { f.x = -f.x; f.y = -f.y; }
+        acc = cadd(acc, f);
+      }
+      j = 1;
+      for (int m = (q == 0 ? n : n - q); m <= L; m += n, ++j) {
+        const double4_32a f4 = A.FS[(size_t)m * A.RP + k];
+        double2 f = slot ? make_double2(f4.z, -f4.w) : make_double2(f4.x, -f4.y);
+        if (rg.shifted && (j & 1)) { f.x = -f.x; f.y = -f.y; }
+        acc = cadd(acc, f);
+      }
+      if (rg.shifted) acc = cmul(acc, hs[q]);
+      if (rg.blue) {
+        buf[q] = cmul(conjd(acc), ch[q]);   // inverse DFT via conj(DFT(conj(G)))
+      } else {
+        buf[q] = acc;
+      }
+    }
+    if (rg.blue) {
+      for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[q] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (rg.blue) {
+      bluestein_conv(buf, rg.logM, Bf, A.tw, A.logMmax);
+    } else {
+      fft_dif(buf, rg.logM, +1, A.tw, A.logMmax);
+    }
+    // pixel values: Re of the inverse DFT
+    if (MODE == RING_SYNTH) {
+      for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const double f = rg.blue ? cmul(ch[p], buf[p]).x : buf[bitrev(p, rg.logM)].x;
+        A.map_out[rg.off + p] = f;
+      }
+      return;
+    }
+    // ---- RING_ITER: Eq. 3 per pixel and the chi^2 partials
+    double c2n = 0.0, c2l = 0.0;
+    const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      const double s = rg.blue ? cmul(ch[p], buf[p]).x : buf[bitrev(p, rg.logM)].x;
+      const double w = A.w[rg.off + p];
+      const double res = A.d[rg.off + p] - s;
+      const double wr2 = w * res * res;
+      const double g = w / (1.0 + l1t * w);   // 1 / (sigma^2 + (lambda - 1) tau), 0 if masked
+      c2n += wr2;
+      c2l += g * res * res;
+      ureal[p] = lt * g * res;                 // a_p (d_p - s_p)
+    }
+    block_sum2(c2n, c2l, red);
+    if (threadIdx.x == 0) {
+      A.ring_part[2 * r] = c2n;
+      A.ring_part[2 * r + 1] = c2l;
+    }
+    __syncthreads();
+  } else {
+    for (int p = threadIdx.x; p < n; p += blockDim.x) ureal[p] = A.map_in[rg.off + p];
+    __syncthreads();
+  }
+
+  // ---- forward DFT of the real ring values
+  if (rg.blue) {
+    for (int p = threadIdx.x; p < M; p += blockDim.x)
+      buf[p] = p < n ? make_double2(ureal[p] * ch[p].x, ureal[p] * ch[p].y) : make_double2(0.0, 0.0);
+    __syncthreads();
+    bluestein_conv(buf, rg.logM, Bf, A.tw, A.logMmax);
+  } else {
+    for (int p = threadIdx.x; p < n; p += blockDim.x) buf[bitrev(p, rg.logM)] = make_double2(ureal[p], 0.0);
+    __syncthreads();
+    fft_dit(buf, rg.logM, -1, A.tw, A.logMmax);
+  }
+  // ---- unfold residues to m = 0 .. L, apply e^{-i m phi0} and Omega
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    const int q = m % n, j = m / n;
+    double2 U = rg.blue ? cmul(ch[q], buf[q]) : buf[q];
+    if (rg.shifted) {
+      U = cmul(U, conjd(hs[q]));
+      if (j & 1) { U.x = -U.x; U.y = -U.y; }
+    }
+    double *dst = reinterpret_cast<double *>(A.FT + (size_t)m * A.RP + k) + 2 * slot;
+    dst[0] = A.omega * U.x;
+    dst[1] = A.omega * U.y;
+  }
+}
+
+// Bluestein filter spectrum per ring length: b_q = conj(c_q) for |q| < n
+// (wrapped into [0, M)), transformed by the DIF FFT (so stored bit-reversed)
+// and scaled by 1/M. One CTA per ring; only the first ring of each length
+// (the north ring of a polar pair) writes.
+__global__ void __launch_bounds__(kThreads) bluestein_setup_kernel(const RingDev *rings, const double2 *tw,
+                                                                   int logMmax, const double2 *chirp,
+                                                                   double2 *B) {
+  extern __shared__ double2 smem[];
+  const RingDev rg = rings[blockIdx.x];
+  if (!rg.blue || rg.side != 0) return;
+  const int n = rg.n, M = 1 << rg.logM;
+  const double2 *ch = chirp + rg.ch_off;
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (q < n) v = conjd(ch[q]);
+    else if (q > M - n) v = conjd(ch[M - q]);
+    smem[q] = v;
+  }
+  __syncthreads();
+  fft_dif(smem, rg.logM, -1, tw, logMmax);
+  const double inv = 1.0 / (double)M;
+  for (int q = threadIdx.x; q < M; q += blockDim.x)
+    B[rg.B_off + q] = make_double2(smem[q].x * inv, smem[q].y * inv);
+}
+
+static size_t ring_smem(int maxM, int maxN) { return (size_t)maxM * sizeof(double2) + (size_t)maxN * sizeof(double); }
+
+void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode) {
+  // the largest ring has at most maxM / 2 pixels when maxM comes from Bluestein, maxM otherwise
+  const size_t sm = ring_smem(maxM, maxM);
+  switch (mode) {
+    case RING_SYNTH:
+      cudaFuncSetAttribute(ring_kernel<RING_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      ring_kernel<RING_SYNTH><<<R, kThreads, sm, s>>>(a);
+      break;
+    case RING_ANALYSIS:
+      cudaFuncSetAttribute(ring_kernel<RING_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      ring_kernel<RING_ANALYSIS><<<R, kThreads, sm, s>>>(a);
+      break;
+    default:
+      cudaFuncSetAttribute(ring_kernel<RING_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      ring_kernel<RING_ITER><<<R, kThreads, sm, s>>>(a);
+      break;
+  }
+}
+
+void launch_bluestein_setup(const RingDev *rings, int R, const double2 *tw, int logMmax, const double2 *chirp,
+                            double2 *B, int maxM, cudaStream_t s) {
+  const size_t sm = (size_t)maxM * sizeof(double2);
+  cudaFuncSetAttribute(bluestein_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  bluestein_setup_kernel<<<R, kThreads, sm, s>>>(rings, tw, logMmax, chirp, B);
+}
+
+}  // namespace wfk

@@ -1,0 +1,114 @@
+// Internal declarations of the GB300 messenger-field Wiener filter library.
+// Device data layout (one plan = one HEALPix nside and one lmax):
+//   rings      R  = 4 nside - 1, north to south; ring pairs RP = 2 nside
+//              (pair k = north ring k and south ring R-1-k; the equator ring
+//              2 nside - 1 is a pair of its own, its south slot unused).
+//   Fourier    F[m * RP + k] = double4_32a (north re, north im, south re, south im),
+//              m = 0 .. lmax, the azimuthal coefficients of ring pair k.
+//              FS: synthesis side (from a_lm), FT: analysis side (to a_lm).
+//   a_lm       m-major complex doubles, index(l, m) = m (2 lmax + 1 - m) / 2 + l.
+//   maps       RING order doubles.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/wf.h"
+
+namespace wfk {
+
+constexpr int kThreads = 256;       // block size of every per-ring / per-m kernel
+constexpr int kLB = 16;             // l values per block of the analysis reduction
+constexpr int kStartExp = -100;     // Legendre terms below 2^-100 are not evaluated
+
+// Per-ring description (host-built, read by the ring kernel).
+struct RingDev {
+  long long off;      // first pixel (RING index)
+  int n;              // pixels in the ring (nphi)
+  int pair;           // ring pair index k
+  int side;           // 0 = north slot, 1 = south slot of the pair
+  int shifted;        // first pixel at phi = pi / n (else at phi = 0)
+  int logM;           // log2 of the FFT size (n itself, or the Bluestein size)
+  int blue;           // 1: n is not a power of two, Bluestein convolution of size M
+  long long hs_off;   // offset of this ring length's half-shift table e^{i pi q / n}
+  long long ch_off;   // offset of this ring length's chirp e^{-i pi j^2 / n} (Bluestein only)
+  long long B_off;    // offset of this ring length's Bluestein filter (bit-reversed, / M)
+};
+
+// Iteration controller state, resident on the device (Sect. 3 schedule).
+struct Ctl {
+  // configuration
+  int mode;             // 0: fixed lambda and lsht for n_fixed iterations; 1: cooling schedule
+  int n_fixed;
+  int max_iter;
+  int cooling, l_iter0, margin, band_limit, min_level_iters, max_level_iters;
+  int lmax;
+  double tol, plateau_eps, final_dchi2, sigma_chi2, tau, omega;
+  // live state
+  double lambda;
+  int lsht, l_iter, level, level_iters, iter, done, converged, numeric;
+  int have_prev;
+  double prev_chi2;
+  double last_rel;
+};
+
+// Record layout of one iteration (mirrors wf_iter_record).
+static_assert(sizeof(wf_iter_record) == 6 * 8 + 2 * 4, "record layout");
+
+struct Plan;
+
+// ---------------------------------------------------------------- launches
+// ring kernel modes
+enum { RING_SYNTH = 0, RING_ANALYSIS = 1, RING_ITER = 2 };
+// Legendre kernel modes
+enum { LEG_SYNTH = 0, LEG_ANALYSIS = 1, LEG_ITER = 2 };
+
+struct RingArgs {
+  const RingDev *rings;
+  const double2 *tw;      // e^{-2 pi i k / Mmax}, k < Mmax / 2
+  int logMmax;
+  const double2 *hs, *chirp, *B;
+  const double4_32a *FS;      // synthesis input (RING_SYNTH / RING_ITER)
+  double4_32a *FT;            // analysis output (RING_ANALYSIS / RING_ITER)
+  int RP;
+  const double *map_in;   // RING_ANALYSIS input
+  double *map_out;        // RING_SYNTH output
+  const double *d, *w;    // RING_ITER: data, inverse noise (0 = masked)
+  double *ring_part;      // RING_ITER: [R][2] chi2_N, chi2_lambda_N partials
+  const Ctl *ctl;         // RING_ITER: lambda, lsht, done
+  int lsht;               // standalone modes
+  double omega, tau;
+};
+
+struct LegArgs {
+  const double *x;        // [RP] cos(theta) of the north ring of each pair
+  const double2 *rec;     // [nalm] recurrence coefficients (a_l, b_l)
+  const int *ls;          // [(lmax+1) RP] first evaluated l
+  const double2 *sv;      // [(lmax+1) RP] (lambda_{ls}, lambda_{ls+1})
+  const double *cl;       // [lmax+1]
+  const double4_32a *FT;      // analysis input
+  double4_32a *FS;            // synthesis output
+  double2 *alm;           // state / output a_lm
+  const double2 *alm_in;  // LEG_SYNTH input
+  double *m_part;         // LEG_ITER: [lmax+1][3] chi2_S, incr2, norm2
+  const Ctl *ctl;
+  int lsht, lmax, RP;
+  double omega, tau;
+};
+
+void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode);
+void launch_legendre(const LegArgs &a, cudaStream_t s, int mode);
+void launch_start_values(const double *x, const double2 *rec, int lmax, int RP, int *ls,
+                         double2 *sv, cudaStream_t s);
+void launch_bluestein_setup(const RingDev *rings, int R, const double2 *tw, int logMmax,
+                            const double2 *chirp, double2 *B, int maxM, cudaStream_t s);
+void launch_control(Ctl *ctl, const double *ring_part, int R, const double *m_part, int lmax,
+                    const double *cl, wf_iter_record *hist, int hist_cap, cudaStream_t s);
+
+// error plumbing
+void set_error(const std::string &msg);
+wf_status cuda_status(cudaError_t e, const char *where);
+
+}  // namespace wfk

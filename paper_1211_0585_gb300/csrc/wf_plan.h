@@ -1,0 +1,61 @@
+// Plan object behind the opaque wf_plan_t handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "wf_internal.h"
+
+struct wf_plan_s {
+  virtual ~wf_plan_s() = default;
+};
+
+namespace wfk {
+
+struct Plan : wf_plan_s {
+  int nside = 0, lmax = 0, R = 0, RP = 0;
+  long long npix = 0, nalm = 0, n_obs = 0;
+  double tau = 0.0, omega = 0.0;
+  wf_options opt{};
+  std::vector<double> h_cl;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int maxM = 1, logMmax = 0;
+  size_t device_bytes = 0;
+  std::vector<void *> allocs;
+
+  // geometry and tables
+  RingDev *d_rings = nullptr;
+  double2 *d_tw = nullptr, *d_hs = nullptr, *d_chirp = nullptr, *d_B = nullptr;
+  double *d_x = nullptr;
+  double2 *d_rec = nullptr, *d_sv = nullptr;
+  int *d_ls = nullptr;
+  double *d_cl = nullptr, *d_w = nullptr;
+  // working state
+  double4_32a *d_FS = nullptr, *d_FT = nullptr;
+  double *d_ring_part = nullptr, *d_m_part = nullptr;
+  Ctl *d_ctl = nullptr;
+  Ctl *h_ctl = nullptr;  // pinned mirror
+  wf_iter_record *d_hist = nullptr;
+  int hist_cap = 0;
+  double *d_d = nullptr;
+  double2 *d_s = nullptr;
+  bool fs_valid = false;
+  int fs_lsht = -1;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~Plan() override;
+  wf_status dalloc(void **p, size_t bytes);
+  wf_status alloc_work();
+  wf_status ensure_hist(int cap);
+  cudaStream_t run_stream() const;
+  RingArgs ring_args() const;
+  LegArgs leg_args() const;
+  void enqueue_iteration(cudaStream_t s);
+  Ctl make_ctl(int mode, double lambda, int lsht, int n_fixed) const;
+  double lambda_of(int l_iter) const;
+};
+
+}  // namespace wfk

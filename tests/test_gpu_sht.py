@@ -1,0 +1,95 @@
+"""GPU spherical harmonic transform pair against the oracle, element by
+element (bar: 1e-12 relative to the largest value)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1211_0585_gb300 import inputs as I
+from paper_1211_0585_gb300 import wf
+
+from gpu_util import dev, host_alm
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(1, 2), (2, 6), (4, 8), (4, 13), (8, 16), (16, 32), (16, 64), (32, 64), (64, 128), (64, 40)]
+
+
+def plan_for(nside, lmax):
+    return wf.Plan(nside, lmax, np.ones(lmax + 1), np.ones(12 * nside * nside))
+
+
+@pytest.mark.parametrize("nside,lmax", CASES)
+def test_alm2map(nside, lmax):
+    import torch
+    rng = np.random.default_rng(nside * 1000 + lmax)
+    alm = I.draw_alm(np.ones(lmax + 1), rng)
+    ref = O.alm2map(nside, lmax, alm)
+    P = plan_for(nside, lmax)
+    a = dev(alm)
+    m = torch.empty(12 * nside * nside, dtype=torch.float64, device="cuda")
+    P.alm2map(lmax, a.data_ptr(), m.data_ptr())
+    torch.cuda.synchronize()
+    got = m.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nside,lmax", CASES)
+def test_map2alm(nside, lmax):
+    import torch
+    rng = np.random.default_rng(nside * 7 + lmax)
+    f = rng.standard_normal(12 * nside * nside)
+    ref = O.map2alm(nside, lmax, f)
+    P = plan_for(nside, lmax)
+    a = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
+    P.map2alm(lmax, dev(f).data_ptr(), a.data_ptr())
+    torch.cuda.synchronize()
+    got = host_alm(a)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nside,lmax,lsht", [(16, 48, 20), (32, 64, 0), (32, 64, 5)])
+def test_band_limited(nside, lmax, lsht):
+    """With band limit lsht only l <= lsht take part; analysis zeroes the rest."""
+    import torch
+    rng = np.random.default_rng(3)
+    alm = I.draw_alm(np.ones(lmax + 1), rng)
+    ref = O.alm2map(nside, lsht, O.truncate_alm(alm, lmax, lsht))
+    P = plan_for(nside, lmax)
+    m = torch.empty(12 * nside * nside, dtype=torch.float64, device="cuda")
+    P.alm2map(lsht, dev(alm).data_ptr(), m.data_ptr())
+    f = rng.standard_normal(12 * nside * nside)
+    a = dev(np.full(P.nalm, 7.0 + 0j))
+    P.map2alm(lsht, dev(f).data_ptr(), a.data_ptr())
+    torch.cuda.synchronize()
+    assert np.max(np.abs(m.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+    refa = O.embed_alm(O.map2alm(nside, lsht, f), lsht, lmax)
+    got = host_alm(a)
+    assert np.max(np.abs(got - refa)) <= 1e-12 * np.max(np.abs(refa))
+
+
+def test_sampled_full_size_nside512():
+    """At the WMAP-shaped size (Nside 512, lmax 1024): sampled pixels of the
+    synthesis and sampled modes of the analysis, each computed one by one by
+    the oracle."""
+    import torch
+    nside, lmax = 512, 1024
+    rng = np.random.default_rng(512)
+    cl = I.cl_lcdm_like(lmax, 13.0)
+    alm = I.draw_alm(cl, rng)
+    P = plan_for(nside, lmax)
+    m = torch.empty(12 * nside * nside, dtype=torch.float64, device="cuda")
+    P.alm2map(lmax, dev(alm).data_ptr(), m.data_ptr())
+    f = rng.standard_normal(12 * nside * nside)
+    a = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
+    P.map2alm(lmax, dev(f).data_ptr(), a.data_ptr())
+    torch.cuda.synchronize()
+    got_map = m.cpu().numpy()
+    pix = np.concatenate([rng.integers(0, f.size, 24), [0, 1, 5, f.size - 1, f.size // 2]])
+    ref = O.alm2map_pixels(nside, lmax, alm, pix)
+    scale = np.max(np.abs(got_map))
+    assert np.max(np.abs(got_map[pix] - ref)) <= 1e-11 * scale
+    ls = np.array([0, 1, 2, 100, 1024, 1024, 700, 513, 1000, 37])
+    ms = np.array([0, 0, 2, 50, 0, 1024, 699, 1, 999, 30])
+    refa = O.map2alm_modes(nside, lmax, f, ls, ms)
+    got = host_alm(a)[O.alm_index(lmax, ls, ms)]
+    assert np.max(np.abs(got - refa)) <= 1e-11 * np.max(np.abs(host_alm(a)))
