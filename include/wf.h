@@ -115,8 +115,8 @@ wf_status wf_options_default(wf_options *opt);
 /* Create a plan for one (nside, lmax, C_l, noise, mask) problem: builds the
  * ring geometry, FFT tables, Legendre recurrence tables, tau = min over
  * observed pixels of noise_var (Sect. 2), and allocates all device buffers.
- *   nside      : power of two, 1 .. 8192
- *   lmax       : 0 .. 4 nside (and <= 16384)
+ *   nside      : power of two, 1 .. 1024 (the ring FFTs keep a whole ring in shared memory)
+ *   lmax       : 0 .. 4 nside
  *   cl         : host [lmax+1], beam folded in, >= 0 and finite (C_l = 0: mode not solved for)
  *   noise_var  : host [Npix] sigma_p^2, finite and > 0 on observed pixels
  *   mask       : host [Npix] 1 = observed, 0 = masked (N^-1 = 0); NULL = all observed
@@ -151,6 +151,14 @@ wf_status wf_map2alm(wf_plan_t plan, int lsht, const double *map_dev, double *al
  * Synchronises the plan's stream before returning. */
 wf_status wf_iterate(wf_plan_t plan, const double *d_dev, double *s_dev, double lambda, int lsht,
                      int niter, int reset_state, wf_iter_record *records);
+
+/* Timing aid: like wf_iterate (no records, state in s_dev), but with CUDA
+ * events around each kernel of the iteration on the plan's stream. Writes the
+ * average device time in ms per launch of: ms[0] the ring kernel (FFTs and the
+ * Eq. 3 update), ms[1] the Legendre kernel (analysis, Eq. 4, synthesis),
+ * ms[2] the controller. Synchronises before returning. */
+wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_dev, double lambda, int lsht,
+                                int niter, float ms[3]);
 
 /* Full solve with the cooling schedule and stop rule of Sect. 3.
  *   d        : [Npix] data, host or device (d_on_device)

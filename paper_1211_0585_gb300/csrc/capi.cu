@@ -480,6 +480,53 @@ wf_status wf_iterate(wf_plan_t plan, const double *d_dev, double *s_dev, double 
   return WF_OK;
 }
 
+wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_dev, double lambda, int lsht,
+                                int niter, float ms[3]) {
+  if (!plan || !d_dev || !s_dev || !ms) { set_error("wf_profile_iterations: NULL argument"); return WF_EINVAL; }
+  Plan *P = static_cast<Plan *>(plan);
+  if (lsht < 0 || lsht > P->lmax || niter < 1 || !(lambda >= 1.0)) {
+    set_error("wf_profile_iterations: bad lambda / lsht / niter");
+    return WF_EINVAL;
+  }
+  wf_status st = P->ensure_hist(niter + 1);
+  if (st) return st;
+  cudaStream_t s = P->run_stream();
+  WF_CUDA(cudaMemcpyAsync(P->d_d, d_dev, sizeof(double) * P->npix, cudaMemcpyDeviceToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_s, s_dev, sizeof(double2) * P->nalm, cudaMemcpyDeviceToDevice, s));
+  LegArgs la = P->leg_args();
+  la.lsht = lsht;
+  la.alm_in = P->d_s;
+  launch_legendre(la, s, LEG_SYNTH);
+  Ctl c = P->make_ctl(0, lambda, lsht, niter);
+  *P->h_ctl = c;
+  WF_CUDA(cudaMemcpyAsync(P->d_ctl, P->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  std::vector<cudaEvent_t> ev(4 * niter);
+  for (auto &e : ev) WF_CUDA(cudaEventCreate(&e));
+  for (int i = 0; i < niter; ++i) {
+    cudaEventRecord(ev[4 * i], s);
+    launch_ring(P->ring_args(), P->R, P->maxM, s, RING_ITER);
+    cudaEventRecord(ev[4 * i + 1], s);
+    launch_legendre(P->leg_args(), s, LEG_ITER);
+    cudaEventRecord(ev[4 * i + 2], s);
+    launch_control(P->d_ctl, P->d_ring_part, P->R, P->d_m_part, P->lmax, P->d_cl, P->d_hist, P->hist_cap, s);
+    cudaEventRecord(ev[4 * i + 3], s);
+  }
+  WF_CUDA(cudaGetLastError());
+  WF_CUDA(cudaMemcpyAsync(s_dev, P->d_s, sizeof(double2) * P->nalm, cudaMemcpyDeviceToDevice, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  double acc[3] = {0, 0, 0};
+  for (int i = 0; i < niter; ++i)
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[4 * i + k], ev[4 * i + k + 1]);
+      acc[k] += t;
+    }
+  for (auto &e : ev) cudaEventDestroy(e);
+  for (int k = 0; k < 3; ++k) ms[k] = (float)(acc[k] / niter);
+  P->fs_valid = false;
+  return WF_OK;
+}
+
 static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *alm_out, int alm_on_device,
                             const double *alm_init, wf_stats *stats, wf_iter_record *records, int max_records,
                             int *n_records) {

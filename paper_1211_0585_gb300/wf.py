@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "W
                 5: "WF_ENUMERIC", 6: "WF_ETIMEOUT", 7: "WF_EBUSY", 8: "WF_ECANCELLED", 9: "WF_ENOTFOUND"}
 
 EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_info", "wf_plan_set_options",
-            "wf_alm2map", "wf_map2alm", "wf_iterate", "wf_solve", "wf_solve_history", "wf_solve_batch",
+            "wf_alm2map", "wf_map2alm", "wf_iterate", "wf_profile_iterations", "wf_solve", "wf_solve_history", "wf_solve_batch",
             "wf_server_create", "wf_submit", "wf_poll", "wf_server_drain", "wf_server_stats",
             "wf_server_destroy", "wf_last_error"]
 
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "wf_alm2map": [_vp, _i, _vp, _vp],
         "wf_map2alm": [_vp, _i, _vp, _vp],
         "wf_iterate": [_vp, _vp, _vp, _d, _i, _i, _i, ctypes.POINTER(IterRecord)],
+        "wf_profile_iterations": [_vp, _vp, _vp, _d, _i, _i, ctypes.POINTER(ctypes.c_float)],
         "wf_solve": [_vp, _vp, _i, _vp, _i, _vp, ctypes.POINTER(Stats)],
         "wf_solve_history": [_vp, _vp, _i, _vp, _i, ctypes.POINTER(Stats), ctypes.POINTER(IterRecord), _i,
                              ctypes.POINTER(_i)],
@@ -191,6 +192,13 @@ class Plan:
         _check(load().wf_iterate(self.handle, ctypes.c_void_p(d_dev), ctypes.c_void_p(s_dev), float(lam), lsht,
                                  niter, 1 if reset else 0, recs))
         return [recs[i].as_dict() for i in range(niter)]
+
+    def profile(self, d_dev: int, s_dev: int, lam: float, lsht: int, niter: int):
+        """Average device ms per launch of (ring kernel, Legendre kernel, controller)."""
+        ms = (ctypes.c_float * 3)()
+        _check(load().wf_profile_iterations(self.handle, ctypes.c_void_p(d_dev), ctypes.c_void_p(s_dev), float(lam),
+                                            lsht, niter, ms))
+        return dict(ring=ms[0], legendre=ms[1], control=ms[2])
 
     def solve(self, d, alm_out=None, alm_init=None, on_device=False, history=0):
         """d: numpy (host) or device address (on_device=True). Returns (alm or None, stats, status, records)."""
