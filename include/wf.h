@@ -143,6 +143,26 @@ wf_status wf_alm2map(wf_plan_t plan, int lsht, const double *alm_dev, double *ma
  * (entries with l > lsht are set to 0): the basis change of Sect. 2. */
 wf_status wf_map2alm(wf_plan_t plan, int lsht, const double *map_dev, double *alm_dev);
 
+/* Allocation-free map2alm: alm = Y^dagger map exactly as wf_map2alm with
+ * lsht = lmax, but with no plan and no device allocation on the call path. The
+ * paper has no counterpart; this entry point exists for callers that cannot
+ * call cudaMalloc -- code running under a device-memory budget owned by another
+ * allocator (a framework's caching allocator or a fixed pool) and
+ * latency-critical loops that cannot take cudaMalloc's implicit device
+ * synchronisation.
+ *   nside, lmax : as wf_plan_create; the tables and Fourier scratch for this
+ *                 size must fit the library's static 16 MiB device array
+ *                 (for example nside 128 with lmax 256 fits, nside 256 does not):
+ *                 larger sizes return WF_EINVAL with the bytes they would need.
+ *   map_dev     : device [Npix] input; alm_dev : device [2*nalm] output.
+ *   stream      : cudaStream_t, NULL = the default stream. Enqueues and returns.
+ * The scratch array is one per GPU, held from library load to process exit and
+ * shared by every call on that GPU: calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * The first call on each device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture. */
+wf_status wf_map2alm_noalloc(int nside, int lmax, const double *map_dev, double *alm_dev, void *stream);
+
 /* Run `niter` messenger iterations (Eqs. 3-4) at fixed lambda (>= 1) and band
  * limit lsht, in place on the device state s_dev [2*nalm], with data d_dev
  * [Npix]. If `reset_state` is 1, s_dev is taken as a fresh start (its synthesis

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "W
                 5: "WF_ENUMERIC", 6: "WF_ETIMEOUT", 7: "WF_EBUSY", 8: "WF_ECANCELLED", 9: "WF_ENOTFOUND"}
 
 EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_info", "wf_plan_set_options",
-            "wf_alm2map", "wf_map2alm", "wf_iterate", "wf_profile_iterations", "wf_solve", "wf_solve_history", "wf_solve_batch",
+            "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
+            "wf_solve_history", "wf_solve_batch",
             "wf_server_create", "wf_submit", "wf_poll", "wf_server_drain", "wf_server_stats",
             "wf_server_destroy", "wf_last_error"]
 
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
         "wf_plan_set_options": [_vp, ctypes.POINTER(Options)],
         "wf_alm2map": [_vp, _i, _vp, _vp],
         "wf_map2alm": [_vp, _i, _vp, _vp],
+        "wf_map2alm_noalloc": [_i, _i, _vp, _vp, _vp],
         "wf_iterate": [_vp, _vp, _vp, _d, _i, _i, _i, ctypes.POINTER(IterRecord)],
         "wf_profile_iterations": [_vp, _vp, _vp, _d, _i, _i, ctypes.POINTER(ctypes.c_float)],
         "wf_solve": [_vp, _vp, _i, _vp, _i, _vp, ctypes.POINTER(Stats)],
@@ -121,6 +123,13 @@ def _check(st, ok=(WF_OK,)):
 
 def _host_ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def map2alm_noalloc(nside: int, lmax: int, map_dev: int, alm_dev: int, stream: int = 0):
+    """Plan-free map2alm that allocates no device memory (static 16 MiB scratch
+    per GPU; concurrent calls on one GPU must be serialised by the caller)."""
+    _check(load().wf_map2alm_noalloc(nside, lmax, ctypes.c_void_p(map_dev), ctypes.c_void_p(alm_dev),
+                                     ctypes.c_void_p(stream) if stream else None))
 
 
 def options(**kw) -> Options:
