@@ -62,7 +62,12 @@ typedef enum {
   WF_ENOTFOUND = 9        /* unknown ticket */
 } wf_status;
 
-typedef enum { WF_PREC_FP64 = 0, WF_PREC_MIXED = 1 } wf_precision;
+/* WF_PREC_FP64        FP64-accurate: the Legendre stage in double-float arithmetic (pairs of
+ *                     floats with error-free transformations, 48-bit significands) because
+ *                     GB300 runs FP64 at 1/63 of its FP32 rate; everything else in double.
+ * WF_PREC_MIXED       FP32 transforms with FP64 residuals and refinement.
+ * WF_PREC_FP64_NATIVE every step in native double arithmetic (the plain reference kernels). */
+typedef enum { WF_PREC_FP64 = 0, WF_PREC_MIXED = 1, WF_PREC_FP64_NATIVE = 2 } wf_precision;
 
 typedef struct wf_plan_s *wf_plan_t;
 typedef struct wf_server_s *wf_server_t;

@@ -177,8 +177,13 @@ static wf_status build_legendre(Plan *P) {
   if ((st = P->dalloc((void **)&P->d_rec, sizeof(double2) * rec.size()))) return st;
   if ((st = P->dalloc((void **)&P->d_ls, sizeof(int) * nmk))) return st;
   if ((st = P->dalloc((void **)&P->d_sv, sizeof(double2) * nmk))) return st;
+  if ((st = P->dalloc((void **)&P->d_dfA, sizeof(float2) * rec.size()))) return st;
+  if ((st = P->dalloc((void **)&P->d_dfg, sizeof(double) * rec.size()))) return st;
+  if ((st = P->dalloc((void **)&P->d_dfls, sizeof(int) * nmk))) return st;
+  if ((st = P->dalloc((void **)&P->d_dfsv, sizeof(float4) * nmk))) return st;
   WF_CUDA(cudaMemcpyAsync(P->d_rec, rec.data(), sizeof(double2) * rec.size(), cudaMemcpyHostToDevice, P->stream));
   launch_start_values(P->d_x, P->d_rec, lmax, P->RP, P->d_ls, P->d_sv, P->stream);
+  launch_df_tables(P->d_x, P->d_rec, lmax, P->RP, P->d_dfg, P->d_dfA, P->d_dfls, P->d_dfsv, P->stream);
   WF_CUDA(cudaStreamSynchronize(P->stream));
   WF_CUDA(cudaGetLastError());
   return WF_OK;
@@ -238,7 +243,7 @@ LegArgs Plan::leg_args() const {
 
 void Plan::enqueue_iteration(cudaStream_t s) {
   launch_ring(ring_args(), R, maxM, s, RING_ITER);
-  launch_legendre(leg_args(), s, LEG_ITER);
+  launch_leg(leg_args(), s, LEG_ITER);
   launch_control(d_ctl, d_ring_part, R, d_m_part, lmax, d_cl, d_hist, hist_cap, s);
 }
 
@@ -301,7 +306,11 @@ wf_status wf_options_default(wf_options *o) {
 }
 
 static wf_status check_options(const wf_options *o) {
-  if (o->precision != WF_PREC_FP64 && o->precision != WF_PREC_MIXED) { set_error("precision"); return WF_EINVAL; }
+  if (o->precision != WF_PREC_FP64 && o->precision != WF_PREC_FP64_NATIVE) {
+    set_error(o->precision == WF_PREC_MIXED ? "wf_options: the mixed-precision path is not available in this build"
+                                            : "wf_options: unknown precision");
+    return WF_EINVAL;
+  }
   if (!(o->tol >= 0.0) || o->max_iter < 1 || o->l_iter0 < 1 || o->lmax_margin < 0 || o->min_level_iters < 1 ||
       o->max_level_iters < 1 || o->graph_iters < 1 || o->graph_iters > 1024 || !(o->plateau_eps >= 0.0) ||
       !(o->final_dchi2 >= 0.0)) {
@@ -416,7 +425,7 @@ wf_status wf_alm2map(wf_plan_t plan, int lsht, const double *alm_dev, double *ma
   LegArgs la = P->leg_args();
   la.lsht = lsht;
   la.alm_in = reinterpret_cast<const double2 *>(alm_dev);
-  launch_legendre(la, s, LEG_SYNTH);
+  P->launch_leg(la, s,LEG_SYNTH);
   RingArgs ra = P->ring_args();
   ra.lsht = lsht;
   ra.map_out = map_dev;
@@ -438,7 +447,7 @@ wf_status wf_map2alm(wf_plan_t plan, int lsht, const double *map_dev, double *al
   LegArgs la = P->leg_args();
   la.lsht = lsht;
   la.alm = reinterpret_cast<double2 *>(alm_dev);
-  launch_legendre(la, s, LEG_ANALYSIS);
+  P->launch_leg(la, s,LEG_ANALYSIS);
   P->fs_valid = false;
   WF_CUDA(cudaGetLastError());
   return WF_OK;
@@ -462,7 +471,7 @@ wf_status wf_iterate(wf_plan_t plan, const double *d_dev, double *s_dev, double 
     LegArgs la = P->leg_args();
     la.lsht = lsht;
     la.alm_in = P->d_s;
-    launch_legendre(la, s, LEG_SYNTH);
+    P->launch_leg(la, s,LEG_SYNTH);
   }
   Ctl c = P->make_ctl(0, lambda, lsht, niter);
   *P->h_ctl = c;
@@ -496,7 +505,7 @@ wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_d
   LegArgs la = P->leg_args();
   la.lsht = lsht;
   la.alm_in = P->d_s;
-  launch_legendre(la, s, LEG_SYNTH);
+  P->launch_leg(la, s,LEG_SYNTH);
   Ctl c = P->make_ctl(0, lambda, lsht, niter);
   *P->h_ctl = c;
   WF_CUDA(cudaMemcpyAsync(P->d_ctl, P->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -506,7 +515,7 @@ wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_d
     cudaEventRecord(ev[4 * i], s);
     launch_ring(P->ring_args(), P->R, P->maxM, s, RING_ITER);
     cudaEventRecord(ev[4 * i + 1], s);
-    launch_legendre(P->leg_args(), s, LEG_ITER);
+    P->launch_leg(P->leg_args(), s, LEG_ITER);
     cudaEventRecord(ev[4 * i + 2], s);
     launch_control(P->d_ctl, P->d_ring_part, P->R, P->d_m_part, P->lmax, P->d_cl, P->d_hist, P->hist_cap, s);
     cudaEventRecord(ev[4 * i + 3], s);
@@ -543,7 +552,7 @@ static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *a
     LegArgs la = P->leg_args();
     la.lsht = lsht0;
     la.alm_in = P->d_s;
-    launch_legendre(la, s, LEG_SYNTH);
+    P->launch_leg(la, s,LEG_SYNTH);
   } else {
     WF_CUDA(cudaMemsetAsync(P->d_s, 0, sizeof(double2) * P->nalm, s));
     WF_CUDA(cudaMemsetAsync(P->d_FS, 0, sizeof(double4_32a) * (size_t)(P->lmax + 1) * P->RP, s));

@@ -1,0 +1,454 @@
+// Legendre stage in double-float arithmetic: FP64-accurate results from the
+// FP32 pipe.
+//
+// GB300 runs FP64 FMAs at 1/63 of the FP32 rate, and the FP64 Legendre kernel
+// (legendre.cu) is bound by that pipe. Here every value of the inner loops is
+// an unevaluated sum of two floats (hi + lo, 48 significant bits) and every
+// operation is built from error-free transformations:
+//   two_prod(a, b)  p = a b, e = fma(a, b, -p)           (exact)
+//   two_sum(a, b)   s = a + b, e = (a - (s - bb)) + (b - bb), bb = s - a  (exact)
+// Sums over rings and over l use the compensated dot product of Ogita, Rump
+// and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005):
+// the running sum in a float S with its exact rounding errors collected in a
+// float C, which is as accurate as a dot product in twice the working
+// precision.
+//
+// The recurrence is rescaled so that it needs one double-float product and one
+// double-float subtraction per step: with lambda_l = g_l mu_l, g_m = g_{m+1} = 1,
+// g_l = b_l g_{l-2},
+//     mu_l = A_l x mu_{l-1} - mu_{l-2},   A_l = a_l g_{l-1} / g_l,
+// (g_l stays within [2^-2.6, 2^0.2] for lmax <= 4096, so mu has lambda's range).
+// The factor g_l is applied in double after the cross-ring reduction (analysis)
+// and folded into the harmonic coefficients before synthesis.
+//
+// Terms with |lambda_lm(x)| < 2^-60 (the evanescent region near the poles) are
+// not evaluated; they lie below the 48-bit precision of any sum they enter.
+#include <cuda_runtime.h>
+
+#include "wf_internal.h"
+
+namespace wfk {
+
+constexpr int kNoStartD = 1 << 30;
+
+struct dfl { float h, l; };
+
+__device__ __forceinline__ dfl df_from(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+// S + C += a * b (compensated; a, b double-float)
+__device__ __forceinline__ void dot2_acc(float &S, float &C, dfl a, dfl b) {
+  const float ph = a.h * b.h;
+  const float pe = fmaf(a.h, b.h, -ph);
+  const float pc = fmaf(a.h, b.l, a.l * b.h);
+  const float s = S + ph;
+  const float bb = s - S;
+  const float e = (S - (s - bb)) + (ph - bb);
+  S = s;
+  C += e + (pe + pc);
+}
+
+// mu_l = (A x) mu1 - mu2, all double-float
+__device__ __forceinline__ dfl df_step(dfl A, dfl x, dfl mu1, dfl mu2) {
+  const float ch = A.h * x.h;
+  float ce = fmaf(A.h, x.h, -ch);
+  ce = fmaf(A.h, x.l, fmaf(A.l, x.h, ce));
+  const float qh = ch * mu1.h;
+  float qe = fmaf(ch, mu1.h, -qh);
+  qe = fmaf(ch, mu1.l, fmaf(ce, mu1.h, qe));
+  const float sh = qh - mu2.h;
+  const float bb = sh - qh;
+  float e = (qh - (sh - bb)) + (-mu2.h - bb);
+  e += qe - mu2.l;
+  const float rh = sh + e;
+  return {rh, e - (rh - sh)};
+}
+
+__device__ __forceinline__ size_t alm_idx_d(int lmax, int l, int m) {
+  return (size_t)m * (2 * lmax + 1 - m) / 2 + l;
+}
+
+// Lane q ends with the double-float sum over the warp's lanes of (S[q], C[q]).
+__device__ __forceinline__ double warp_transpose_sum_df(float (&S)[32], float (&C)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < off; ++j) {
+      const float sS = up ? S[j] : S[j + off], sC = up ? C[j] : C[j + off];
+      const float kS = up ? S[j + off] : S[j], kC = up ? C[j + off] : C[j];
+      const float rS = __shfl_xor_sync(0xffffffffu, sS, off);
+      const float rC = __shfl_xor_sync(0xffffffffu, sC, off);
+      const float s = kS + rS;
+      const float bb = s - kS;
+      const float e = (kS - (s - bb)) + (rS - bb);
+      S[j] = s;
+      C[j] = kC + rC + e;
+    }
+  }
+  return (double)S[0] + (double)C[0];
+}
+
+// 16 recurrence steps of one ring pair from l0, accumulating mu * (E or O)
+// into the 32 compensated sums; INJECT places the table start values.
+template <bool INJECT>
+__device__ __forceinline__ void analysis_block(int l0, int m, const float2 *sA, dfl x, dfl &p1, dfl &p2, int ls,
+                                               dfl v0, dfl v1, dfl Er, dfl Ei, dfl Or, dfl Oi, float (&S)[32],
+                                               float (&C)[32]) {
+#pragma unroll
+  for (int j = 0; j < kLB; ++j) {
+    const int l = l0 + j;
+    const float2 a2 = sA[l - m];
+    dfl mu = df_step(dfl{a2.x, a2.y}, x, p1, p2);
+    if (INJECT) {
+      if (l == ls) mu = v0;
+      if (l == ls + 1) mu = v1;
+    }
+    p2 = p1;
+    p1 = mu;
+    dot2_acc(S[2 * j], C[2 * j], mu, (j & 1) ? Or : Er);
+    dot2_acc(S[2 * j + 1], C[2 * j + 1], mu, (j & 1) ? Oi : Ei);
+  }
+}
+
+// Start values for the double-float recurrence: first l with |lambda| >= 2^-60,
+// and mu at that l and the next (mu = lambda / g), one thread per (m, k).
+__global__ void start_values_df_kernel(const double *xk, const double2 *rec, const double *g, int lmax, int RP,
+                                       int *ls_out, float4 *sv_out) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)(lmax + 1) * RP) return;
+  const int m = (int)(id / RP), k = (int)(id % RP);
+  const double x = xk[k];
+  const double st = sqrt((1.0 - x) * (1.0 + x));
+  int ls = kNoStartD;
+  double v0 = 0.0, v1 = 0.0;
+  if (m == 0 || st > 0.0) {
+    double v = 0.28209479177387814347;  // 1 / sqrt(4 pi)
+    int e = 0;
+    for (int i = 1; i <= m; ++i) {
+      v *= -sqrt((2.0 * i + 1.0) / (2.0 * i)) * st;
+      if (fabs(v) < 0x1p-400) { v *= 0x1p400; e -= 400; }
+    }
+    double p2 = v, p1 = x * sqrt(2.0 * m + 3.0) * v;
+    for (int l = m; l <= lmax; ++l) {
+      if (p2 != 0.0 && ilogb(p2) + e >= -60) {
+        ls = l;
+        v0 = ldexp(p2, e);
+        v1 = (l + 1 <= lmax) ? ldexp(p1, e) : 0.0;
+        break;
+      }
+      if (l + 2 <= lmax) {
+        const double2 ab = rec[alm_idx_d(lmax, l + 2, m)];
+        const double nx = ab.x * x * p1 - ab.y * p2;
+        p2 = p1;
+        p1 = nx;
+        if (fabs(p2) > 0x1p400 || fabs(p1) > 0x1p400) { p1 *= 0x1p-400; p2 *= 0x1p-400; e += 400; }
+      } else {
+        p2 = p1;
+        p1 = 0.0;
+      }
+    }
+  }
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (ls != kNoStartD) {
+    const size_t base = alm_idx_d(lmax, m, m);
+    const dfl a = df_from(v0 / g[base + (ls - m)]);
+    const dfl b = (ls + 1 <= lmax) ? df_from(v1 / g[base + (ls + 1 - m)]) : dfl{0.f, 0.f};
+    out = make_float4(a.h, a.l, b.h, b.l);
+  }
+  ls_out[id] = ls;
+  sv_out[id] = out;
+}
+
+// g_l and A_l of the rescaled recurrence, one CTA per m (serial in l).
+__global__ void rescale_coeffs_kernel(const double2 *rec, int lmax, double *g, float2 *A) {
+  const int m = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  const size_t base = alm_idx_d(lmax, m, m);
+  double g2 = 1.0, g1 = 1.0;  // g_{l-2}, g_{l-1}
+  for (int l = m; l <= lmax; ++l) {
+    const double2 ab = rec[base + (l - m)];
+    double gl, Al;
+    if (l <= m + 1) {
+      gl = 1.0;
+      Al = ab.x;  // a_{m+1} (a_m = 0)
+    } else {
+      gl = ab.y * g2;
+      Al = ab.x * g1 / gl;
+    }
+    g[base + (l - m)] = gl;
+    const dfl d = df_from(Al);
+    A[base + (l - m)] = make_float2(d.h, d.l);
+    g2 = g1;
+    g1 = gl;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs A, const LegDfArgs D) {
+  extern __shared__ double2 dsm[];
+  __shared__ double red[kThreads / 32][32];
+  __shared__ double mred[kThreads / 32][3];
+  const int m = blockIdx.x;
+  const int lmax = A.lmax, RP = A.RP;
+  int L = A.lsht;
+  double lam = 1.0;
+  if (MODE == LEG_ITER) {
+    if (A.ctl->done) return;
+    L = A.ctl->lsht;
+    lam = A.ctl->lambda;
+  }
+  const size_t base = alm_idx_d(lmax, m, m);
+  if (m > L) {
+    if (MODE == LEG_ITER || MODE == LEG_ANALYSIS) {
+      double c2 = 0.0, inc = 0.0;
+      for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+        const double2 so = A.alm[base + (l - m)];
+        const double wgt = (m == 0) ? 1.0 : 2.0;
+        const double a2 = so.x * so.x + so.y * so.y;
+        if (MODE == LEG_ITER) {
+          if (A.cl[l] > 0.0) c2 += wgt * a2 / A.cl[l];
+          inc += wgt * a2;
+        }
+        A.alm[base + (l - m)] = make_double2(0.0, 0.0);
+      }
+      if (MODE == LEG_ITER) {
+        for (int o = 16; o > 0; o >>= 1) {
+          c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+          inc += __shfl_xor_sync(0xffffffffu, inc, o);
+        }
+        if ((threadIdx.x & 31) == 0) { mred[threadIdx.x >> 5][0] = c2; mred[threadIdx.x >> 5][1] = inc; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double a = 0.0, b = 0.0;
+          for (int w = 0; w < kThreads / 32; ++w) { a += mred[w][0]; b += mred[w][1]; }
+          A.m_part[3 * m] = a;
+          A.m_part[3 * m + 1] = b;
+          A.m_part[3 * m + 2] = 0.0;
+        }
+      }
+    }
+    if (MODE == LEG_ITER || MODE == LEG_SYNTH) {
+      for (int k = threadIdx.x; k < RP; k += blockDim.x)
+        A.FS[(size_t)m * RP + k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    }
+    return;
+  }
+  const int Lm = L - m + 1;
+  const int Lp = Lm + kLB;
+  // shared: tl [Lp] double2 | sA [Lp] float2 | ss [Lp] float4 (synthesis coefficients g_l s_lm)
+  double2 *tl = dsm;
+  float2 *sA = reinterpret_cast<float2 *>(dsm + Lp);
+  float4 *ss = reinterpret_cast<float4 *>(sA + Lp + (Lp & 1));
+  for (int i = threadIdx.x; i < Lp; i += blockDim.x) {
+    sA[i] = (i < Lm) ? D.A[base + i] : make_float2(0.f, 0.f);
+    tl[i] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (MODE == LEG_ANALYSIS || MODE == LEG_ITER) {
+    // per ring pair state in shared memory: the thread's sums then cover all of
+    // its ring pairs before one reduction per block of kLB values of l
+    float4 *stE = ss;                            // (Er, Ei) as hi/lo
+    float4 *stO = stE + RP;                      // (Or, Oi)
+    float4 *stP = stO + RP;                      // (p1, p2)
+    for (int k = threadIdx.x; k < RP; k += blockDim.x) {
+      const double4_32a t = A.FT[(size_t)m * RP + k];
+      const dfl er = df_from(t.x + t.z), ei = df_from(t.y + t.w);
+      const dfl orr = df_from(t.x - t.z), oi = df_from(t.y - t.w);
+      stE[k] = make_float4(er.h, er.l, ei.h, ei.l);
+      stO[k] = make_float4(orr.h, orr.l, oi.h, oi.l);
+      stP[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    for (int l0 = m; l0 <= L; l0 += kLB) {
+      float S[32], C[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) { S[j] = 0.f; C[j] = 0.f; }
+      for (int k = threadIdx.x; k < RP; k += blockDim.x) {
+        const size_t mk = (size_t)m * RP + k;
+        const int ls = D.ls[mk];
+        if (ls >= l0 + kLB) continue;            // no evaluated term yet in this block
+        const dfl x = df_from(A.x[k]);
+        const float4 e4 = stE[k], o4 = stO[k], q4 = stP[k];
+        dfl p1 = dfl{q4.x, q4.y}, p2 = dfl{q4.z, q4.w};
+        if (ls + 1 >= l0) {                      // a start value falls in this block
+          const float4 s4 = D.sv[mk];
+          analysis_block<true>(l0, m, sA, x, p1, p2, ls, dfl{s4.x, s4.y}, dfl{s4.z, s4.w}, dfl{e4.x, e4.y},
+                               dfl{e4.z, e4.w}, dfl{o4.x, o4.y}, dfl{o4.z, o4.w}, S, C);
+        } else {
+          analysis_block<false>(l0, m, sA, x, p1, p2, ls, dfl{0.f, 0.f}, dfl{0.f, 0.f}, dfl{e4.x, e4.y},
+                                dfl{e4.z, e4.w}, dfl{o4.x, o4.y}, dfl{o4.z, o4.w}, S, C);
+        }
+        stP[k] = make_float4(p1.h, p1.l, p2.h, p2.l);
+      }
+      const double s = warp_transpose_sum_df(S, C);
+      red[warp][lane] = s;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
+        double *dst = reinterpret_cast<double *>(&tl[l0 - m + (threadIdx.x >> 1)]);
+        dst[threadIdx.x & 1] += t;
+      }
+      __syncthreads();
+    }
+    // undo the rescaling: lambda = g mu
+    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+      const double gl = D.g[base + (l - m)];
+      tl[l - m].x *= gl;
+      tl[l - m].y *= gl;
+    }
+    __syncthreads();
+  }
+
+  if (MODE == LEG_ANALYSIS) {
+    for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x)
+      A.alm[base + (l - m)] = (l <= L) ? tl[l - m] : make_double2(0.0, 0.0);
+    return;
+  }
+
+  if (MODE == LEG_ITER) {
+    double c2 = 0.0, inc = 0.0, nrm = 0.0;
+    const double wgt = (m == 0) ? 1.0 : 2.0;
+    const double lto = lam * A.tau * A.omega;
+    for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+      const double2 so = A.alm[base + (l - m)];
+      const double c = A.cl[l];
+      double2 sn = make_double2(0.0, 0.0);
+      if (l <= L && c > 0.0) {
+        const double f = c / (c + lto);
+        const double2 t = tl[l - m];
+        sn = make_double2(f * (so.x + t.x), f * (so.y + t.y));
+      }
+      if (c > 0.0) c2 += wgt * (so.x * so.x + so.y * so.y) / c;
+      const double dx = sn.x - so.x, dy = sn.y - so.y;
+      inc += wgt * (dx * dx + dy * dy);
+      nrm += wgt * (sn.x * sn.x + sn.y * sn.y);
+      A.alm[base + (l - m)] = sn;
+      if (l <= L) {
+        const double gl = D.g[base + (l - m)];
+        const dfl re = df_from(gl * sn.x), im = df_from(gl * sn.y);
+        ss[l - m] = make_float4(re.h, re.l, im.h, im.l);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+      inc += __shfl_xor_sync(0xffffffffu, inc, o);
+      nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    }
+    if (lane == 0) { mred[warp][0] = c2; mred[warp][1] = inc; mred[warp][2] = nrm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0, c = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) { a += mred[w][0]; b += mred[w][1]; c += mred[w][2]; }
+      A.m_part[3 * m] = a;
+      A.m_part[3 * m + 1] = b;
+      A.m_part[3 * m + 2] = c;
+    }
+  } else {  // LEG_SYNTH
+    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+      const double gl = D.g[base + (l - m)];
+      const double2 s = A.alm_in[base + (l - m)];
+      const dfl re = df_from(gl * s.x), im = df_from(gl * s.y);
+      ss[l - m] = make_float4(re.h, re.l, im.h, im.l);
+    }
+    __syncthreads();
+  }
+
+  // ---- synthesis onto every ring pair (one ring pair per thread at a time)
+  for (int k = threadIdx.x; k < RP; k += blockDim.x) {
+    const size_t mk = (size_t)m * RP + k;
+    const int ls = D.ls[mk];
+    float ERs = 0.f, ERc = 0.f, EIs = 0.f, EIc = 0.f, ORs = 0.f, ORc = 0.f, OIs = 0.f, OIc = 0.f;
+    if (ls <= L) {
+      const dfl x = df_from(A.x[k]);
+      const float4 s4 = D.sv[mk];
+      dfl p2 = dfl{s4.x, s4.y};
+      dfl p1 = dfl{s4.z, s4.w};
+      int l = ls;
+      {
+        const float4 c = ss[l - m];
+        if (((l - m) & 1) == 0) { dot2_acc(ERs, ERc, p2, dfl{c.x, c.y}); dot2_acc(EIs, EIc, p2, dfl{c.z, c.w}); }
+        else { dot2_acc(ORs, ORc, p2, dfl{c.x, c.y}); dot2_acc(OIs, OIc, p2, dfl{c.z, c.w}); }
+      }
+      if (l + 1 <= L) {
+        const float4 c = ss[l + 1 - m];
+        if (((l + 1 - m) & 1) == 0) { dot2_acc(ERs, ERc, p1, dfl{c.x, c.y}); dot2_acc(EIs, EIc, p1, dfl{c.z, c.w}); }
+        else { dot2_acc(ORs, ORc, p1, dfl{c.x, c.y}); dot2_acc(OIs, OIc, p1, dfl{c.z, c.w}); }
+      }
+      l += 2;
+      if (((l - m) & 1) == 1 && l <= L) {
+        const float2 a2 = sA[l - m];
+        const dfl mu = df_step(dfl{a2.x, a2.y}, x, p1, p2);
+        p2 = p1; p1 = mu;
+        const float4 c = ss[l - m];
+        dot2_acc(ORs, ORc, mu, dfl{c.x, c.y});
+        dot2_acc(OIs, OIc, mu, dfl{c.z, c.w});
+        ++l;
+      }
+      for (; l + 1 <= L; l += 2) {
+        const float2 a0 = sA[l - m], a1 = sA[l + 1 - m];
+        const dfl me = df_step(dfl{a0.x, a0.y}, x, p1, p2);
+        const dfl mo = df_step(dfl{a1.x, a1.y}, x, me, p1);
+        p2 = me; p1 = mo;
+        const float4 ce = ss[l - m], co = ss[l + 1 - m];
+        dot2_acc(ERs, ERc, me, dfl{ce.x, ce.y});
+        dot2_acc(EIs, EIc, me, dfl{ce.z, ce.w});
+        dot2_acc(ORs, ORc, mo, dfl{co.x, co.y});
+        dot2_acc(OIs, OIc, mo, dfl{co.z, co.w});
+      }
+      if (l <= L) {
+        const float2 a0 = sA[l - m];
+        const dfl me = df_step(dfl{a0.x, a0.y}, x, p1, p2);
+        const float4 ce = ss[l - m];
+        dot2_acc(ERs, ERc, me, dfl{ce.x, ce.y});
+        dot2_acc(EIs, EIc, me, dfl{ce.z, ce.w});
+      }
+    }
+    const double er = (double)ERs + (double)ERc, ei = (double)EIs + (double)EIc;
+    const double orr = (double)ORs + (double)ORc, oi = (double)OIs + (double)OIc;
+    A.FS[mk] = make_double4_32a(er + orr, ei + oi, er - orr, ei - oi);
+  }
+}
+
+// tl [Lp] double2 | sA [Lp (+1)] float2 | max(Lp, 3 RP) float4 (synthesis
+// coefficients, or the per-ring-pair analysis state)
+static size_t leg_df_smem(int lmax, int RP) {
+  const size_t Lp = (size_t)lmax + 1 + kLB;
+  const size_t q = Lp > 3 * (size_t)RP ? Lp : 3 * (size_t)RP;
+  return Lp * sizeof(double2) + (Lp + 1) * sizeof(float2) + q * sizeof(float4) + 16;
+}
+
+void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode) {
+  const size_t sm = leg_df_smem(a.lmax, a.RP);
+  const int grid = a.lmax + 1;
+  switch (mode) {
+    case LEG_SYNTH:
+      cudaFuncSetAttribute(legendre_df_kernel<LEG_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      legendre_df_kernel<LEG_SYNTH><<<grid, kThreads, sm, s>>>(a, d);
+      break;
+    case LEG_ANALYSIS:
+      cudaFuncSetAttribute(legendre_df_kernel<LEG_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      legendre_df_kernel<LEG_ANALYSIS><<<grid, kThreads, sm, s>>>(a, d);
+      break;
+    default:
+      cudaFuncSetAttribute(legendre_df_kernel<LEG_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      legendre_df_kernel<LEG_ITER><<<grid, kThreads, sm, s>>>(a, d);
+      break;
+  }
+}
+
+void launch_df_tables(const double *x, const double2 *rec, int lmax, int RP, double *g, float2 *A, int *ls,
+                      float4 *sv, cudaStream_t s) {
+  rescale_coeffs_kernel<<<lmax + 1, 32, 0, s>>>(rec, lmax, g, A);
+  const long long n = (long long)(lmax + 1) * RP;
+  start_values_df_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(x, rec, g, lmax, RP, ls, sv);
+}
+
+}  // namespace wfk

@@ -98,8 +98,19 @@ struct LegArgs {
   double omega, tau;
 };
 
+// Tables of the double-float Legendre kernel (legendre_df.cu).
+struct LegDfArgs {
+  const float2 *A;        // [nalm] rescaled recurrence coefficient A_l (hi, lo)
+  const double *g;        // [nalm] rescaling factor g_l (lambda = g mu)
+  const int *ls;          // [(lmax+1) RP] first evaluated l (|lambda| >= 2^-60)
+  const float4 *sv;       // [(lmax+1) RP] mu_{ls} (hi, lo), mu_{ls+1} (hi, lo)
+};
+
 void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode);
 void launch_legendre(const LegArgs &a, cudaStream_t s, int mode);
+void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode);
+void launch_df_tables(const double *x, const double2 *rec, int lmax, int RP, double *g, float2 *A, int *ls,
+                      float4 *sv, cudaStream_t s);
 void launch_start_values(const double *x, const double2 *rec, int lmax, int RP, int *ls,
                          double2 *sv, cudaStream_t s);
 void launch_bluestein_setup(const RingDev *rings, int R, const double2 *tw, int logMmax,

@@ -32,6 +32,11 @@ struct Plan : wf_plan_s {
   double2 *d_rec = nullptr, *d_sv = nullptr;
   int *d_ls = nullptr;
   double *d_cl = nullptr, *d_w = nullptr;
+  // double-float Legendre tables
+  float2 *d_dfA = nullptr;
+  double *d_dfg = nullptr;
+  int *d_dfls = nullptr;
+  float4 *d_dfsv = nullptr;
   // working state
   double4_32a *d_FS = nullptr, *d_FT = nullptr;
   double *d_ring_part = nullptr, *d_m_part = nullptr;
@@ -53,6 +58,12 @@ struct Plan : wf_plan_s {
   cudaStream_t run_stream() const;
   RingArgs ring_args() const;
   LegArgs leg_args() const;
+  LegDfArgs legdf_args() const { return LegDfArgs{d_dfA, d_dfg, d_dfls, d_dfsv}; }
+  // the Legendre stage of the plan's precision
+  void launch_leg(const LegArgs &a, cudaStream_t s, int mode) const {
+    if (opt.precision == WF_PREC_FP64_NATIVE) launch_legendre(a, s, mode);
+    else launch_legendre_df(a, legdf_args(), s, mode);
+  }
   void enqueue_iteration(cudaStream_t s);
   Ctl make_ctl(int mode, double lambda, int lsht, int n_fixed) const;
   double lambda_of(int l_iter) const;

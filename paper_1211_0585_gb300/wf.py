@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libwf.so")
 
 WF_OK, WF_EINVAL, WF_ENOMEM, WF_ECUDA, WF_ENOTCONVERGED, WF_ENUMERIC, WF_ETIMEOUT, WF_EBUSY, \
     WF_ECANCELLED, WF_ENOTFOUND = range(10)
-WF_PREC_FP64, WF_PREC_MIXED = 0, 1
+WF_PREC_FP64, WF_PREC_MIXED, WF_PREC_FP64_NATIVE = 0, 1, 2
 STATUS_NAMES = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "WF_ENOTCONVERGED",
                 5: "WF_ENUMERIC", 6: "WF_ETIMEOUT", 7: "WF_EBUSY", 8: "WF_ECANCELLED", 9: "WF_ENOTFOUND"}
 

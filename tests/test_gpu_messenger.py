@@ -25,6 +25,10 @@ def run_oracle_schedule(p, d, schedule):
     return res, states
 
 
+PRECS = [wf.WF_PREC_FP64, wf.WF_PREC_FP64_NATIVE]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("kind,nside,lmax,lam,lsht,n", [
     ("small", 16, 32, 1.0, 32, 4),
     ("small", 16, 32, 500.0, 20, 4),
@@ -32,11 +36,11 @@ def run_oracle_schedule(p, d, schedule):
     ("wmap", 32, 64, 1.0, 64, 3),
     ("wmap", 64, 128, 2.5, 100, 2),
 ])
-def test_iterates_match(kind, nside, lmax, lam, lsht, n):
+def test_iterates_match(kind, nside, lmax, lam, lsht, n, prec):
     import torch
     p, d = problem(kind, seed=2, nside=nside, lmax=lmax)
     res, states = run_oracle_schedule(p, d, [(lam, lsht, n)])
-    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask)
+    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(precision=prec))
     dd = dev(d)
     s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
     for k in range(n):
@@ -49,12 +53,13 @@ def test_iterates_match(kind, nside, lmax, lam, lsht, n):
         assert math.sqrt(recs[0]["incr2"] / recs[0]["norm2"]) == pytest.approx(h["rel_incr"], rel=1e-8)
 
 
-def test_config1_two_hundred_iterations():
+@pytest.mark.parametrize("prec", PRECS)
+def test_config1_two_hundred_iterations(prec):
     """Nside 16, lmax 32, C_l = 1/(l(l+1)), 200 plain iterations at lambda = 1."""
     import torch
     p, d = problem("small", seed=1)
     res, _ = run_oracle_schedule(p, d, [(1.0, 32, 200)])
-    P = wf.Plan(16, 32, p.cl, p.noise_var, p.mask)
+    P = wf.Plan(16, 32, p.cl, p.noise_var, p.mask, wf.options(precision=prec))
     s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
     recs = P.iterate(dev(d).data_ptr(), s.data_ptr(), 1.0, 32, 200, reset=True)
     assert O.rel_l2(host_alm(s), res.alm, 32) < TOL
@@ -69,6 +74,7 @@ def test_config1_two_hundred_iterations():
     ("wmap", 64, 128, dict(tol=1e-6, max_iter=2000, l_iter0=8, lmax_margin=20)),
 ])
 def test_cooled_solve_matches(kind, nside, lmax, opts):
+    """Default precision (double-float Legendre stage)."""
     """The device-resident controller takes the oracle's decisions: same
     lambda levels, band limits and iteration count, same result."""
     p, d = problem(kind, seed=5, nside=nside, lmax=lmax)
@@ -98,7 +104,8 @@ def test_solve_on_device_buffers_and_warm_start():
     assert O.rel_l2(alm_w, alm_h, 32) < 1e-8
 
 
-def test_full_size_first_iteration_nside512():
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_first_iteration_nside512(prec):
     """WMAP-shaped Nside 512 / lmax 1024 at the bench's launch shapes: the
     first iteration from s = 0 is s_lm = f_l (Y^dagger a d)_lm; sampled
     modes are checked against the oracle one by one."""
@@ -108,7 +115,7 @@ def test_full_size_first_iteration_nside512():
     p = I.wmap_problem(seed=1, nside=nside, lmax=lmax)
     rng = np.random.default_rng(7)
     d = rng.standard_normal(p.npix) * np.sqrt(p.noise_var) + 50.0 * np.cos(3 * np.arange(p.npix) / p.npix)
-    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask)
+    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(precision=prec))
     lam = 4.0
     s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
     recs = P.iterate(dev(d).data_ptr(), s.data_ptr(), lam, lmax, 1, reset=True)

@@ -14,17 +14,21 @@ pytestmark = pytest.mark.gpu
 CASES = [(1, 2), (2, 6), (4, 8), (4, 13), (8, 16), (16, 32), (16, 64), (32, 64), (64, 128), (64, 40)]
 
 
-def plan_for(nside, lmax):
-    return wf.Plan(nside, lmax, np.ones(lmax + 1), np.ones(12 * nside * nside))
+PRECS = [wf.WF_PREC_FP64, wf.WF_PREC_FP64_NATIVE]
 
 
+def plan_for(nside, lmax, prec=wf.WF_PREC_FP64):
+    return wf.Plan(nside, lmax, np.ones(lmax + 1), np.ones(12 * nside * nside), opts=wf.options(precision=prec))
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("nside,lmax", CASES)
-def test_alm2map(nside, lmax):
+def test_alm2map(nside, lmax, prec):
     import torch
     rng = np.random.default_rng(nside * 1000 + lmax)
     alm = I.draw_alm(np.ones(lmax + 1), rng)
     ref = O.alm2map(nside, lmax, alm)
-    P = plan_for(nside, lmax)
+    P = plan_for(nside, lmax, prec)
     a = dev(alm)
     m = torch.empty(12 * nside * nside, dtype=torch.float64, device="cuda")
     P.alm2map(lmax, a.data_ptr(), m.data_ptr())
@@ -33,13 +37,14 @@ def test_alm2map(nside, lmax):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("nside,lmax", CASES)
-def test_map2alm(nside, lmax):
+def test_map2alm(nside, lmax, prec):
     import torch
     rng = np.random.default_rng(nside * 7 + lmax)
     f = rng.standard_normal(12 * nside * nside)
     ref = O.map2alm(nside, lmax, f)
-    P = plan_for(nside, lmax)
+    P = plan_for(nside, lmax, prec)
     a = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
     P.map2alm(lmax, dev(f).data_ptr(), a.data_ptr())
     torch.cuda.synchronize()
@@ -67,7 +72,8 @@ def test_band_limited(nside, lmax, lsht):
     assert np.max(np.abs(got - refa)) <= 1e-12 * np.max(np.abs(refa))
 
 
-def test_sampled_full_size_nside512():
+@pytest.mark.parametrize("prec", PRECS)
+def test_sampled_full_size_nside512(prec):
     """At the WMAP-shaped size (Nside 512, lmax 1024): sampled pixels of the
     synthesis and sampled modes of the analysis, each computed one by one by
     the oracle."""
@@ -76,7 +82,7 @@ def test_sampled_full_size_nside512():
     rng = np.random.default_rng(512)
     cl = I.cl_lcdm_like(lmax, 13.0)
     alm = I.draw_alm(cl, rng)
-    P = plan_for(nside, lmax)
+    P = plan_for(nside, lmax, prec)
     m = torch.empty(12 * nside * nside, dtype=torch.float64, device="cuda")
     P.alm2map(lmax, dev(alm).data_ptr(), m.data_ptr())
     f = rng.standard_normal(12 * nside * nside)
