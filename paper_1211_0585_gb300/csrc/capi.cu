@@ -150,6 +150,19 @@ static wf_status build_geometry(Plan *P) {
   WF_CUDA(cudaMemcpyAsync(P->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_x, xk.data(), sizeof(double) * P->RP, cudaMemcpyHostToDevice, s));
   if (B_tot > 0) launch_bluestein_setup(P->d_rings, R, P->d_tw, P->logMmax, P->d_chirp, P->d_B, maxM, s);
+  // double-float copies for the ring_df kernels
+  P->n_tw = (long long)tw.size();
+  P->n_hs = (long long)hs.size();
+  P->n_ch = (long long)ch.size();
+  P->n_B = B_tot > 0 ? B_tot : 1;
+  if ((st = P->dalloc((void **)&P->d_twf, sizeof(float4) * P->n_tw))) return st;
+  if ((st = P->dalloc((void **)&P->d_hsf, sizeof(float4) * P->n_hs))) return st;
+  if ((st = P->dalloc((void **)&P->d_chf, sizeof(float4) * P->n_ch))) return st;
+  if ((st = P->dalloc((void **)&P->d_Bf, sizeof(float4) * P->n_B))) return st;
+  launch_to_df(P->d_tw, P->d_twf, P->n_tw, s);
+  launch_to_df(P->d_hs, P->d_hsf, P->n_hs, s);
+  launch_to_df(P->d_chirp, P->d_chf, P->n_ch, s);
+  launch_to_df(P->d_B, P->d_Bf, P->n_B, s);
   WF_CUDA(cudaStreamSynchronize(s));
   WF_CUDA(cudaGetLastError());
   return WF_OK;
@@ -242,7 +255,7 @@ LegArgs Plan::leg_args() const {
 }
 
 void Plan::enqueue_iteration(cudaStream_t s) {
-  launch_ring(ring_args(), R, maxM, s, RING_ITER);
+  launch_rng(ring_args(), s, RING_ITER);
   launch_leg(leg_args(), s, LEG_ITER);
   launch_control(d_ctl, d_ring_part, R, d_m_part, lmax, d_cl, d_hist, hist_cap, s);
 }
@@ -429,7 +442,7 @@ wf_status wf_alm2map(wf_plan_t plan, int lsht, const double *alm_dev, double *ma
   RingArgs ra = P->ring_args();
   ra.lsht = lsht;
   ra.map_out = map_dev;
-  launch_ring(ra, P->R, P->maxM, s, RING_SYNTH);
+  P->launch_rng(ra, s, RING_SYNTH);
   P->fs_valid = false;
   WF_CUDA(cudaGetLastError());
   return WF_OK;
@@ -443,7 +456,7 @@ wf_status wf_map2alm(wf_plan_t plan, int lsht, const double *map_dev, double *al
   RingArgs ra = P->ring_args();
   ra.lsht = lsht;
   ra.map_in = map_dev;
-  launch_ring(ra, P->R, P->maxM, s, RING_ANALYSIS);
+  P->launch_rng(ra, s, RING_ANALYSIS);
   LegArgs la = P->leg_args();
   la.lsht = lsht;
   la.alm = reinterpret_cast<double2 *>(alm_dev);
@@ -513,7 +526,7 @@ wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_d
   for (auto &e : ev) WF_CUDA(cudaEventCreate(&e));
   for (int i = 0; i < niter; ++i) {
     cudaEventRecord(ev[4 * i], s);
-    launch_ring(P->ring_args(), P->R, P->maxM, s, RING_ITER);
+    P->launch_rng(P->ring_args(), s, RING_ITER);
     cudaEventRecord(ev[4 * i + 1], s);
     P->launch_leg(P->leg_args(), s, LEG_ITER);
     cudaEventRecord(ev[4 * i + 2], s);

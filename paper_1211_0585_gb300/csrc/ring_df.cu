@@ -1,0 +1,271 @@
+// Ring stage in double-float arithmetic (FP64-accurate FFTs on the FP32 pipe).
+//
+// Same algorithm and data flow as ring.cu (fold F_m onto residues with the
+// half-pixel shift, inverse DFT, Eq. 3 per pixel with the chi^2 partials,
+// forward DFT, unfold), but every FFT value is a pair of floats per real
+// component and every butterfly is built from error-free transformations
+// (two_sum, two_prod), because GB300's FP64 pipe is 1/63 of its FP32 pipe.
+// The per-pixel Eq. 3 update and the chi^2 partials stay in double (one pass
+// over the ring's pixels). Tables (twiddles, half-shift, chirp, Bluestein
+// filter) are stored as double-float pairs, converted once from the double
+// tables when the plan is built.
+#include <cuda_runtime.h>
+
+#include "wf_internal.h"
+
+namespace wfk {
+
+namespace {
+
+struct dd { float h, l; };
+
+__device__ __forceinline__ dd mk(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double todbl(dd a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ dd dadd(dd a, dd b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  const float r = s + e;
+  return {r, e - (r - s)};
+}
+__device__ __forceinline__ dd dneg(dd a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dd dmul(dd a, dd b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  const float r = p + e;
+  return {r, e - (r - p)};
+}
+
+// complex double-float held as float4 (re.h, re.l, im.h, im.l)
+__device__ __forceinline__ float4 pack(dd re, dd im) { return make_float4(re.h, re.l, im.h, im.l); }
+__device__ __forceinline__ dd RE(float4 v) { return {v.x, v.y}; }
+__device__ __forceinline__ dd IM(float4 v) { return {v.z, v.w}; }
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) { return pack(dadd(RE(a), RE(b)), dadd(IM(a), IM(b))); }
+__device__ __forceinline__ float4 csub(float4 a, float4 b) {
+  return pack(dadd(RE(a), dneg(RE(b))), dadd(IM(a), dneg(IM(b))));
+}
+__device__ __forceinline__ float4 cmul(float4 a, float4 b) {
+  const dd re = dadd(dmul(RE(a), RE(b)), dneg(dmul(IM(a), IM(b))));
+  const dd im = dadd(dmul(RE(a), IM(b)), dmul(IM(a), RE(b)));
+  return pack(re, im);
+}
+__device__ __forceinline__ float4 cconj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 cneg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+
+__device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+
+__device__ void fft_dif(float4 *buf, int logM, int sign, const float4 *tw, int logMmax) {
+  const int M = 1 << logM;
+  for (int s = logM; s >= 1; --s) {
+    const int half = 1 << (s - 1);
+    const int tsh = logMmax - s;
+    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
+      const int pos = t & (half - 1);
+      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
+      float4 w = tw[pos << tsh];
+      if (sign > 0) w = cconj(w);
+      const float4 a = buf[i0], b = buf[i1];
+      buf[i0] = cadd(a, b);
+      buf[i1] = cmul(csub(a, b), w);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void fft_dit(float4 *buf, int logM, int sign, const float4 *tw, int logMmax) {
+  const int M = 1 << logM;
+  for (int s = 1; s <= logM; ++s) {
+    const int half = 1 << (s - 1);
+    const int tsh = logMmax - s;
+    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
+      const int pos = t & (half - 1);
+      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
+      float4 w = tw[pos << tsh];
+      if (sign > 0) w = cconj(w);
+      const float4 a = buf[i0], b = cmul(buf[i1], w);
+      buf[i0] = cadd(a, b);
+      buf[i1] = csub(a, b);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void bluestein_conv(float4 *buf, int logM, const float4 *Bf, const float4 *tw, int logMmax) {
+  const int M = 1 << logM;
+  fft_dif(buf, logM, -1, tw, logMmax);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) buf[i] = cmul(buf[i], Bf[i]);
+  __syncthreads();
+  fft_dit(buf, logM, +1, tw, logMmax);
+}
+
+__device__ void block_sum2(double &a, double &b, double *red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[2 * warp] = a; red[2 * warp + 1] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { sa += red[2 * w2]; sb += red[2 * w2 + 1]; }
+    a = sa; b = sb;
+  }
+}
+
+}  // namespace
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) ring_df_kernel(const RingArgs A, const RingDfArgs T) {
+  extern __shared__ float4 rsm[];
+  const int r = blockIdx.x;
+  const RingDev rg = A.rings[r];
+  const int n = rg.n;
+  const int M = 1 << rg.logM;
+  float4 *buf = rsm;                                        // [M]
+  double *ureal = reinterpret_cast<double *>(rsm + M);      // [n]
+  __shared__ double red[64];
+
+  int L = A.lsht;
+  double lam = 1.0;
+  if (MODE == RING_ITER) {
+    if (A.ctl->done) return;
+    L = A.ctl->lsht;
+    lam = A.ctl->lambda;
+  }
+  const float4 *hs = T.hs + rg.hs_off;
+  const float4 *ch = T.chirp + rg.ch_off;
+  const float4 *Bf = T.B + rg.B_off;
+  const int k = rg.pair;
+  const int slot = rg.side;
+
+  if (MODE == RING_SYNTH || MODE == RING_ITER) {
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      double ar = 0.0, ai = 0.0;  // folding is a handful of additions: done in double
+      int j = 0;
+      for (int m = q; m <= L; m += n, ++j) {
+        const double4_32a f4 = A.FS[(size_t)m * A.RP + k];
+        double fr = slot ? f4.z : f4.x, fi = slot ? f4.w : f4.y;
+        if (rg.shifted && (j & 1)) { fr = -fr; fi = -fi; }
+        ar += fr; ai += fi;
+      }
+      j = 1;
+      for (int m = (q == 0 ? n : n - q); m <= L; m += n, ++j) {
+        const double4_32a f4 = A.FS[(size_t)m * A.RP + k];
+        double fr = slot ? f4.z : f4.x, fi = slot ? -f4.w : -f4.y;
+        if (rg.shifted && (j & 1)) { fr = -fr; fi = -fi; }
+        ar += fr; ai += fi;
+      }
+      float4 acc = pack(mk(ar), mk(ai));
+      if (rg.shifted) acc = cmul(acc, hs[q]);
+      buf[q] = rg.blue ? cmul(cconj(acc), ch[q]) : acc;
+    }
+    if (rg.blue) {
+      for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (rg.blue) bluestein_conv(buf, rg.logM, Bf, T.tw, A.logMmax);
+    else fft_dif(buf, rg.logM, +1, T.tw, A.logMmax);
+    if (MODE == RING_SYNTH) {
+      for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const dd f = rg.blue ? RE(cmul(ch[p], buf[p])) : RE(buf[bitrev(p, rg.logM)]);
+        A.map_out[rg.off + p] = todbl(f);
+      }
+      return;
+    }
+    double c2n = 0.0, c2l = 0.0;
+    const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      const dd sdf = rg.blue ? RE(cmul(ch[p], buf[p])) : RE(buf[bitrev(p, rg.logM)]);
+      const double s = todbl(sdf);
+      const double w = A.w[rg.off + p];
+      const double res = A.d[rg.off + p] - s;
+      const double g = w / (1.0 + l1t * w);
+      c2n += w * res * res;
+      c2l += g * res * res;
+      ureal[p] = lt * g * res;
+    }
+    block_sum2(c2n, c2l, red);
+    if (threadIdx.x == 0) {
+      A.ring_part[2 * r] = c2n;
+      A.ring_part[2 * r + 1] = c2l;
+    }
+    __syncthreads();
+  } else {
+    for (int p = threadIdx.x; p < n; p += blockDim.x) ureal[p] = A.map_in[rg.off + p];
+    __syncthreads();
+  }
+
+  if (rg.blue) {
+    for (int p = threadIdx.x; p < M; p += blockDim.x) {
+      if (p < n) {
+        const dd u = mk(ureal[p]);
+        const float4 c = ch[p];
+        buf[p] = pack(dmul(u, RE(c)), dmul(u, IM(c)));
+      } else {
+        buf[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    bluestein_conv(buf, rg.logM, Bf, T.tw, A.logMmax);
+  } else {
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      const dd u = mk(ureal[p]);
+      buf[bitrev(p, rg.logM)] = make_float4(u.h, u.l, 0.f, 0.f);
+    }
+    __syncthreads();
+    fft_dit(buf, rg.logM, -1, T.tw, A.logMmax);
+  }
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    const int q = m % n, j = m / n;
+    float4 U = rg.blue ? cmul(ch[q], buf[q]) : buf[q];
+    if (rg.shifted) {
+      U = cmul(U, cconj(hs[q]));
+      if (j & 1) U = cneg(U);
+    }
+    double *dst = reinterpret_cast<double *>(A.FT + (size_t)m * A.RP + k) + 2 * slot;
+    dst[0] = A.omega * todbl(RE(U));
+    dst[1] = A.omega * todbl(IM(U));
+  }
+}
+
+// double -> double-float table conversion
+__global__ void to_df_kernel(const double2 *src, float4 *dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    dst[i] = pack(mk(v.x), mk(v.y));
+  }
+}
+
+void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  to_df_kernel<<<(int)blocks, 256, 0, s>>>(src, dst, n);
+}
+
+void launch_ring_df(const RingArgs &a, const RingDfArgs &t, int R, int maxM, cudaStream_t s, int mode) {
+  const size_t sm = (size_t)maxM * sizeof(float4) + (size_t)maxM * sizeof(double);
+  switch (mode) {
+    case RING_SYNTH:
+      cudaFuncSetAttribute(ring_df_kernel<RING_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      ring_df_kernel<RING_SYNTH><<<R, kThreads, sm, s>>>(a, t);
+      break;
+    case RING_ANALYSIS:
+      cudaFuncSetAttribute(ring_df_kernel<RING_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      ring_df_kernel<RING_ANALYSIS><<<R, kThreads, sm, s>>>(a, t);
+      break;
+    default:
+      cudaFuncSetAttribute(ring_df_kernel<RING_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      ring_df_kernel<RING_ITER><<<R, kThreads, sm, s>>>(a, t);
+      break;
+  }
+}
+
+}  // namespace wfk

@@ -106,7 +106,15 @@ struct LegDfArgs {
   const float4 *sv;       // [(lmax+1) RP] mu_{ls} (hi, lo), mu_{ls+1} (hi, lo)
 };
 
+// Double-float copies of the ring-stage tables (ring_df.cu): float4 =
+// (re hi, re lo, im hi, im lo).
+struct RingDfArgs {
+  const float4 *tw, *hs, *chirp, *B;
+};
+
 void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode);
+void launch_ring_df(const RingArgs &a, const RingDfArgs &t, int R, int maxM, cudaStream_t s, int mode);
+void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s);
 void launch_legendre(const LegArgs &a, cudaStream_t s, int mode);
 void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode);
 void launch_df_tables(const double *x, const double2 *rec, int lmax, int RP, double *g, float2 *A, int *ls,

@@ -32,6 +32,9 @@ struct Plan : wf_plan_s {
   double2 *d_rec = nullptr, *d_sv = nullptr;
   int *d_ls = nullptr;
   double *d_cl = nullptr, *d_w = nullptr;
+  // double-float ring tables
+  float4 *d_twf = nullptr, *d_hsf = nullptr, *d_chf = nullptr, *d_Bf = nullptr;
+  long long n_tw = 0, n_hs = 0, n_ch = 0, n_B = 0;
   // double-float Legendre tables
   float2 *d_dfA = nullptr;
   double *d_dfg = nullptr;
@@ -59,6 +62,12 @@ struct Plan : wf_plan_s {
   RingArgs ring_args() const;
   LegArgs leg_args() const;
   LegDfArgs legdf_args() const { return LegDfArgs{d_dfA, d_dfg, d_dfls, d_dfsv}; }
+  RingDfArgs ringdf_args() const { return RingDfArgs{d_twf, d_hsf, d_chf, d_Bf}; }
+  // the ring stage of the plan's precision
+  void launch_rng(const RingArgs &a, cudaStream_t s, int mode) const {
+    if (opt.precision == WF_PREC_FP64_NATIVE) launch_ring(a, R, maxM, s, mode);
+    else launch_ring_df(a, ringdf_args(), R, maxM, s, mode);
+  }
   // the Legendre stage of the plan's precision
   void launch_leg(const LegArgs &a, cudaStream_t s, int mode) const {
     if (opt.precision == WF_PREC_FP64_NATIVE) launch_legendre(a, s, mode);
