@@ -87,6 +87,7 @@ typedef struct {
   int min_level_iters;   /* iterations at a lambda level before a plateau can end it (3) */
   int max_level_iters;   /* a level ends after this many iterations regardless (1000) */
   int graph_iters;       /* iterations captured per CUDA graph launch (16) */
+  int batch_slots;       /* slots of the batched mixed-precision engine, 1 .. 64 (64) */
   void *stream;          /* cudaStream_t to run on; NULL = the plan's own stream */
 } wf_options;
 

@@ -1,15 +1,261 @@
-// Multiple right-hand sides sharing one plan (C_l, noise, mask).
+// Batched engine (host side) and the multi-right-hand-side entry point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "batch_engine.h"
 #include "wf_internal.h"
 #include "wf_plan.h"
+
+namespace wfk {
+
+#define ENG_CUDA(call)                                     \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_status(e_, #call);  \
+  } while (0)
+
+static size_t nalm_of(int lmax) { return (size_t)(lmax + 1) * (lmax + 2) / 2; }
+
+static void make_tiles(int lmax, int RP, std::vector<int2> &ana, std::vector<int2> &syn) {
+  ana.clear();
+  syn.clear();
+  for (int m = 0; m <= lmax; ++m)
+    for (int l0 = m; l0 <= lmax; l0 += 64) ana.push_back(make_int2(m, l0));
+  for (int m = 0; m <= lmax; ++m)
+    for (int k0 = 0; k0 < RP; k0 += 32) syn.push_back(make_int2(m, k0));
+}
+
+size_t Engine::bytes_needed(int nside, int lmax, int nslots) {
+  const size_t RP = 2 * (size_t)nside, R = 4 * (size_t)nside - 1, npix = 12 * (size_t)nside * nside;
+  const size_t nalm = nalm_of(lmax), nF = (size_t)(lmax + 1) * RP;
+  size_t ntiles = 0;
+  for (int m = 0; m <= lmax; ++m) ntiles += (size_t)(lmax - m) / 64 + 1;
+  return nalm * RP * sizeof(float) + 2 * nF * nslots * sizeof(float4) + nalm * nslots * sizeof(float2) +
+         2 * npix * nslots * sizeof(double) + nslots * (size_t)(lmax + 1) * sizeof(double) +
+         nslots * nalm * sizeof(double2) + nslots * R * 2 * sizeof(double) + nslots * ntiles * 3 * sizeof(double) +
+         (ntiles + nF / 32 + 64) * sizeof(int2) + nslots * (sizeof(Ctl) + sizeof(wf_iter_record) + 8);
+}
+
+wf_status Engine::dalloc(void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc (batched engine)");
+  allocs.push_back(*p);
+  device_bytes += bytes;
+  return WF_OK;
+}
+
+Engine::~Engine() {
+  if (stream) cudaStreamSynchronize(stream);
+  if (graph) cudaGraphExecDestroy(graph);
+  for (void *p : allocs) cudaFree(p);
+  if (h_ctl) cudaFreeHost(h_ctl);
+  if (h_active) cudaFreeHost(h_active);
+  if (h_last) cudaFreeHost(h_last);
+}
+
+BatchArgs Engine::args() const {
+  BatchArgs a{};
+  a.rings = geo->d_rings;
+  a.twf = geo->d_twf; a.hsf = geo->d_hsf; a.chf = geo->d_chf; a.Bf = geo->d_Bf;
+  a.logMmax = geo->logMmax;
+  a.lam = lam;
+  a.lmax = geo->lmax; a.RP = geo->RP; a.R = geo->R; a.B = B;
+  a.npix = geo->npix; a.nalm = geo->nalm; a.omega = geo->omega;
+  a.d = d; a.w = w; a.cl = cl; a.d32 = d32; a.w32 = w32; a.s = s; a.FS = FS; a.FT = FT; a.SP = SP;
+  a.ctl = ctl; a.active = active; a.ring_part = ring_part; a.m_part = m_part;
+  a.ntiles = ntiles; a.tiles = tiles; a.stiles = stiles; a.bstate = bstate; a.last = last;
+  return a;
+}
+
+wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
+  geo = shape_plan;
+  B = nslots;
+  stream = s_;
+  if (B < 1 || B > kBatchMax) { set_error("batched engine: slots must be in [1, 64]"); return WF_EINVAL; }
+  const int lmax = geo->lmax, RP = geo->RP, R = geo->R;
+  const size_t nalm = geo->nalm, npix = geo->npix, nF = (size_t)(lmax + 1) * RP;
+  std::vector<int2> ana, syn;
+  make_tiles(lmax, RP, ana, syn);
+  ntiles = (int)ana.size();
+  nstiles = (int)syn.size();
+  wf_status st;
+  if ((st = dalloc((void **)&lam, sizeof(float) * nalm * RP)) || (st = dalloc((void **)&FS, sizeof(float4) * nF * B)) ||
+      (st = dalloc((void **)&FT, sizeof(float4) * nF * B)) || (st = dalloc((void **)&SP, sizeof(float2) * nalm * B)) ||
+      (st = dalloc((void **)&d, sizeof(double) * npix * B)) || (st = dalloc((void **)&w, sizeof(double) * npix * B)) ||
+      (st = dalloc((void **)&d32, sizeof(float) * npix * B)) || (st = dalloc((void **)&w32, sizeof(float) * npix * B)) ||
+      (st = dalloc((void **)&cl, sizeof(double) * (lmax + 1) * B)) ||
+      (st = dalloc((void **)&s, sizeof(double2) * nalm * B)) || (st = dalloc((void **)&ctl, sizeof(Ctl) * B)) ||
+      (st = dalloc((void **)&active, sizeof(int) * B)) ||
+      (st = dalloc((void **)&ring_part, sizeof(double) * 2 * R * B)) ||
+      (st = dalloc((void **)&m_part, sizeof(double) * 3 * (size_t)ntiles * B)) ||
+      (st = dalloc((void **)&tiles, sizeof(int2) * ana.size())) ||
+      (st = dalloc((void **)&stiles, sizeof(int2) * syn.size())) || (st = dalloc((void **)&bstate, sizeof(int) * 2)) ||
+      (st = dalloc((void **)&last, sizeof(wf_iter_record) * B)))
+    return st;
+  ENG_CUDA(cudaMallocHost((void **)&h_ctl, sizeof(Ctl) * B));
+  ENG_CUDA(cudaMallocHost((void **)&h_active, sizeof(int) * B));
+  ENG_CUDA(cudaMallocHost((void **)&h_last, sizeof(wf_iter_record) * B));
+  std::fill(h_active, h_active + B, 0);
+  ENG_CUDA(cudaMemcpyAsync(tiles, ana.data(), sizeof(int2) * ana.size(), cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(stiles, syn.data(), sizeof(int2) * syn.size(), cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemsetAsync(FS, 0, sizeof(float4) * nF * B, stream));
+  ENG_CUDA(cudaMemsetAsync(FT, 0, sizeof(float4) * nF * B, stream));
+  ENG_CUDA(cudaMemsetAsync(s, 0, sizeof(double2) * nalm * B, stream));
+  ENG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) * B, stream));
+  ENG_CUDA(cudaMemsetAsync(active, 0, sizeof(int) * B, stream));
+  ENG_CUDA(cudaMemsetAsync(last, 0, sizeof(wf_iter_record) * B, stream));
+  launch_lam_table(geo->d_x, geo->legdf_args(), lmax, RP, lam, stream);
+  launch_batch_state(args(), bstate, stream);
+  ENG_CUDA(cudaGetLastError());
+  ENG_CUDA(cudaStreamSynchronize(stream));
+  return WF_OK;
+}
+
+wf_status Engine::load_slot(int b, const double *dsrc, int d_on_device, const double *wsrc_dev, const double *cl_host,
+                            const Ctl &c) {
+  const int lmax = geo->lmax;
+  const size_t npix = geo->npix;
+  launch_batch_zero_slot(args(), b, stream);
+  ENG_CUDA(cudaMemcpyAsync(d + b * npix, dsrc, sizeof(double) * npix,
+                           d_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(w + b * npix, wsrc_dev, sizeof(double) * npix, cudaMemcpyDeviceToDevice, stream));
+  launch_batch_convert_slot(args(), b, stream);
+  ENG_CUDA(cudaMemcpyAsync(cl + (size_t)b * (lmax + 1), cl_host, sizeof(double) * (lmax + 1), cudaMemcpyHostToDevice,
+                           stream));
+  h_ctl[b] = c;
+  ENG_CUDA(cudaMemcpyAsync(ctl + b, h_ctl + b, sizeof(Ctl), cudaMemcpyHostToDevice, stream));
+  h_active[b] = 1;
+  ENG_CUDA(cudaMemcpyAsync(active + b, h_active + b, sizeof(int), cudaMemcpyHostToDevice, stream));
+  return WF_OK;
+}
+
+wf_status Engine::release_slot(int b) {
+  h_active[b] = 0;
+  ENG_CUDA(cudaMemcpyAsync(active + b, h_active + b, sizeof(int), cudaMemcpyHostToDevice, stream));
+  return WF_OK;
+}
+
+wf_status Engine::refresh_state() {
+  launch_batch_state(args(), bstate, stream);
+  ENG_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+wf_status Engine::step() {
+  if (!graph) {
+    cudaGraph_t g;
+    ENG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < graph_iters; ++i) launch_batch_iteration(args(), geo->maxM, nstiles, bstate, stream);
+    ENG_CUDA(cudaStreamEndCapture(stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate (batched engine)");
+  }
+  ENG_CUDA(cudaGraphLaunch(graph, stream));
+  ENG_CUDA(cudaMemcpyAsync(h_ctl, ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost, stream));
+  ENG_CUDA(cudaMemcpyAsync(h_last, last, sizeof(wf_iter_record) * B, cudaMemcpyDeviceToHost, stream));
+  return WF_OK;
+}
+
+wf_status Engine::sync_host() {
+  ENG_CUDA(cudaStreamSynchronize(stream));
+  return WF_OK;
+}
+
+static void fill_stats(wf_stats *st, const Ctl &c, const wf_iter_record &r, long long n_obs, double ms) {
+  if (!st) return;
+  st->iters = c.iter;
+  st->converged = c.converged;
+  st->levels = c.level + 1;
+  st->lmax_sht_final = c.lsht;
+  st->lambda_final = c.lambda;
+  st->chi2_prior = r.chi2_prior;
+  st->chi2_noise = r.chi2_noise;
+  st->chi2 = r.chi2_prior + r.chi2_noise;
+  st->chi2_per_dof = st->chi2 / (double)n_obs;
+  st->rel_increment = c.last_rel;
+  st->ms_device = ms;
+}
+
+// Mixed-precision solves of nrhs data maps sharing the plan's C_l, noise and
+// mask, streamed through the plan's batched engine: every slot that finishes
+// is refilled with the next right-hand side before the next step.
+wf_status solve_mixed(Plan *P, int nrhs, const double *dsrc, int d_on_device, double *alm_out, int alm_on_device,
+                      wf_stats *stats) {
+  const int want = std::min(nrhs, P->opt.batch_slots);
+  if (!P->engine || P->engine->B != want) {
+    delete P->engine;
+    P->engine = new (std::nothrow) Engine();
+    if (!P->engine) { set_error("out of host memory"); return WF_ENOMEM; }
+    wf_status st = P->engine->create(P, want, P->run_stream());
+    if (st) { delete P->engine; P->engine = nullptr; return st; }
+  }
+  Engine *E = P->engine;
+  E->stream = P->run_stream();
+  const double lam0 = P->opt.cooling ? P->lambda_of(P->opt.l_iter0) : 1.0;
+  const int lb = P->opt.l_iter0 + P->opt.lmax_margin;
+  const int lsht0 = (lam0 <= 1.0 || !P->opt.band_limit) ? P->lmax : std::min(lb, P->lmax);
+  const Ctl c0 = P->make_ctl(1, lam0, lsht0, 0);
+  std::vector<int> slot_of(E->B, -1);
+  std::vector<std::chrono::steady_clock::time_point> t_in(E->B);
+  int next = 0, finished = 0;
+  bool any_not_conv = false, any_numeric = false;
+  wf_status st;
+  auto admit = [&](int b) -> wf_status {
+    if (next >= nrhs) { slot_of[b] = -1; return WF_OK; }
+    wf_status s2 = E->load_slot(b, dsrc + (size_t)next * P->npix, d_on_device, P->d_w, P->h_cl.data(), c0);
+    if (s2) return s2;
+    slot_of[b] = next++;
+    t_in[b] = std::chrono::steady_clock::now();
+    return WF_OK;
+  };
+  for (int b = 0; b < E->B; ++b)
+    if ((st = admit(b))) return st;
+  if ((st = E->refresh_state())) return st;
+  const long long max_steps = (long long)nrhs * ((P->opt.max_iter + E->graph_iters - 1) / E->graph_iters + 2);
+  for (long long it = 0; finished < nrhs && it < max_steps; ++it) {
+    if ((st = E->step()) || (st = E->sync_host())) return st;
+    bool changed = false;
+    for (int b = 0; b < E->B; ++b) {
+      if (slot_of[b] < 0 || !E->h_ctl[b].done) continue;
+      const int i = slot_of[b];
+      const double ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_in[b]).count();
+      ENG_CUDA(cudaMemcpyAsync(alm_out + (size_t)i * 2 * P->nalm, E->s + (size_t)b * P->nalm,
+                               sizeof(double2) * P->nalm,
+                               alm_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, E->stream));
+      fill_stats(stats ? stats + i : nullptr, E->h_ctl[b], E->h_last[b], P->n_obs, ms);
+      any_not_conv |= !E->h_ctl[b].converged;
+      any_numeric |= E->h_ctl[b].numeric != 0;
+      if ((st = E->release_slot(b))) return st;
+      ++finished;
+      if ((st = admit(b))) return st;
+      changed = true;
+    }
+    if (changed && (st = E->refresh_state())) return st;
+  }
+  if ((st = E->sync_host())) return st;
+  if (finished < nrhs) { set_error("batched solve: step limit reached"); return WF_ENOTCONVERGED; }
+  if (any_numeric) { set_error("batched solve: chi^2 is not finite"); return WF_ENUMERIC; }
+  if (any_not_conv) { set_error("batched solve: max_iter reached before the stop rule"); return WF_ENOTCONVERGED; }
+  return WF_OK;
+}
+
+}  // namespace wfk
 
 using namespace wfk;
 
 extern "C" wf_status wf_solve_batch(wf_plan_t plan, int nrhs, const double *d, int d_on_device, double *alm_out,
                                     int alm_on_device, wf_stats *stats) {
   if (!plan || !d || !alm_out || nrhs < 0) { set_error("wf_solve_batch: bad argument"); return WF_EINVAL; }
+  if (nrhs == 0) return WF_OK;
   Plan *P = static_cast<Plan *>(plan);
+  if (P->opt.precision == WF_PREC_MIXED)
+    return solve_mixed(P, nrhs, d, d_on_device, alm_out, alm_on_device, stats);
   wf_status worst = WF_OK;
   for (int i = 0; i < nrhs; ++i) {
     const wf_status st = wf_solve(plan, d + (size_t)i * P->npix, d_on_device, alm_out + (size_t)i * 2 * P->nalm,

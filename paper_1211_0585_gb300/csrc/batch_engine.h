@@ -1,0 +1,60 @@
+// Host side of the batched engine: B slots of one (nside, lmax) shape that
+// advance one messenger iteration per step, each with its own data, noise,
+// mask, C_l and schedule. Slots are filled and emptied between graph launches,
+// so a finished solve frees its slot for the next one while the others keep
+// iterating (continuous batching).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "wf_internal.h"
+#include "wf_plan.h"
+
+namespace wfk {
+
+struct Engine {
+  Plan *geo = nullptr;  // tables of the shape (not owned)
+  int B = 0;
+  int graph_iters = 4;
+  cudaStream_t stream = nullptr;
+  size_t device_bytes = 0;
+  std::vector<void *> allocs;
+
+  float *lam = nullptr;
+  float4 *FS = nullptr, *FT = nullptr;
+  float2 *SP = nullptr;
+  double *d = nullptr, *w = nullptr, *cl = nullptr;
+  float *d32 = nullptr, *w32 = nullptr;
+  double2 *s = nullptr;
+  Ctl *ctl = nullptr;
+  int *active = nullptr;
+  double *ring_part = nullptr, *m_part = nullptr;
+  int2 *tiles = nullptr, *stiles = nullptr;
+  int ntiles = 0, nstiles = 0;
+  int *bstate = nullptr;
+  wf_iter_record *last = nullptr;
+  // pinned host mirrors
+  Ctl *h_ctl = nullptr;
+  int *h_active = nullptr;
+  wf_iter_record *h_last = nullptr;
+  cudaGraphExec_t graph = nullptr;
+
+  ~Engine();
+  wf_status create(Plan *shape_plan, int nslots, cudaStream_t s);
+  BatchArgs args() const;
+  wf_status dalloc(void **p, size_t bytes);
+  // Load one problem into slot b (device state zeroed, controller initialised).
+  //   dsrc: [npix] data (host or device), wsrc: [npix] inverse noise (device),
+  //   clsrc: [lmax+1] (host), c: controller configuration for this request.
+  wf_status load_slot(int b, const double *dsrc, int d_on_device, const double *wsrc_dev, const double *cl_host,
+                      const Ctl &c);
+  wf_status refresh_state();           // recompute the live band limit after slots changed
+  wf_status step();                    // one graph launch (graph_iters iterations), then mirror ctl to host
+  wf_status sync_host();               // wait for the last step's mirrors
+  wf_status release_slot(int b);
+  static size_t bytes_needed(int nside, int lmax, int nslots);
+};
+
+}  // namespace wfk

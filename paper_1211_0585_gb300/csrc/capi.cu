@@ -5,12 +5,14 @@
 // legendre.cu and control.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include "batch_engine.h"
 #include "wf_internal.h"
 #include "wf_plan.h"
 
@@ -49,6 +51,7 @@ wf_status Plan::dalloc(void **p, size_t bytes) {
 }
 
 Plan::~Plan() {
+  delete engine;
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   for (void *p : allocs) cudaFree(p);
   if (h_ctl) cudaFreeHost(h_ctl);
@@ -111,7 +114,10 @@ static wf_status build_geometry(Plan *P) {
   P->maxM = maxM;
   P->logMmax = ilog2(maxM);
   // tables
-  std::vector<double2> hs(hs_tot), ch(ch_tot > 0 ? ch_tot : 1), tw(maxM / 2 > 0 ? maxM / 2 : 1);
+  // the chirp table is padded to the longest ring so that an index q < n is
+  // always inside it, even on rings that never use it
+  std::vector<double2> hs(hs_tot), ch(std::max<long long>(ch_tot, 4LL * ns), make_double2(0.0, 0.0));
+  std::vector<double2> tw(maxM / 2 > 0 ? maxM / 2 : 1);
   for (int i = 1; i <= ns; ++i) {
     const long long n = 4LL * i;
     for (long long q = 0; q < n; ++q) {
@@ -314,18 +320,19 @@ wf_status wf_options_default(wf_options *o) {
   o->min_level_iters = 3;
   o->max_level_iters = 1000;
   o->graph_iters = 16;
+  o->batch_slots = kBatchMax;
   o->stream = nullptr;
   return WF_OK;
 }
 
 static wf_status check_options(const wf_options *o) {
-  if (o->precision != WF_PREC_FP64 && o->precision != WF_PREC_FP64_NATIVE) {
-    set_error(o->precision == WF_PREC_MIXED ? "wf_options: the mixed-precision path is not available in this build"
-                                            : "wf_options: unknown precision");
+  if (o->precision != WF_PREC_FP64 && o->precision != WF_PREC_FP64_NATIVE && o->precision != WF_PREC_MIXED) {
+    set_error("wf_options: unknown precision");
     return WF_EINVAL;
   }
   if (!(o->tol >= 0.0) || o->max_iter < 1 || o->l_iter0 < 1 || o->lmax_margin < 0 || o->min_level_iters < 1 ||
-      o->max_level_iters < 1 || o->graph_iters < 1 || o->graph_iters > 1024 || !(o->plateau_eps >= 0.0) ||
+      o->max_level_iters < 1 || o->graph_iters < 1 || o->graph_iters > 1024 || o->batch_slots < 1 ||
+      o->batch_slots > kBatchMax || !(o->plateau_eps >= 0.0) ||
       !(o->final_dchi2 >= 0.0)) {
     set_error("wf_options: value out of range");
     return WF_EINVAL;
@@ -552,6 +559,11 @@ wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_d
 static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *alm_out, int alm_on_device,
                             const double *alm_init, wf_stats *stats, wf_iter_record *records, int max_records,
                             int *n_records) {
+  if (P->opt.precision == WF_PREC_MIXED) {
+    if (n_records) *n_records = 0;
+    if (alm_init) { set_error("wf_solve: warm start is available on the FP64 paths only"); return WF_EINVAL; }
+    return solve_mixed(P, 1, d, d_on_device, alm_out, alm_on_device, stats);
+  }
   cudaStream_t s = P->run_stream();
   const auto kind_in = d_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   WF_CUDA(cudaEventRecord(P->ev0, s));

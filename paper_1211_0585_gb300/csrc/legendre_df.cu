@@ -25,46 +25,12 @@
 // not evaluated; they lie below the 48-bit precision of any sum they enter.
 #include <cuda_runtime.h>
 
+#include "df.cuh"
 #include "wf_internal.h"
 
 namespace wfk {
 
 constexpr int kNoStartD = 1 << 30;
-
-struct dfl { float h, l; };
-
-__device__ __forceinline__ dfl df_from(double v) {
-  const float h = (float)v;
-  return {h, (float)(v - (double)h)};
-}
-
-// S + C += a * b (compensated; a, b double-float)
-__device__ __forceinline__ void dot2_acc(float &S, float &C, dfl a, dfl b) {
-  const float ph = a.h * b.h;
-  const float pe = fmaf(a.h, b.h, -ph);
-  const float pc = fmaf(a.h, b.l, a.l * b.h);
-  const float s = S + ph;
-  const float bb = s - S;
-  const float e = (S - (s - bb)) + (ph - bb);
-  S = s;
-  C += e + (pe + pc);
-}
-
-// mu_l = (A x) mu1 - mu2, all double-float
-__device__ __forceinline__ dfl df_step(dfl A, dfl x, dfl mu1, dfl mu2) {
-  const float ch = A.h * x.h;
-  float ce = fmaf(A.h, x.h, -ch);
-  ce = fmaf(A.h, x.l, fmaf(A.l, x.h, ce));
-  const float qh = ch * mu1.h;
-  float qe = fmaf(ch, mu1.h, -qh);
-  qe = fmaf(ch, mu1.l, fmaf(ce, mu1.h, qe));
-  const float sh = qh - mu2.h;
-  const float bb = sh - qh;
-  float e = (qh - (sh - bb)) + (-mu2.h - bb);
-  e += qe - mu2.l;
-  const float rh = sh + e;
-  return {rh, e - (rh - sh)};
-}
 
 __device__ __forceinline__ size_t alm_idx_d(int lmax, int l, int m) {
   return (size_t)m * (2 * lmax + 1 - m) / 2 + l;

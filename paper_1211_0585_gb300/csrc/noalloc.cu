@@ -68,7 +68,7 @@ Layout layout_for(int nside, int lmax) {
   size_t o = 0;
   L.rings = o; o = align256(o + sizeof(RingDev) * R);
   L.hs = o;    o = align256(o + sizeof(double2) * hs);
-  L.chirp = o; o = align256(o + sizeof(double2) * (ch > 0 ? ch : 1));
+  L.chirp = o; o = align256(o + sizeof(double2) * (ch > 4LL * nside ? ch : 4LL * nside));
   L.B = o;     o = align256(o + sizeof(double2) * (B > 0 ? B : 1));
   L.tw = o;    o = align256(o + sizeof(double2) * (maxM / 2 > 0 ? maxM / 2 : 1));
   L.x = o;     o = align256(o + sizeof(double) * RP);

@@ -112,6 +112,39 @@ struct RingDfArgs {
   const float4 *tw, *hs, *chirp, *B;
 };
 
+// Batched engine (batch_kernels.cu): B slots of one shape in lockstep.
+constexpr int kBatchMax = 64;
+
+struct BatchArgs {
+  const RingDev *rings;
+  const float4 *twf, *hsf, *chf, *Bf;
+  int logMmax;
+  const float *lam;          // [nalm][RP] lambda_lm(x_k), FP32
+  int lmax, RP, R, B;
+  long long npix, nalm;
+  double omega;
+  const double *d, *w, *cl;  // [B][npix], [B][npix], [B][lmax+1]
+  float *d32, *w32;          // [B][npix] FP32 copies read by the mixed-precision ring stage
+  double2 *s;                // [B][nalm] state
+  float4 *FS, *FT;           // [(m RP + k) B + b] (north re, north im, south re, south im)
+  float2 *SP;                // [nalm][B] synthesis coefficients
+  Ctl *ctl;                  // [B]
+  const int *active;         // [B]
+  double *ring_part;         // [B][R][2]
+  double *m_part;            // [B][ntiles][3]
+  int ntiles;
+  const int2 *tiles;         // analysis tiles (m, l0), 64 l each
+  const int2 *stiles;        // synthesis tiles (m, k0), 32 ring pairs each
+  const int *bstate;         // [0] largest live band limit, [1] live slots
+  wf_iter_record *last;      // [B]
+};
+
+void launch_lam_table(const double *x, const LegDfArgs &D, int lmax, int RP, float *lam, cudaStream_t s);
+void launch_batch_iteration(const BatchArgs &a, int maxM, int n_stiles, int *bstate, cudaStream_t s);
+void launch_batch_state(const BatchArgs &a, int *bstate, cudaStream_t s);
+void launch_batch_zero_slot(const BatchArgs &a, int b, cudaStream_t s);
+void launch_batch_convert_slot(const BatchArgs &a, int b, cudaStream_t s);
+
 void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode);
 void launch_ring_df(const RingArgs &a, const RingDfArgs &t, int R, int maxM, cudaStream_t s, int mode);
 void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s);

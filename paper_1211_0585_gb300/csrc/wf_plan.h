@@ -13,7 +13,10 @@ struct wf_plan_s {
 
 namespace wfk {
 
+struct Engine;
+
 struct Plan : wf_plan_s {
+  Engine *engine = nullptr;  // batched engine of this shape (mixed precision), built on first use
   int nside = 0, lmax = 0, R = 0, RP = 0;
   long long npix = 0, nalm = 0, n_obs = 0;
   double tau = 0.0, omega = 0.0;
@@ -77,5 +80,9 @@ struct Plan : wf_plan_s {
   Ctl make_ctl(int mode, double lambda, int lsht, int n_fixed) const;
   double lambda_of(int l_iter) const;
 };
+
+// Mixed-precision solves through the plan's batched engine (batch.cu).
+wf_status solve_mixed(Plan *P, int nrhs, const double *d, int d_on_device, double *alm_out, int alm_on_device,
+                      wf_stats *stats);
 
 }  // namespace wfk

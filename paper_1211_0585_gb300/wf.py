@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("band_limit", ctypes.c_int), ("plateau_eps", ctypes.c_double),
                 ("final_dchi2", ctypes.c_double), ("min_level_iters", ctypes.c_int),
                 ("max_level_iters", ctypes.c_int), ("graph_iters", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("batch_slots", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
