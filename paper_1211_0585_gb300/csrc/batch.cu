@@ -133,6 +133,23 @@ wf_status Engine::load_slot(int b, const double *dsrc, int d_on_device, const do
   return WF_OK;
 }
 
+wf_status Engine::load_slot_host(int b, const double *d_host, const double *w_host, const double *cl_host,
+                                 const Ctl &c) {
+  const int lmax = geo->lmax;
+  const size_t npix = geo->npix;
+  launch_batch_zero_slot(args(), b, stream);
+  ENG_CUDA(cudaMemcpyAsync(d + b * npix, d_host, sizeof(double) * npix, cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(w + b * npix, w_host, sizeof(double) * npix, cudaMemcpyHostToDevice, stream));
+  launch_batch_convert_slot(args(), b, stream);
+  ENG_CUDA(cudaMemcpyAsync(cl + (size_t)b * (lmax + 1), cl_host, sizeof(double) * (lmax + 1), cudaMemcpyHostToDevice,
+                           stream));
+  h_ctl[b] = c;
+  ENG_CUDA(cudaMemcpyAsync(ctl + b, h_ctl + b, sizeof(Ctl), cudaMemcpyHostToDevice, stream));
+  h_active[b] = 1;
+  ENG_CUDA(cudaMemcpyAsync(active + b, h_active + b, sizeof(int), cudaMemcpyHostToDevice, stream));
+  return WF_OK;
+}
+
 wf_status Engine::release_slot(int b) {
   h_active[b] = 0;
   ENG_CUDA(cudaMemcpyAsync(active + b, h_active + b, sizeof(int), cudaMemcpyHostToDevice, stream));

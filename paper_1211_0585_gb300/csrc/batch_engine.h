@@ -50,6 +50,8 @@ struct Engine {
   //   clsrc: [lmax+1] (host), c: controller configuration for this request.
   wf_status load_slot(int b, const double *dsrc, int d_on_device, const double *wsrc_dev, const double *cl_host,
                       const Ctl &c);
+  // As load_slot, with the inverse noise given on the host (serving).
+  wf_status load_slot_host(int b, const double *d_host, const double *w_host, const double *cl_host, const Ctl &c);
   wf_status refresh_state();           // recompute the live band limit after slots changed
   wf_status step();                    // one graph launch (graph_iters iterations), then mirror ctl to host
   wf_status sync_host();               // wait for the last step's mirrors

@@ -1,34 +1,425 @@
-// Serving loop (continuous batching) -- entry points; the scheduler lands in
-// a later change.
+// Serving loop: continuous batching of Wiener-filter requests.
+//
+// Requests of any (nside, lmax, C_l, noise, mask) arrive through wf_submit
+// and never block on the GPU. A worker thread admits them:
+//   - tol > 1e-7 (mixed precision): into a free slot of the batched engine of
+//     their shape (one engine, stream and FP32 Lambda table per shape, created
+//     on first use when its device-memory footprint fits the budget, evicted
+//     when idle and the budget is needed). Every step advances all live slots
+//     of an engine by a block of iterations; finished slots are harvested and
+//     refilled before the next step, so a request that arrives while others
+//     iterate joins at the next step with its own lambda schedule.
+//   - tol <= 1e-7 (FP64 path): one at a time on a second worker with a plan
+//     of its own (double-float kernels), overlapping with the engines' work
+//     on the device.
+// Latency is measured from wf_submit to the moment the result is on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "batch_engine.h"
 #include "wf_internal.h"
+#include "wf_plan.h"
 
 using namespace wfk;
+using Clock = std::chrono::steady_clock;
 
-struct wf_server_s {};
+namespace {
+
+constexpr double kFp64Tol = 1e-7;
+
+struct Request {
+  uint64_t ticket = 0;
+  int nside = 0, lmax = 0;
+  double tol = 1e-6;
+  std::vector<double> cl, noise, w, d;
+  std::vector<uint8_t> mask;
+  double tau = 0.0;
+  long long n_obs = 0;
+  Clock::time_point t_submit;
+  // result
+  bool done = false;
+  wf_status status = WF_OK;
+  std::vector<double> alm;
+  wf_stats stats{};
+  size_t fp64_bytes = 0;
+};
+
+struct ShapeRunner {
+  int nside = 0, lmax = 0;
+  Plan *shape = nullptr;              // tables of the shape (unit noise)
+  std::unique_ptr<Engine> engine;
+  std::vector<std::shared_ptr<Request>> slot;  // request in each slot (or null)
+  size_t bytes = 0;
+  Clock::time_point last_used;
+  ~ShapeRunner() {
+    engine.reset();
+    if (shape) wf_plan_destroy(shape);
+  }
+  int live() const {
+    int n = 0;
+    for (auto &r : slot) n += r != nullptr;
+    return n;
+  }
+};
+
+}  // namespace
+
+struct wf_server_s {
+  size_t budget = 0;
+  int max_batch = 16;
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  std::deque<std::shared_ptr<Request>> pending;      // mixed requests not yet in a slot
+  std::deque<std::shared_ptr<Request>> fp64_queue;   // FP64 requests
+  std::map<uint64_t, std::shared_ptr<Request>> all;  // every uncollected request
+  int in_flight = 0;                                 // submitted and not finished
+  std::vector<double> latencies_ms;
+  int64_t completed = 0;
+  std::map<std::pair<int, int>, std::unique_ptr<ShapeRunner>> runners;  // worker thread only
+  size_t fp64_bytes_in_use = 0;
+  std::thread worker, fp64_worker;
+  std::string worker_error;
+
+  void finish(const std::shared_ptr<Request> &r) {
+    std::lock_guard<std::mutex> lk(mu);
+    r->done = true;
+    latencies_ms.push_back(std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count());
+    ++completed;
+    --in_flight;
+    cv_done.notify_all();
+  }
+};
+
+namespace {
+
+size_t engine_bytes(int nside, int lmax, int slots) {
+  // engine buffers plus the shape plan's tables (about 70 bytes per (m, ring pair) entry)
+  return Engine::bytes_needed(nside, lmax, slots) + (size_t)(lmax + 1) * 2 * nside * 72 + 64 * nside * (size_t)nside;
+}
+
+Ctl request_ctl(const Plan *shape, const Request &r) {
+  wf_options o;
+  wf_options_default(&o);
+  Ctl c{};
+  c.mode = 1;
+  c.max_iter = o.max_iter;
+  c.cooling = o.cooling;
+  c.l_iter0 = o.l_iter0;
+  c.margin = o.lmax_margin;
+  c.band_limit = o.band_limit;
+  c.min_level_iters = o.min_level_iters;
+  c.max_level_iters = o.max_level_iters;
+  c.lmax = r.lmax;
+  c.tol = r.tol;
+  c.plateau_eps = o.plateau_eps;
+  c.final_dchi2 = o.final_dchi2;
+  c.sigma_chi2 = std::sqrt(2.0 * (double)r.n_obs);
+  c.tau = r.tau;
+  c.omega = shape->omega;
+  double lam = 1.0;
+  if (o.cooling && o.l_iter0 <= r.lmax) lam = std::max(1.0, r.cl[o.l_iter0] / (r.tau * shape->omega));
+  c.lambda = lam;
+  const int lb = o.l_iter0 + o.lmax_margin;
+  c.lsht = (lam <= 1.0 || !o.band_limit) ? r.lmax : std::min(lb, r.lmax);
+  c.l_iter = o.l_iter0;
+  return c;
+}
+
+size_t bytes_in_use(wf_server_s *S) {
+  size_t b = S->fp64_bytes_in_use;
+  for (auto &kv : S->runners) b += kv.second->bytes;
+  return b;
+}
+
+// Find or create the runner of a shape within the budget (evicting idle ones).
+ShapeRunner *runner_for(wf_server_s *S, int nside, int lmax) {
+  auto key = std::make_pair(nside, lmax);
+  auto it = S->runners.find(key);
+  if (it != S->runners.end()) return it->second.get();
+  const size_t need = engine_bytes(nside, lmax, S->max_batch);
+  while (bytes_in_use(S) + need > S->budget) {
+    // evict the least recently used idle runner
+    auto victim = S->runners.end();
+    for (auto jt = S->runners.begin(); jt != S->runners.end(); ++jt)
+      if (jt->second->live() == 0 &&
+          (victim == S->runners.end() || jt->second->last_used < victim->second->last_used))
+        victim = jt;
+    if (victim == S->runners.end()) return nullptr;  // no room yet: wait for slots to free
+    S->runners.erase(victim);
+  }
+  auto R = std::make_unique<ShapeRunner>();
+  R->nside = nside;
+  R->lmax = lmax;
+  std::vector<double> unit(12LL * nside * nside, 1.0), cl(lmax + 1, 1.0);
+  wf_plan_t p = nullptr;
+  if (wf_plan_create(nside, lmax, cl.data(), unit.data(), nullptr, nullptr, &p) != WF_OK) return nullptr;
+  R->shape = static_cast<Plan *>(p);
+  R->engine = std::make_unique<Engine>();
+  if (R->engine->create(R->shape, S->max_batch, R->shape->stream) != WF_OK) return nullptr;
+  R->engine->graph_iters = 8;
+  R->slot.assign(S->max_batch, nullptr);
+  R->bytes = need;
+  R->last_used = Clock::now();
+  ShapeRunner *raw = R.get();
+  S->runners[key] = std::move(R);
+  return raw;
+}
+
+void worker_loop(wf_server_s *S) {
+  for (;;) {
+    // admission
+    std::vector<std::shared_ptr<Request>> take;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      bool busy = false;
+      for (auto &kv : S->runners) busy |= kv.second->live() > 0;
+      if (!busy) S->cv.wait_for(lk, std::chrono::milliseconds(20), [&] { return S->stop || !S->pending.empty(); });
+      if (S->stop) return;
+      take.assign(S->pending.begin(), S->pending.end());
+      S->pending.clear();
+    }
+    std::vector<std::shared_ptr<Request>> keep;
+    std::map<ShapeRunner *, bool> changed;
+    for (auto &r : take) {
+      ShapeRunner *R = runner_for(S, r->nside, r->lmax);
+      int b = -1;
+      if (R)
+        for (int i = 0; i < (int)R->slot.size(); ++i)
+          if (!R->slot[i]) { b = i; break; }
+      if (!R || b < 0) { keep.push_back(r); continue; }
+      const Ctl c = request_ctl(R->shape, *r);
+      if (R->engine->load_slot_host(b, r->d.data(), r->w.data(), r->cl.data(), c) != WF_OK) {
+        r->status = WF_ECUDA;
+        S->finish(r);
+        continue;
+      }
+      R->slot[b] = r;
+      changed[R] = true;
+    }
+    if (!keep.empty()) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->pending.insert(S->pending.begin(), keep.begin(), keep.end());
+    }
+    // one step of every engine with live slots (their streams overlap on the device)
+    std::vector<ShapeRunner *> stepped;
+    for (auto &kv : S->runners) {
+      ShapeRunner *R = kv.second.get();
+      if (R->live() == 0) continue;
+      if (changed.count(R)) R->engine->refresh_state();
+      if (R->engine->step() == WF_OK) stepped.push_back(R);
+    }
+    for (ShapeRunner *R : stepped) {
+      R->engine->sync_host();
+      R->last_used = Clock::now();
+      bool any = false;
+      for (int b = 0; b < (int)R->slot.size(); ++b) {
+        auto &r = R->slot[b];
+        if (!r || !R->engine->h_ctl[b].done) continue;
+        const Ctl &c = R->engine->h_ctl[b];
+        const wf_iter_record &last = R->engine->h_last[b];
+        r->alm.resize(2 * (size_t)R->shape->nalm);
+        cudaMemcpyAsync(r->alm.data(), R->engine->s + (size_t)b * R->shape->nalm,
+                        sizeof(double2) * R->shape->nalm, cudaMemcpyDeviceToHost, R->engine->stream);
+        cudaStreamSynchronize(R->engine->stream);
+        r->stats.iters = c.iter;
+        r->stats.converged = c.converged;
+        r->stats.levels = c.level + 1;
+        r->stats.lmax_sht_final = c.lsht;
+        r->stats.lambda_final = c.lambda;
+        r->stats.chi2_prior = last.chi2_prior;
+        r->stats.chi2_noise = last.chi2_noise;
+        r->stats.chi2 = last.chi2_prior + last.chi2_noise;
+        r->stats.chi2_per_dof = r->stats.chi2 / (double)r->n_obs;
+        r->stats.rel_increment = c.last_rel;
+        r->stats.ms_device =
+            std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+        r->status = c.numeric ? WF_ENUMERIC : (c.converged ? WF_OK : WF_ENOTCONVERGED);
+        R->engine->release_slot(b);
+        S->finish(r);
+        r.reset();
+        any = true;
+      }
+      if (any) R->engine->refresh_state();
+    }
+  }
+}
+
+void fp64_loop(wf_server_s *S) {
+  for (;;) {
+    std::shared_ptr<Request> r;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return S->stop || !S->fp64_queue.empty(); });
+      if (S->stop) return;
+      if (S->fp64_queue.empty()) continue;
+      r = S->fp64_queue.front();
+      const size_t need = engine_bytes(r->nside, r->lmax, 1);
+      if (S->fp64_bytes_in_use + need > S->budget) continue;  // wait for room
+      S->fp64_queue.pop_front();
+      S->fp64_bytes_in_use += need;
+      r->fp64_bytes = need;
+    }
+    wf_options o;
+    wf_options_default(&o);
+    o.tol = r->tol;
+    wf_plan_t p = nullptr;
+    wf_status st = wf_plan_create(r->nside, r->lmax, r->cl.data(), r->noise.data(),
+                                  r->mask.empty() ? nullptr : r->mask.data(), &o, &p);
+    if (st == WF_OK) {
+      r->alm.resize(2 * (size_t)(r->lmax + 1) * (r->lmax + 2) / 2);
+      st = wf_solve(p, r->d.data(), 0, r->alm.data(), 0, nullptr, &r->stats);
+      r->stats.ms_device = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+      wf_plan_destroy(p);
+    }
+    r->status = st;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->fp64_bytes_in_use -= r->fp64_bytes;
+    }
+    S->finish(r);
+  }
+}
+
+}  // namespace
 
 extern "C" {
-wf_status wf_server_create(size_t, int, wf_server_t *out) {
-  if (out) *out = nullptr;
-  set_error("wf_server_create: serving is not available in this build");
-  return WF_EINVAL;
+
+wf_status wf_server_create(size_t hbm_budget_bytes, int max_batch, wf_server_t *out) {
+  if (!out) { set_error("wf_server_create: NULL out"); return WF_EINVAL; }
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > kBatchMax) { set_error("wf_server_create: max_batch must be in [1, 64]"); return WF_EINVAL; }
+  size_t budget = hbm_budget_bytes;
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMemGetInfo");
+    budget = (size_t)(0.9 * (double)fr);
+  }
+  wf_server_s *S = new (std::nothrow) wf_server_s();
+  if (!S) { set_error("out of host memory"); return WF_ENOMEM; }
+  S->budget = budget;
+  S->max_batch = max_batch;
+  S->worker = std::thread(worker_loop, S);
+  S->fp64_worker = std::thread(fp64_loop, S);
+  *out = S;
+  return WF_OK;
 }
-wf_status wf_submit(wf_server_t, int, int, const double *, const double *, const uint8_t *, const double *, double,
-                    uint64_t *) {
-  set_error("wf_submit: serving is not available in this build");
-  return WF_EINVAL;
+
+wf_status wf_submit(wf_server_t S, int nside, int lmax, const double *cl, const double *noise_var,
+                    const uint8_t *mask, const double *d, double tol, uint64_t *ticket) {
+  if (!S || !cl || !noise_var || !d || !ticket) { set_error("wf_submit: NULL argument"); return WF_EINVAL; }
+  if (nside < 1 || nside > 1024 || (nside & (nside - 1)) != 0 || lmax < 0 || lmax > 4 * nside) {
+    set_error("wf_submit: nside must be a power of two in [1, 1024] and 0 <= lmax <= 4 nside");
+    return WF_EINVAL;
+  }
+  if (!(tol > 0.0) || !std::isfinite(tol)) { set_error("wf_submit: tol must be > 0"); return WF_EINVAL; }
+  auto r = std::make_shared<Request>();
+  const long long npix = 12LL * nside * nside;
+  r->nside = nside;
+  r->lmax = lmax;
+  r->tol = tol;
+  r->cl.assign(cl, cl + lmax + 1);
+  for (double c : r->cl)
+    if (!std::isfinite(c) || c < 0.0) { set_error("wf_submit: C_l must be finite and >= 0"); return WF_EINVAL; }
+  r->noise.assign(noise_var, noise_var + npix);
+  r->d.assign(d, d + npix);
+  if (mask) r->mask.assign(mask, mask + npix);
+  r->w.assign(npix, 0.0);
+  double tau = INFINITY;
+  for (long long p = 0; p < npix; ++p) {
+    if (mask && !mask[p]) continue;
+    const double v = noise_var[p];
+    if (!std::isfinite(v) || !(v > 0.0)) {
+      set_error("wf_submit: noise variance must be finite and > 0 on observed pixels");
+      return WF_EINVAL;
+    }
+    r->w[p] = 1.0 / v;
+    tau = std::min(tau, v);
+    ++r->n_obs;
+  }
+  if (r->n_obs == 0) { set_error("wf_submit: no observed pixel"); return WF_EINVAL; }
+  r->tau = tau;
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->ticket = S->next_ticket++;
+    S->all[r->ticket] = r;
+    ++S->in_flight;
+    if (tol <= kFp64Tol) S->fp64_queue.push_back(r);
+    else S->pending.push_back(r);
+  }
+  S->cv.notify_all();
+  *ticket = r->ticket;
+  return WF_OK;
 }
-wf_status wf_poll(wf_server_t, uint64_t, int *done, double *, wf_stats *) {
-  if (done) *done = 0;
-  set_error("wf_poll: serving is not available in this build");
-  return WF_EINVAL;
+
+wf_status wf_poll(wf_server_t S, uint64_t ticket, int *done, double *alm_out, wf_stats *stats) {
+  if (!S || !done) { set_error("wf_poll: NULL argument"); return WF_EINVAL; }
+  std::shared_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) { *done = 0; set_error("wf_poll: unknown ticket"); return WF_ENOTFOUND; }
+    if (!it->second->done) { *done = 0; return WF_EBUSY; }
+    r = it->second;
+    S->all.erase(it);
+  }
+  *done = 1;
+  if (alm_out && !r->alm.empty()) std::copy(r->alm.begin(), r->alm.end(), alm_out);
+  if (stats) *stats = r->stats;
+  if (r->status != WF_OK) set_error("wf_poll: request finished with an error status");
+  return r->status;
 }
-wf_status wf_server_drain(wf_server_t, int) {
-  set_error("wf_server_drain: serving is not available in this build");
-  return WF_EINVAL;
+
+wf_status wf_server_drain(wf_server_t S, int timeout_ms) {
+  if (!S) { set_error("wf_server_drain: NULL server"); return WF_EINVAL; }
+  std::unique_lock<std::mutex> lk(S->mu);
+  const bool ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                      [&] { return S->in_flight == 0; });
+  if (!ok) { set_error("wf_server_drain: timed out"); return WF_ETIMEOUT; }
+  return WF_OK;
 }
-wf_status wf_server_stats(wf_server_t, double *, double *, int64_t *) {
-  set_error("wf_server_stats: serving is not available in this build");
-  return WF_EINVAL;
+
+wf_status wf_server_stats(wf_server_t S, double *p50_ms, double *p99_ms, int64_t *completed) {
+  if (!S) { set_error("wf_server_stats: NULL server"); return WF_EINVAL; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  std::vector<double> v = S->latencies_ms;
+  std::sort(v.begin(), v.end());
+  auto pct = [&](double q) {
+    if (v.empty()) return 0.0;
+    const size_t i = std::min(v.size() - 1, (size_t)std::ceil(q * (double)v.size()) - (q > 0 ? 1 : 0));
+    return v[i];
+  };
+  if (p50_ms) *p50_ms = pct(0.50);
+  if (p99_ms) *p99_ms = pct(0.99);
+  if (completed) *completed = S->completed;
+  return WF_OK;
 }
-wf_status wf_server_destroy(wf_server_t) { return WF_OK; }
+
+wf_status wf_server_destroy(wf_server_t S) {
+  if (!S) return WF_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  if (S->fp64_worker.joinable()) S->fp64_worker.join();
+  S->runners.clear();
+  delete S;
+  return WF_OK;
 }
+
+}  // extern "C"

@@ -275,7 +275,7 @@ class Server:
     def poll(self, ticket):
         """Returns None while running, else (alm, stats, status)."""
         done = ctypes.c_int()
-        out = np.empty(self._nalm[ticket], dtype=np.complex128)
+        out = np.empty(self._nalm.get(ticket, 1), dtype=np.complex128)
         st = Stats()
         status = load().wf_poll(self.handle, ticket, ctypes.byref(done), out.ctypes.data_as(ctypes.c_void_p),
                                 ctypes.byref(st))
