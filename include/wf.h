@@ -137,6 +137,12 @@ wf_status wf_plan_destroy(wf_plan_t plan);
 wf_status wf_plan_info(wf_plan_t plan, int64_t *npix, int64_t *nalm, double *tau,
                        int64_t *n_obs, size_t *device_bytes);
 
+/* Work of the Legendre stage at band limit lsht: the number of (l, m, ring
+ * pair) terms with l, m <= lsht that the double-float kernels evaluate (terms
+ * with |lambda_lm| below 2^-60 are skipped), and the full count
+ * (lsht+1)(lsht+2)/2 * 2 nside for comparison. Either out pointer may be NULL. */
+wf_status wf_plan_legendre_terms(wf_plan_t plan, int lsht, int64_t *evaluated, int64_t *full);
+
 /* Replace the plan's options (precision, tolerances, schedule knobs, stream). */
 wf_status wf_plan_set_options(wf_plan_t plan, const wf_options *opt);
 

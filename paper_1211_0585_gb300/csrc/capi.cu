@@ -422,6 +422,24 @@ wf_status wf_plan_info(wf_plan_t plan, int64_t *npix, int64_t *nalm, double *tau
   return WF_OK;
 }
 
+wf_status wf_plan_legendre_terms(wf_plan_t plan, int lsht, int64_t *evaluated, int64_t *full) {
+  if (!plan) { set_error("wf_plan_legendre_terms: NULL plan"); return WF_EINVAL; }
+  Plan *P = static_cast<Plan *>(plan);
+  if (lsht < 0 || lsht > P->lmax) { set_error("wf_plan_legendre_terms: lsht out of range"); return WF_EINVAL; }
+  const size_t nmk = (size_t)(P->lmax + 1) * P->RP;
+  std::vector<int> ls(nmk);
+  WF_CUDA(cudaMemcpy(ls.data(), P->d_dfls, sizeof(int) * nmk, cudaMemcpyDeviceToHost));
+  int64_t ev = 0;
+  for (int m = 0; m <= lsht; ++m)
+    for (int k = 0; k < P->RP; ++k) {
+      const int l0 = ls[(size_t)m * P->RP + k];
+      if (l0 <= lsht) ev += lsht - l0 + 1;
+    }
+  if (evaluated) *evaluated = ev;
+  if (full) *full = (int64_t)(lsht + 1) * (lsht + 2) / 2 * P->RP;
+  return WF_OK;
+}
+
 wf_status wf_plan_set_options(wf_plan_t plan, const wf_options *opt) {
   if (!plan || !opt) { set_error("wf_plan_set_options: NULL"); return WF_EINVAL; }
   if (check_options(opt)) return WF_EINVAL;

@@ -22,7 +22,8 @@ WF_PREC_FP64, WF_PREC_MIXED, WF_PREC_FP64_NATIVE = 0, 1, 2
 STATUS_NAMES = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "WF_ENOTCONVERGED",
                 5: "WF_ENUMERIC", 6: "WF_ETIMEOUT", 7: "WF_EBUSY", 8: "WF_ECANCELLED", 9: "WF_ENOTFOUND"}
 
-EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_info", "wf_plan_set_options",
+EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_info", "wf_plan_legendre_terms",
+            "wf_plan_set_options",
             "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
             "wf_solve_history", "wf_solve_batch",
             "wf_server_create", "wf_submit", "wf_poll", "wf_server_drain", "wf_server_stats",
@@ -85,6 +86,7 @@ def load(path: str = LIB_PATH):
         "wf_plan_info": [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _dp,
                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t)],
         "wf_plan_set_options": [_vp, ctypes.POINTER(Options)],
+        "wf_plan_legendre_terms": [_vp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
         "wf_alm2map": [_vp, _i, _vp, _vp],
         "wf_map2alm": [_vp, _i, _vp, _vp],
         "wf_map2alm_noalloc": [_i, _i, _vp, _vp, _vp],
@@ -185,6 +187,12 @@ class Plan:
         _check(load().wf_plan_info(self.handle, ctypes.byref(npix), ctypes.byref(nalm), ctypes.byref(tau),
                                    ctypes.byref(nobs), ctypes.byref(nbytes)))
         return dict(npix=npix.value, nalm=nalm.value, tau=tau.value, n_obs=nobs.value, device_bytes=nbytes.value)
+
+    def legendre_terms(self, lsht):
+        """(evaluated, full) counts of (l, m, ring pair) Legendre terms at band limit lsht."""
+        ev, full = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().wf_plan_legendre_terms(self.handle, lsht, ctypes.byref(ev), ctypes.byref(full)))
+        return ev.value, full.value
 
     def set_options(self, opts: Options):
         _check(load().wf_plan_set_options(self.handle, ctypes.byref(opts)))
