@@ -15,6 +15,7 @@
 
 #include "ctl.cuh"
 #include "df.cuh"
+#include "fft.cuh"
 #include "wf_internal.h"
 
 namespace wfk {
@@ -30,52 +31,6 @@ __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 f2conj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.x, v.z); }  // hi parts of a df complex
-
-__device__ __forceinline__ int bitrev_b(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
-
-__device__ void fft_dif_f(float2 *buf, int logM, int sign, const float4 *tw, int logMmax) {
-  const int M = 1 << logM;
-  for (int s = logM; s >= 1; --s) {
-    const int half = 1 << (s - 1);
-    const int tsh = logMmax - s;
-    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      float2 w = hi2(tw[pos << tsh]);
-      if (sign > 0) w.y = -w.y;
-      const float2 a = buf[i0], b = buf[i1];
-      buf[i0] = f2add(a, b);
-      buf[i1] = f2mul(f2sub(a, b), w);
-    }
-    __syncthreads();
-  }
-}
-
-__device__ void fft_dit_f(float2 *buf, int logM, int sign, const float4 *tw, int logMmax) {
-  const int M = 1 << logM;
-  for (int s = 1; s <= logM; ++s) {
-    const int half = 1 << (s - 1);
-    const int tsh = logMmax - s;
-    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      float2 w = hi2(tw[pos << tsh]);
-      if (sign > 0) w.y = -w.y;
-      const float2 a = buf[i0], b = f2mul(buf[i1], w);
-      buf[i0] = f2add(a, b);
-      buf[i1] = f2sub(a, b);
-    }
-    __syncthreads();
-  }
-}
-
-__device__ void bluestein_f(float2 *buf, int logM, const float4 *Bf, const float4 *tw, int logMmax) {
-  const int M = 1 << logM;
-  fft_dif_f(buf, logM, -1, tw, logMmax);
-  for (int i = threadIdx.x; i < M; i += blockDim.x) buf[i] = f2mul(buf[i], hi2(Bf[i]));
-  __syncthreads();
-  fft_dit_f(buf, logM, +1, tw, logMmax);
-}
 
 }  // namespace
 
@@ -113,61 +68,7 @@ __global__ void lam_table_kernel(const double *xk, const LegDfArgs D, int lmax, 
 // One CTA per (ring, group of G slots): the G slots share every twiddle load
 // and read their Fourier coefficients as one contiguous run of G float4.
 template <int G>
-__device__ void fft_dif_g(float2 *buf, int M, int logM, int sign, const float4 *tw, int logMmax) {
-  for (int s = logM; s >= 1; --s) {
-    const int half = 1 << (s - 1);
-    const int tsh = logMmax - s;
-    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      float2 w = hi2(tw[pos << tsh]);
-      if (sign > 0) w.y = -w.y;
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const float2 a = buf[g * M + i0], b = buf[g * M + i1];
-        buf[g * M + i0] = f2add(a, b);
-        buf[g * M + i1] = f2mul(f2sub(a, b), w);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <int G>
-__device__ void fft_dit_g(float2 *buf, int M, int logM, int sign, const float4 *tw, int logMmax) {
-  for (int s = 1; s <= logM; ++s) {
-    const int half = 1 << (s - 1);
-    const int tsh = logMmax - s;
-    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      float2 w = hi2(tw[pos << tsh]);
-      if (sign > 0) w.y = -w.y;
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const float2 a = buf[g * M + i0], b = f2mul(buf[g * M + i1], w);
-        buf[g * M + i0] = f2add(a, b);
-        buf[g * M + i1] = f2sub(a, b);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <int G>
-__device__ void bluestein_g(float2 *buf, int M, int logM, const float4 *Bf, const float4 *tw, int logMmax) {
-  fft_dif_g<G>(buf, M, logM, -1, tw, logMmax);
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    const float2 f = hi2(Bf[i]);
-#pragma unroll
-    for (int g = 0; g < G; ++g) buf[g * M + i] = f2mul(buf[g * M + i], f);
-  }
-  __syncthreads();
-  fft_dit_g<G>(buf, M, logM, +1, tw, logMmax);
-}
-
-template <int G>
-__global__ void __launch_bounds__(kThreads) bring_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) {
   extern __shared__ float2 bsm[];
   const int r = blockIdx.x, b0 = blockIdx.y * G;
   const int B = A.B;
@@ -185,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) bring_kernel(const BatchArgs A) {
   const int n = rg.n, M = 1 << rg.logM;
   float2 *buf = bsm;                                          // [G][M]
   float *ureal = reinterpret_cast<float *>(bsm + G * M);      // [G][n]
-  __shared__ double red[kThreads / 32][2 * G];
+  __shared__ double red[kRingThreads / 32][2 * G];
   const float4 *hs = A.hsf + rg.hs_off;
   const float4 *ch = A.chf + rg.ch_off;
   const float4 *Bf = A.Bf + rg.B_off;
@@ -249,8 +150,8 @@ __global__ void __launch_bounds__(kThreads) bring_kernel(const BatchArgs A) {
 #pragma unroll
       for (int g = 0; g < G; ++g) buf[g * M + q] = make_float2(0.f, 0.f);
   __syncthreads();
-  if (rg.blue) bluestein_g<G>(buf, M, rg.logM, Bf, A.twf, A.logMmax);
-  else fft_dif_g<G>(buf, M, rg.logM, +1, A.twf, A.logMmax);
+  if (rg.blue) bluestein4<OpsF32, G>(buf, M, rg.logM, Bf, A.twf, A.logMmax);
+  else fft_dif4<OpsF32, G>(buf, M, rg.logM, +1, A.twf, A.logMmax);
 
   // Eq. 3 per pixel and the chi^2 partials in FP32 (per-thread sums of at
   // most 16 terms), the block reduction in double
@@ -259,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) bring_kernel(const BatchArgs A) {
   for (int g = 0; g < G; ++g) { c2n[g] = 0.f; c2l[g] = 0.f; }
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const float2 cp = rg.blue ? hi2(ch[p]) : make_float2(0.f, 0.f);
-    const int br = rg.blue ? p : bitrev_b(p, rg.logM);
+    const int br = rg.blue ? p : digitrev(p, rg.logM);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       if (!on[g]) { ureal[g * n + p] = 0.f; continue; }
@@ -288,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) bring_kernel(const BatchArgs A) {
     if (threadIdx.x < G && on[threadIdx.x]) {
       const int g = threadIdx.x;
       double sa = 0.0, sb = 0.0;
-      for (int w2 = 0; w2 < kThreads / 32; ++w2) { sa += red[w2][2 * g]; sb += red[w2][2 * g + 1]; }
+      for (int w2 = 0; w2 < kRingThreads / 32; ++w2) { sa += red[w2][2 * g]; sb += red[w2][2 * g + 1]; }
       A.ring_part[((size_t)(b0 + g) * A.R + r) * 2] = sa;
       A.ring_part[((size_t)(b0 + g) * A.R + r) * 2 + 1] = sb;
     }
@@ -304,15 +205,15 @@ __global__ void __launch_bounds__(kThreads) bring_kernel(const BatchArgs A) {
       }
     }
     __syncthreads();
-    bluestein_g<G>(buf, M, rg.logM, Bf, A.twf, A.logMmax);
+    bluestein4<OpsF32, G>(buf, M, rg.logM, Bf, A.twf, A.logMmax);
   } else {
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const int br = bitrev_b(p, rg.logM);
+      const int br = digitrev(p, rg.logM);
 #pragma unroll
       for (int g = 0; g < G; ++g) buf[g * M + br] = make_float2(ureal[g * n + p], 0.f);
     }
     __syncthreads();
-    fft_dit_g<G>(buf, M, rg.logM, -1, A.twf, A.logMmax);
+    fft_dit4<OpsF32, G>(buf, M, rg.logM, -1, A.twf, A.logMmax);
   }
   const float om = (float)A.omega;
   for (int m = threadIdx.x; m <= Lmax; m += blockDim.x) {
@@ -632,7 +533,7 @@ template <int G>
 static void launch_bring(const BatchArgs &a, int maxM, cudaStream_t s) {
   const size_t sm = (size_t)G * ((size_t)maxM * sizeof(float2) + (size_t)maxM * sizeof(float));
   cudaFuncSetAttribute(bring_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  bring_kernel<G><<<dim3(a.R, (a.B + G - 1) / G), kThreads, sm, s>>>(a);
+  bring_kernel<G><<<dim3(a.R, (a.B + G - 1) / G), kRingThreads, sm, s>>>(a);
 }
 
 void launch_batch_iteration(const BatchArgs &a, int maxM, int n_stiles, int *bstate, cudaStream_t s) {

@@ -117,7 +117,7 @@ static wf_status build_geometry(Plan *P) {
   // the chirp table is padded to the longest ring so that an index q < n is
   // always inside it, even on rings that never use it
   std::vector<double2> hs(hs_tot), ch(std::max<long long>(ch_tot, 4LL * ns), make_double2(0.0, 0.0));
-  std::vector<double2> tw(maxM / 2 > 0 ? maxM / 2 : 1);
+  std::vector<double2> tw(maxM);  // e^{-2 pi i k / Mmax}, k < Mmax (radix-4 stages reach 3 Mmax / 4)
   for (int i = 1; i <= ns; ++i) {
     const long long n = 4LL * i;
     for (long long q = 0; q < n; ++q) {
@@ -132,11 +132,10 @@ static wf_status build_geometry(Plan *P) {
       }
     }
   }
-  for (int k = 0; k < maxM / 2; ++k) {
+  for (int k = 0; k < maxM; ++k) {
     const double a = 2.0 * M_PI * (double)k / (double)maxM;
     tw[k] = make_double2(cos(a), -sin(a));
   }
-  if (maxM < 2) tw[0] = make_double2(1.0, 0.0);
   std::vector<double> xk(P->RP);
   for (int k = 0; k < P->RP; ++k) {
     const int i = k + 1;
@@ -218,6 +217,12 @@ wf_status Plan::alloc_work() {
   if ((st = dalloc((void **)&d_ctl, sizeof(Ctl)))) return st;
   if ((st = dalloc((void **)&d_d, sizeof(double) * npix))) return st;
   if ((st = dalloc((void **)&d_s, sizeof(double2) * nalm))) return st;
+  if ((st = dalloc((void **)&d_gain, sizeof(double) * npix))) return st;
+  if ((st = dalloc((void **)&d_gainlam, sizeof(double) * R))) return st;
+  {
+    std::vector<double> neg(R, -1.0);
+    WF_CUDA(cudaMemcpy(d_gainlam, neg.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
+  }
   WF_CUDA(cudaMemsetAsync(d_FS, 0, sizeof(double4_32a) * nF, stream));
   WF_CUDA(cudaMemsetAsync(d_FT, 0, sizeof(double4_32a) * nF, stream));
   WF_CUDA(cudaMallocHost((void **)&h_ctl, sizeof(Ctl)));
@@ -249,7 +254,7 @@ RingArgs Plan::ring_args() const {
   RingArgs a{};
   a.rings = d_rings; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;
   a.FS = d_FS; a.FT = d_FT; a.RP = RP; a.d = d_d; a.w = d_w; a.ring_part = d_ring_part; a.ctl = d_ctl;
-  a.lsht = lmax; a.omega = omega; a.tau = tau;
+  a.lsht = lmax; a.omega = omega; a.tau = tau; a.gain = d_gain; a.gainlam = d_gainlam;
   return a;
 }
 

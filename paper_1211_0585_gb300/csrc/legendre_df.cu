@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
     float4 *stE = ss;                            // (Er, Ei) as hi/lo
     float4 *stO = stE + RP;                      // (Or, Oi)
     float4 *stP = stO + RP;                      // (p1, p2)
+    float2 *stX = reinterpret_cast<float2 *>(stP + RP);  // x as double-float
     for (int k = threadIdx.x; k < RP; k += blockDim.x) {
       const double4_32a t = A.FT[(size_t)m * RP + k];
       const dfl er = df_from(t.x + t.z), ei = df_from(t.y + t.w);
@@ -229,6 +230,8 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
       stE[k] = make_float4(er.h, er.l, ei.h, ei.l);
       stO[k] = make_float4(orr.h, orr.l, oi.h, oi.l);
       stP[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const dfl xk = df_from(A.x[k]);
+      stX[k] = make_float2(xk.h, xk.l);
     }
     __syncthreads();
     for (int l0 = m; l0 <= L; l0 += kLB) {
@@ -239,7 +242,8 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
         const size_t mk = (size_t)m * RP + k;
         const int ls = D.ls[mk];
         if (ls >= l0 + kLB) continue;            // no evaluated term yet in this block
-        const dfl x = df_from(A.x[k]);
+        const float2 x2 = stX[k];
+        const dfl x = dfl{x2.x, x2.y};
         const float4 e4 = stE[k], o4 = stO[k], q4 = stP[k];
         dfl p1 = dfl{q4.x, q4.y}, p2 = dfl{q4.z, q4.w};
         if (ls + 1 >= l0) {                      // a start value falls in this block
@@ -387,7 +391,8 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
 // coefficients, or the per-ring-pair analysis state)
 static size_t leg_df_smem(int lmax, int RP) {
   const size_t Lp = (size_t)lmax + 1 + kLB;
-  const size_t q = Lp > 3 * (size_t)RP ? Lp : 3 * (size_t)RP;
+  const size_t st = 3 * (size_t)RP + ((size_t)RP + 1) / 2;
+  const size_t q = Lp > st ? Lp : st;
   return Lp * sizeof(double2) + (Lp + 1) * sizeof(float2) + q * sizeof(float4) + 16;
 }
 

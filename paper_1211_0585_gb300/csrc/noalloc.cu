@@ -70,7 +70,7 @@ Layout layout_for(int nside, int lmax) {
   L.hs = o;    o = align256(o + sizeof(double2) * hs);
   L.chirp = o; o = align256(o + sizeof(double2) * (ch > 4LL * nside ? ch : 4LL * nside));
   L.B = o;     o = align256(o + sizeof(double2) * (B > 0 ? B : 1));
-  L.tw = o;    o = align256(o + sizeof(double2) * (maxM / 2 > 0 ? maxM / 2 : 1));
+  L.tw = o;    o = align256(o + sizeof(double2) * maxM);
   L.x = o;     o = align256(o + sizeof(double) * RP);
   L.rec = o;   o = align256(o + sizeof(double2) * nalm);
   L.ls = o;    o = align256(o + sizeof(int) * nmk);
@@ -135,12 +135,11 @@ __global__ void noalloc_geometry_kernel(int nside, int maxM, RingDev *rings, dou
     hs_off += n;
     if (!pow2) ch_off += n;
   }
-  for (long long k = gid; k < maxM / 2; k += stride) {
+  for (long long k = gid; k < maxM; k += stride) {
     double s, co;
     sincospi(2.0 * (double)k / (double)maxM, &s, &co);
     tw[k] = make_double2(co, -s);
   }
-  if (gid == 0 && maxM < 2) tw[0] = make_double2(1.0, 0.0);
   for (long long k = gid; k < 2 * nside; k += stride) {
     const int i = (int)k + 1;
     x[k] = (i < nside) ? 1.0 - (double)i * i / (3.0 * (double)nside * nside)

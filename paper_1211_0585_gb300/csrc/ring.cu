@@ -9,10 +9,10 @@
 //     f_j  = sum_q G_q e^{+2 pi i j q / n},  G_q = e^{i q phi0} sum_{m = q mod n} (-1)^{(m-q)/n [shifted]} F_m
 //     T_m  = Omega e^{-i m phi0} sum_j u_j e^{-2 pi i j m / n}
 // (Sect. 2: the basis change between pixel space and harmonic space, here its
-// azimuthal half.) Power-of-two n use an in-place radix-2 FFT in shared
-// memory; other n (polar rings, n = 4i) use Bluestein's chirp-z convolution
-// with a power-of-two size M >= 2n - 1, whose filter spectrum is precomputed
-// per ring length.
+// azimuthal half.) Power-of-two n use the in-place radix-4/2 FFT of fft.cuh
+// in shared memory; other n (polar rings, n = 4i) use Bluestein's chirp-z
+// convolution with a power-of-two size M >= 2n - 1, whose filter spectrum is
+// precomputed per ring length.
 //
 // RING_ITER fuses the pixel-space half of one messenger iteration between the
 // two transforms: s_p = f_p, r_p = d_p - s_p, the chi^2 partials of Sect. 3
@@ -20,6 +20,7 @@
 // u_p = t_p - s_p = a_p r_p with a_p = lambda tau w_p / (1 + (lambda - 1) tau w_p).
 #include <cuda_runtime.h>
 
+#include "fft.cuh"
 #include "wf_internal.h"
 
 namespace wfk {
@@ -30,58 +31,6 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
-
-__device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
-
-// In-place radix-2 decimation in frequency: natural order in, bit-reversed out.
-// sign < 0: kernel e^{-2 pi i jk / M}; sign > 0: e^{+2 pi i jk / M} (unnormalised).
-__device__ void fft_dif(double2 *buf, int logM, int sign, const double2 *tw, int logMmax) {
-  const int M = 1 << logM;
-  for (int s = logM; s >= 1; --s) {
-    const int half = 1 << (s - 1);
-    const int tsh = logMmax - s;
-    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      double2 w = tw[pos << tsh];
-      if (sign > 0) w.y = -w.y;
-      const double2 a = buf[i0], b = buf[i1];
-      buf[i0] = cadd(a, b);
-      buf[i1] = cmul(csub(a, b), w);
-    }
-    __syncthreads();
-  }
-}
-
-// In-place radix-2 decimation in time: bit-reversed order in, natural out.
-__device__ void fft_dit(double2 *buf, int logM, int sign, const double2 *tw, int logMmax) {
-  const int M = 1 << logM;
-  for (int s = 1; s <= logM; ++s) {
-    const int half = 1 << (s - 1);
-    const int tsh = logMmax - s;
-    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      double2 w = tw[pos << tsh];
-      if (sign > 0) w.y = -w.y;
-      const double2 a = buf[i0], b = cmul(buf[i1], w);
-      buf[i0] = cadd(a, b);
-      buf[i1] = csub(a, b);
-    }
-    __syncthreads();
-  }
-}
-
-// Bluestein core: on entry buf[0..n) holds x_j c_j (c_j = e^{-i pi j^2 / n}),
-// buf[n..M) zero; on exit buf[k] (natural order) = sum_j x_j c_j conj(c_{k-j}),
-// so that DFT_n(x)_k = c_k buf[k] for k < n.
-__device__ void bluestein_conv(double2 *buf, int logM, const double2 *Bf, const double2 *tw, int logMmax) {
-  const int M = 1 << logM;
-  fft_dif(buf, logM, -1, tw, logMmax);
-  for (int i = threadIdx.x; i < M; i += blockDim.x) buf[i] = cmul(buf[i], Bf[i]);
-  __syncthreads();
-  fft_dit(buf, logM, +1, tw, logMmax);
-}
 
 // Deterministic block sum of two doubles (fixed tree); result valid in thread 0.
 __device__ void block_sum2(double &a, double &b, double *red) {
@@ -100,7 +49,7 @@ __device__ void block_sum2(double &a, double &b, double *red) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) ring_kernel(const RingArgs A) {
+__global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
   extern __shared__ double2 smem[];
   const int r = blockIdx.x;
   const RingDev rg = A.rings[r];
@@ -153,14 +102,14 @@ __global__ void __launch_bounds__(kThreads) ring_kernel(const RingArgs A) {
     }
     __syncthreads();
     if (rg.blue) {
-      bluestein_conv(buf, rg.logM, Bf, A.tw, A.logMmax);
+      bluestein4<OpsF64, 1>(buf, M, rg.logM, Bf, A.tw, A.logMmax);
     } else {
-      fft_dif(buf, rg.logM, +1, A.tw, A.logMmax);
+      fft_dif4<OpsF64, 1>(buf, M, rg.logM, +1, A.tw, A.logMmax);
     }
     // pixel values: Re of the inverse DFT
     if (MODE == RING_SYNTH) {
       for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const double f = rg.blue ? cmul(ch[p], buf[p]).x : buf[bitrev(p, rg.logM)].x;
+        const double f = rg.blue ? cmul(ch[p], buf[p]).x : buf[digitrev(p, rg.logM)].x;
         A.map_out[rg.off + p] = f;
       }
       return;
@@ -169,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) ring_kernel(const RingArgs A) {
     double c2n = 0.0, c2l = 0.0;
     const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const double s = rg.blue ? cmul(ch[p], buf[p]).x : buf[bitrev(p, rg.logM)].x;
+      const double s = rg.blue ? cmul(ch[p], buf[p]).x : buf[digitrev(p, rg.logM)].x;
       const double w = A.w[rg.off + p];
       const double res = A.d[rg.off + p] - s;
       const double wr2 = w * res * res;
@@ -194,11 +143,11 @@ __global__ void __launch_bounds__(kThreads) ring_kernel(const RingArgs A) {
     for (int p = threadIdx.x; p < M; p += blockDim.x)
       buf[p] = p < n ? make_double2(ureal[p] * ch[p].x, ureal[p] * ch[p].y) : make_double2(0.0, 0.0);
     __syncthreads();
-    bluestein_conv(buf, rg.logM, Bf, A.tw, A.logMmax);
+    bluestein4<OpsF64, 1>(buf, M, rg.logM, Bf, A.tw, A.logMmax);
   } else {
-    for (int p = threadIdx.x; p < n; p += blockDim.x) buf[bitrev(p, rg.logM)] = make_double2(ureal[p], 0.0);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) buf[digitrev(p, rg.logM)] = make_double2(ureal[p], 0.0);
     __syncthreads();
-    fft_dit(buf, rg.logM, -1, A.tw, A.logMmax);
+    fft_dit4<OpsF64, 1>(buf, M, rg.logM, -1, A.tw, A.logMmax);
   }
   // ---- unfold residues to m = 0 .. L, apply e^{-i m phi0} and Omega
   for (int m = threadIdx.x; m <= L; m += blockDim.x) {
@@ -215,10 +164,10 @@ __global__ void __launch_bounds__(kThreads) ring_kernel(const RingArgs A) {
 }
 
 // Bluestein filter spectrum per ring length: b_q = conj(c_q) for |q| < n
-// (wrapped into [0, M)), transformed by the DIF FFT (so stored bit-reversed)
+// (wrapped into [0, M)), transformed by the DIF FFT (so stored digit-reversed)
 // and scaled by 1/M. One CTA per ring; only the first ring of each length
 // (the north ring of a polar pair) writes.
-__global__ void __launch_bounds__(kThreads) bluestein_setup_kernel(const RingDev *rings, const double2 *tw,
+__global__ void __launch_bounds__(kRingThreads) bluestein_setup_kernel(const RingDev *rings, const double2 *tw,
                                                                    int logMmax, const double2 *chirp,
                                                                    double2 *B) {
   extern __shared__ double2 smem[];
@@ -233,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) bluestein_setup_kernel(const RingDev
     smem[q] = v;
   }
   __syncthreads();
-  fft_dif(smem, rg.logM, -1, tw, logMmax);
+  fft_dif4<OpsF64, 1>(smem, M, rg.logM, -1, tw, logMmax);
   const double inv = 1.0 / (double)M;
   for (int q = threadIdx.x; q < M; q += blockDim.x)
     B[rg.B_off + q] = make_double2(smem[q].x * inv, smem[q].y * inv);
@@ -247,15 +196,15 @@ void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode) {
   switch (mode) {
     case RING_SYNTH:
       cudaFuncSetAttribute(ring_kernel<RING_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_kernel<RING_SYNTH><<<R, kThreads, sm, s>>>(a);
+      ring_kernel<RING_SYNTH><<<R, kRingThreads, sm, s>>>(a);
       break;
     case RING_ANALYSIS:
       cudaFuncSetAttribute(ring_kernel<RING_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_kernel<RING_ANALYSIS><<<R, kThreads, sm, s>>>(a);
+      ring_kernel<RING_ANALYSIS><<<R, kRingThreads, sm, s>>>(a);
       break;
     default:
       cudaFuncSetAttribute(ring_kernel<RING_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_kernel<RING_ITER><<<R, kThreads, sm, s>>>(a);
+      ring_kernel<RING_ITER><<<R, kRingThreads, sm, s>>>(a);
       break;
   }
 }
@@ -264,7 +213,7 @@ void launch_bluestein_setup(const RingDev *rings, int R, const double2 *tw, int 
                             double2 *B, int maxM, cudaStream_t s) {
   const size_t sm = (size_t)maxM * sizeof(double2);
   cudaFuncSetAttribute(bluestein_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  bluestein_setup_kernel<<<R, kThreads, sm, s>>>(rings, tw, logMmax, chirp, B);
+  bluestein_setup_kernel<<<R, kRingThreads, sm, s>>>(rings, tw, logMmax, chirp, B);
 }
 
 }  // namespace wfk

@@ -11,6 +11,7 @@
 // tables when the plan is built.
 #include <cuda_runtime.h>
 
+#include "fft.cuh"
 #include "wf_internal.h"
 
 namespace wfk {
@@ -58,52 +59,6 @@ __device__ __forceinline__ float4 cmul(float4 a, float4 b) {
 __device__ __forceinline__ float4 cconj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
 __device__ __forceinline__ float4 cneg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
 
-__device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
-
-__device__ void fft_dif(float4 *buf, int logM, int sign, const float4 *tw, int logMmax) {
-  const int M = 1 << logM;
-  for (int s = logM; s >= 1; --s) {
-    const int half = 1 << (s - 1);
-    const int tsh = logMmax - s;
-    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      float4 w = tw[pos << tsh];
-      if (sign > 0) w = cconj(w);
-      const float4 a = buf[i0], b = buf[i1];
-      buf[i0] = cadd(a, b);
-      buf[i1] = cmul(csub(a, b), w);
-    }
-    __syncthreads();
-  }
-}
-
-__device__ void fft_dit(float4 *buf, int logM, int sign, const float4 *tw, int logMmax) {
-  const int M = 1 << logM;
-  for (int s = 1; s <= logM; ++s) {
-    const int half = 1 << (s - 1);
-    const int tsh = logMmax - s;
-    for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-      const int pos = t & (half - 1);
-      const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-      float4 w = tw[pos << tsh];
-      if (sign > 0) w = cconj(w);
-      const float4 a = buf[i0], b = cmul(buf[i1], w);
-      buf[i0] = cadd(a, b);
-      buf[i1] = csub(a, b);
-    }
-    __syncthreads();
-  }
-}
-
-__device__ void bluestein_conv(float4 *buf, int logM, const float4 *Bf, const float4 *tw, int logMmax) {
-  const int M = 1 << logM;
-  fft_dif(buf, logM, -1, tw, logMmax);
-  for (int i = threadIdx.x; i < M; i += blockDim.x) buf[i] = cmul(buf[i], Bf[i]);
-  __syncthreads();
-  fft_dit(buf, logM, +1, tw, logMmax);
-}
-
 __device__ void block_sum2(double &a, double &b, double *red) {
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -122,7 +77,7 @@ __device__ void block_sum2(double &a, double &b, double *red) {
 }  // namespace
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) ring_df_kernel(const RingArgs A, const RingDfArgs T) {
+__global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A, const RingDfArgs T) {
   extern __shared__ float4 rsm[];
   const int r = blockIdx.x;
   const RingDev rg = A.rings[r];
@@ -170,23 +125,25 @@ __global__ void __launch_bounds__(kThreads) ring_df_kernel(const RingArgs A, con
       for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    if (rg.blue) bluestein_conv(buf, rg.logM, Bf, T.tw, A.logMmax);
-    else fft_dif(buf, rg.logM, +1, T.tw, A.logMmax);
+    if (rg.blue) bluestein4<OpsDF, 1>(buf, M, rg.logM, Bf, T.tw, A.logMmax);
+    else fft_dif4<OpsDF, 1>(buf, M, rg.logM, +1, T.tw, A.logMmax);
     if (MODE == RING_SYNTH) {
       for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const dd f = rg.blue ? RE(cmul(ch[p], buf[p])) : RE(buf[bitrev(p, rg.logM)]);
+        const dd f = rg.blue ? RE(cmul(ch[p], buf[p])) : RE(buf[digitrev(p, rg.logM)]);
         A.map_out[rg.off + p] = todbl(f);
       }
       return;
     }
     double c2n = 0.0, c2l = 0.0;
+    const bool fresh = A.gainlam[r] == lam;   // gains of this ring already at this lambda
     const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const dd sdf = rg.blue ? RE(cmul(ch[p], buf[p])) : RE(buf[bitrev(p, rg.logM)]);
+      const dd sdf = rg.blue ? RE(cmul(ch[p], buf[p])) : RE(buf[digitrev(p, rg.logM)]);
       const double s = todbl(sdf);
       const double w = A.w[rg.off + p];
       const double res = A.d[rg.off + p] - s;
-      const double g = w / (1.0 + l1t * w);
+      const double g = fresh ? A.gain[rg.off + p] : w / (1.0 + l1t * w);
+      if (!fresh) A.gain[rg.off + p] = g;
       c2n += w * res * res;
       c2l += g * res * res;
       ureal[p] = lt * g * res;
@@ -195,6 +152,7 @@ __global__ void __launch_bounds__(kThreads) ring_df_kernel(const RingArgs A, con
     if (threadIdx.x == 0) {
       A.ring_part[2 * r] = c2n;
       A.ring_part[2 * r + 1] = c2l;
+      if (!fresh) A.gainlam[r] = lam;   // after block_sum2's barrier: every gain of the ring is written
     }
     __syncthreads();
   } else {
@@ -213,14 +171,14 @@ __global__ void __launch_bounds__(kThreads) ring_df_kernel(const RingArgs A, con
       }
     }
     __syncthreads();
-    bluestein_conv(buf, rg.logM, Bf, T.tw, A.logMmax);
+    bluestein4<OpsDF, 1>(buf, M, rg.logM, Bf, T.tw, A.logMmax);
   } else {
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
       const dd u = mk(ureal[p]);
-      buf[bitrev(p, rg.logM)] = make_float4(u.h, u.l, 0.f, 0.f);
+      buf[digitrev(p, rg.logM)] = make_float4(u.h, u.l, 0.f, 0.f);
     }
     __syncthreads();
-    fft_dit(buf, rg.logM, -1, T.tw, A.logMmax);
+    fft_dit4<OpsDF, 1>(buf, M, rg.logM, -1, T.tw, A.logMmax);
   }
   for (int m = threadIdx.x; m <= L; m += blockDim.x) {
     const int q = m % n, j = m / n;
@@ -255,15 +213,15 @@ void launch_ring_df(const RingArgs &a, const RingDfArgs &t, int R, int maxM, cud
   switch (mode) {
     case RING_SYNTH:
       cudaFuncSetAttribute(ring_df_kernel<RING_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_df_kernel<RING_SYNTH><<<R, kThreads, sm, s>>>(a, t);
+      ring_df_kernel<RING_SYNTH><<<R, kRingThreads, sm, s>>>(a, t);
       break;
     case RING_ANALYSIS:
       cudaFuncSetAttribute(ring_df_kernel<RING_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_df_kernel<RING_ANALYSIS><<<R, kThreads, sm, s>>>(a, t);
+      ring_df_kernel<RING_ANALYSIS><<<R, kRingThreads, sm, s>>>(a, t);
       break;
     default:
       cudaFuncSetAttribute(ring_df_kernel<RING_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_df_kernel<RING_ITER><<<R, kThreads, sm, s>>>(a, t);
+      ring_df_kernel<RING_ITER><<<R, kRingThreads, sm, s>>>(a, t);
       break;
   }
 }

@@ -19,7 +19,9 @@
 
 namespace wfk {
 
-constexpr int kThreads = 256;       // block size of every per-ring / per-m kernel
+constexpr int kThreads = 256;       // block size of the per-m Legendre kernels
+constexpr int kRingThreads = 512;   // block size of the ring (FFT) kernels: one CTA per ring fills
+                                    // an SM's shared memory, so its own warps must hide the latency
 constexpr int kLB = 16;             // l values per block of the analysis reduction
 constexpr int kStartExp = -100;     // Legendre terms below 2^-100 are not evaluated
 
@@ -80,6 +82,8 @@ struct RingArgs {
   const Ctl *ctl;         // RING_ITER: lambda, lsht, done
   int lsht;               // standalone modes
   double omega, tau;
+  double *gain;           // [npix] cached w / (1 + (lambda - 1) tau w) (double-float ring kernel)
+  double *gainlam;        // [R] lambda the cached gains of each ring belong to (-1: none)
 };
 
 struct LegArgs {

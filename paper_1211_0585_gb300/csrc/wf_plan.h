@@ -51,6 +51,7 @@ struct Plan : wf_plan_s {
   wf_iter_record *d_hist = nullptr;
   int hist_cap = 0;
   double *d_d = nullptr;
+  double *d_gain = nullptr, *d_gainlam = nullptr;  // cached Eq. 3 gains per pixel, lambda per ring
   double2 *d_s = nullptr;
   bool fs_valid = false;
   int fs_lsht = -1;
