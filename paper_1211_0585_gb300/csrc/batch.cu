@@ -36,7 +36,7 @@ size_t Engine::bytes_needed(int nside, int lmax, int nslots) {
   for (int m = 0; m <= lmax; ++m) ntiles += (size_t)(lmax - m) / 64 + 1;
   return nalm * RP * sizeof(float) + 2 * nF * nslots * sizeof(float4) + nalm * nslots * sizeof(float2) +
          2 * npix * nslots * sizeof(double) + nslots * (size_t)(lmax + 1) * sizeof(double) +
-         nslots * nalm * sizeof(double2) + nslots * R * 2 * sizeof(double) + nslots * ntiles * 3 * sizeof(double) +
+         nslots * nalm * (sizeof(double2) + sizeof(float4)) + nslots * (size_t)(lmax + 1) * (sizeof(float2) + sizeof(float)) + nslots * R * 2 * sizeof(double) + nslots * ntiles * 3 * sizeof(double) +
          (ntiles + nF / 32 + 64) * sizeof(int2) + nslots * (sizeof(Ctl) + sizeof(wf_iter_record) + 8);
 }
 
@@ -65,7 +65,7 @@ BatchArgs Engine::args() const {
   a.lam = lam;
   a.lmax = geo->lmax; a.RP = geo->RP; a.R = geo->R; a.B = B;
   a.npix = geo->npix; a.nalm = geo->nalm; a.omega = geo->omega;
-  a.d = d; a.w = w; a.cl = cl; a.d32 = d32; a.w32 = w32; a.s = s; a.FS = FS; a.FT = FT; a.SP = SP;
+  a.d = d; a.w = w; a.cl = cl; a.d32 = d32; a.w32 = w32; a.s = s; a.sdf = sdf; a.fdf = fdf; a.icl = icl; a.FS = FS; a.FT = FT; a.SP = SP;
   a.ctl = ctl; a.active = active; a.ring_part = ring_part; a.m_part = m_part;
   a.ntiles = ntiles; a.tiles = tiles; a.stiles = stiles; a.bstate = bstate; a.last = last;
   return a;
@@ -88,7 +88,8 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
       (st = dalloc((void **)&d, sizeof(double) * npix * B)) || (st = dalloc((void **)&w, sizeof(double) * npix * B)) ||
       (st = dalloc((void **)&d32, sizeof(float) * npix * B)) || (st = dalloc((void **)&w32, sizeof(float) * npix * B)) ||
       (st = dalloc((void **)&cl, sizeof(double) * (lmax + 1) * B)) ||
-      (st = dalloc((void **)&s, sizeof(double2) * nalm * B)) || (st = dalloc((void **)&ctl, sizeof(Ctl) * B)) ||
+      (st = dalloc((void **)&s, sizeof(double2) * nalm * B)) || (st = dalloc((void **)&sdf, sizeof(float4) * nalm * B)) ||
+      (st = dalloc((void **)&fdf, sizeof(float2) * (lmax + 1) * B)) || (st = dalloc((void **)&icl, sizeof(float) * (lmax + 1) * B)) || (st = dalloc((void **)&ctl, sizeof(Ctl) * B)) ||
       (st = dalloc((void **)&active, sizeof(int) * B)) ||
       (st = dalloc((void **)&ring_part, sizeof(double) * 2 * R * B)) ||
       (st = dalloc((void **)&m_part, sizeof(double) * 3 * (size_t)ntiles * B)) ||
@@ -105,6 +106,9 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ENG_CUDA(cudaMemsetAsync(FS, 0, sizeof(float4) * nF * B, stream));
   ENG_CUDA(cudaMemsetAsync(FT, 0, sizeof(float4) * nF * B, stream));
   ENG_CUDA(cudaMemsetAsync(s, 0, sizeof(double2) * nalm * B, stream));
+  ENG_CUDA(cudaMemsetAsync(sdf, 0, sizeof(float4) * nalm * B, stream));
+  ENG_CUDA(cudaMemsetAsync(fdf, 0, sizeof(float2) * (lmax + 1) * B, stream));
+  ENG_CUDA(cudaMemsetAsync(icl, 0, sizeof(float) * (lmax + 1) * B, stream));
   ENG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) * B, stream));
   ENG_CUDA(cudaMemsetAsync(active, 0, sizeof(int) * B, stream));
   ENG_CUDA(cudaMemsetAsync(last, 0, sizeof(wf_iter_record) * B, stream));
@@ -153,6 +157,12 @@ wf_status Engine::load_slot_host(int b, const double *d_host, const double *w_ho
 wf_status Engine::release_slot(int b) {
   h_active[b] = 0;
   ENG_CUDA(cudaMemcpyAsync(active + b, h_active + b, sizeof(int), cudaMemcpyHostToDevice, stream));
+  return WF_OK;
+}
+
+wf_status Engine::export_slot(int b) {
+  launch_batch_export_slot(args(), b, stream);
+  ENG_CUDA(cudaGetLastError());
   return WF_OK;
 }
 
@@ -242,6 +252,7 @@ wf_status solve_mixed(Plan *P, int nrhs, const double *dsrc, int d_on_device, do
       const int i = slot_of[b];
       const double ms =
           std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_in[b]).count();
+      if ((st = E->export_slot(b))) return st;
       ENG_CUDA(cudaMemcpyAsync(alm_out + (size_t)i * 2 * P->nalm, E->s + (size_t)b * P->nalm,
                                sizeof(double2) * P->nalm,
                                alm_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, E->stream));

@@ -27,7 +27,10 @@ struct Engine {
   float2 *SP = nullptr;
   double *d = nullptr, *w = nullptr, *cl = nullptr;
   float *d32 = nullptr, *w32 = nullptr;
-  double2 *s = nullptr;
+  double2 *s = nullptr;      // exported a_lm of finished slots
+  float4 *sdf = nullptr;     // double-float state
+  float2 *fdf = nullptr;
+  float *icl = nullptr;
   Ctl *ctl = nullptr;
   int *active = nullptr;
   double *ring_part = nullptr, *m_part = nullptr;
@@ -56,6 +59,8 @@ struct Engine {
   wf_status step();                    // one graph launch (graph_iters iterations), then mirror ctl to host
   wf_status sync_host();               // wait for the last step's mirrors
   wf_status release_slot(int b);
+  // Write slot b's double-float state as double a_lm into s + b nalm (stream-ordered).
+  wf_status export_slot(int b);
   static size_t bytes_needed(int nside, int lmax, int nslots);
 };
 

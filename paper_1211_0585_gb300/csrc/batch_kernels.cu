@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) 
   else fft_dif4<OpsF32, G>(buf, M, rg.logM, +1, A.twf, A.logMmax);
 
   // Eq. 3 per pixel and the chi^2 partials in FP32 (per-thread sums of at
-  // most 16 terms), the block reduction in double
+  // most 16 terms, warp sums by shuffles), the sum over warps in double
   float c2n[G], c2l[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) { c2n[g] = 0.f; c2l[g] = 0.f; }
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      double a = c2n[g], bsum = c2l[g];
+      float a = c2n[g], bsum = c2l[g];   // warp sums in FP32, the per-warp partials in double
       for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
@@ -314,38 +314,38 @@ __global__ void __launch_bounds__(256) bana_kernel(const BatchArgs A) {
       __syncthreads();
     }
   }
-  // epilogue: Eq. 4 per (l, slot) in double, prior chi^2 / increment / norm partials
+  // epilogue: Eq. 4 per (l, slot) on the double-float state (f_l from the
+  // per-iteration table, 0 above the slot's band limit and where C_l = 0),
+  // prior chi^2 / increment / norm partials in FP32 (all on the FP32 pipe)
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) {
     const int bb = 4 * cg + jj;      // slot of columns 8 cg + 2 jj, + 1
-    double c2 = 0.0, inc = 0.0, nrm = 0.0;
+    float c2 = 0.f, inc = 0.f, nrm = 0.f;
     if (bb < B && A.active[bb] && !A.ctl[bb].done) {
-      const Ctl &c = A.ctl[bb];
-      const int Lb = c.lsht;
-      const double lto = c.lambda * c.tau * c.omega;
-      const double *clb = A.cl + (size_t)bb * (lmax + 1);
-      double2 *sb = A.s + (size_t)bb * A.nalm;
+      const float2 *fb = A.fdf + (size_t)bb * (lmax + 1);
+      const float *ib = A.icl + (size_t)bb * (lmax + 1);
+      float4 *sb = A.sdf + (size_t)bb * A.nalm;
+      const float wgt = (m == 0) ? 1.f : 2.f;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int l = l0 + par + 2 * (4 * rg + i);
         if (l > lmax) continue;
         const size_t idx = aidx(lmax, l, m);
-        const double2 so = sb[idx];
-        const double cl = clb[l];
-        double2 sn = make_double2(0.0, 0.0);
-        if (live && l <= Lb && m <= Lb && cl > 0.0) {
-          const double f = cl / (cl + lto);
-          const double tr = (double)ah[i][2 * jj] + (double)al[i][2 * jj];
-          const double ti = (double)ah[i][2 * jj + 1] + (double)al[i][2 * jj + 1];
-          sn = make_double2(f * (so.x + tr), f * (so.y + ti));
+        const float4 so = sb[idx];
+        float4 sn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live) {
+          const float2 f2 = fb[l];
+          const dfl f = dfl{f2.x, f2.y};
+          const dfl re = df_mul(f, df_add(dfl{so.x, so.y}, dfl{ah[i][2 * jj], al[i][2 * jj]}));
+          const dfl im = df_mul(f, df_add(dfl{so.z, so.w}, dfl{ah[i][2 * jj + 1], al[i][2 * jj + 1]}));
+          sn = make_float4(re.h, re.l, im.h, im.l);
         }
-        const double wgt = (m == 0) ? 1.0 : 2.0;
-        if (cl > 0.0) c2 += wgt * (so.x * so.x + so.y * so.y) / cl;
-        const double dx = sn.x - so.x, dy = sn.y - so.y;
+        c2 += wgt * (so.x * so.x + so.z * so.z) * ib[l];
+        const float dx = (sn.x - so.x) + (sn.y - so.y), dy = (sn.z - so.z) + (sn.w - so.w);
         inc += wgt * (dx * dx + dy * dy);
-        nrm += wgt * (sn.x * sn.x + sn.y * sn.y);
+        nrm += wgt * (sn.x * sn.x + sn.z * sn.z);
         sb[idx] = sn;
-        A.SP[idx * B + bb] = make_float2((float)sn.x, (float)sn.y);
+        A.SP[idx * B + bb] = make_float2(sn.x, sn.z);
       }
     }
     if (bb < kBatchMax) {
@@ -501,7 +501,36 @@ __global__ void bzero_slot_kernel(const BatchArgs A, int b) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += (long long)gridDim.x * blockDim.x)
     A.FS[i * A.B + b] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nalm; i += (long long)gridDim.x * blockDim.x)
-    A.s[(size_t)b * A.nalm + i] = make_double2(0.0, 0.0);
+    A.sdf[(size_t)b * A.nalm + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// the double-float state of slot b as double a_lm (export of a finished solve)
+__global__ void bexport_slot_kernel(const BatchArgs A, int b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nalm; i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = A.sdf[(size_t)b * A.nalm + i];
+    A.s[(size_t)b * A.nalm + i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+}
+
+// per-iteration filter table f_l(lambda_b) = C_l / (C_l + lambda tau Omega)
+// (0 above the slot's band limit or where C_l = 0) and 1 / C_l (0 where C_l = 0)
+__global__ void bfilter_kernel(const BatchArgs A) {
+  const int b = blockIdx.x;
+  if (!A.active[b] || A.ctl[b].done) return;
+  const Ctl &c = A.ctl[b];
+  const double lto = c.lambda * c.tau * c.omega;
+  const double *clb = A.cl + (size_t)b * (A.lmax + 1);
+  for (int l = threadIdx.x; l <= A.lmax; l += blockDim.x) {
+    const double cl = clb[l];
+    const double f = (cl > 0.0 && l <= c.lsht) ? cl / (cl + lto) : 0.0;
+    const dfl fd = df_from(f);
+    A.fdf[(size_t)b * (A.lmax + 1) + l] = make_float2(fd.h, fd.l);
+    A.icl[(size_t)b * (A.lmax + 1) + l] = cl > 0.0 ? (float)(1.0 / cl) : 0.f;
+  }
+}
+
+void launch_batch_export_slot(const BatchArgs &a, int b, cudaStream_t s) {
+  bexport_slot_kernel<<<256, 256, 0, s>>>(a, b);
 }
 
 void launch_lam_table(const double *x, const LegDfArgs &D, int lmax, int RP, float *lam, cudaStream_t s) {
@@ -541,6 +570,7 @@ void launch_batch_iteration(const BatchArgs &a, int maxM, int n_stiles, int *bst
   if (G == 4) launch_bring<4>(a, maxM, s);
   else if (G == 2) launch_bring<2>(a, maxM, s);
   else launch_bring<1>(a, maxM, s);
+  bfilter_kernel<<<a.B, 256, 0, s>>>(a);
   bana_kernel<<<a.ntiles, 256, 0, s>>>(a);
   bsyn_kernel<<<n_stiles, 256, 0, s>>>(a);
   bctl_kernel<<<a.B, 256, 0, s>>>(a);

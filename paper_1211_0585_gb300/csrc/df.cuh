@@ -17,6 +17,25 @@ __device__ __forceinline__ dfl df_from(double v) {
 
 __device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
 
+// a + b (two_sum of the high parts, low parts added, renormalised)
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  const float r = s + e;
+  return {r, e - (r - s)};
+}
+
+// a * b (two_prod of the high parts plus the cross terms, renormalised)
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  const float r = p + e;
+  return {r, e - (r - p)};
+}
+
 // S + C += a * b: compensated dot-product step (Ogita, Rump and Oishi,
 // "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005)
 __device__ __forceinline__ void dot2_acc(float &S, float &C, dfl a, dfl b) {

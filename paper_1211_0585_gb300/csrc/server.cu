@@ -230,6 +230,7 @@ void worker_loop(wf_server_s *S) {
         const Ctl &c = R->engine->h_ctl[b];
         const wf_iter_record &last = R->engine->h_last[b];
         r->alm.resize(2 * (size_t)R->shape->nalm);
+        R->engine->export_slot(b);
         cudaMemcpyAsync(r->alm.data(), R->engine->s + (size_t)b * R->shape->nalm,
                         sizeof(double2) * R->shape->nalm, cudaMemcpyDeviceToHost, R->engine->stream);
         cudaStreamSynchronize(R->engine->stream);

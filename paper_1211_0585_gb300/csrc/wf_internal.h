@@ -129,8 +129,11 @@ struct BatchArgs {
   double omega;
   const double *d, *w, *cl;  // [B][npix], [B][npix], [B][lmax+1]
   float *d32, *w32;          // [B][npix] FP32 copies read by the mixed-precision ring stage
-  double2 *s;                // [B][nalm] state
-  float4 *FS, *FT;           // [(m RP + k) B + b] (north re, north im, south re, south im)
+  double2 *s;                // [B][nalm] exported a_lm of finished slots
+  float4 *sdf;               // [B][nalm] state, double-float (re hi, re lo, im hi, im lo)
+  float2 *fdf;               // [B][lmax+1] Eq. 4 filter f_l(lambda_b) of this iteration, double-float
+  float *icl;                // [B][lmax+1] 1 / C_l (0 where C_l = 0)
+  float4 *FS, *FT;        // [(m RP + k) B + b] (north re, north im, south re, south im)
   float2 *SP;                // [nalm][B] synthesis coefficients
   Ctl *ctl;                  // [B]
   const int *active;         // [B]
@@ -148,6 +151,7 @@ void launch_batch_iteration(const BatchArgs &a, int maxM, int n_stiles, int *bst
 void launch_batch_state(const BatchArgs &a, int *bstate, cudaStream_t s);
 void launch_batch_zero_slot(const BatchArgs &a, int b, cudaStream_t s);
 void launch_batch_convert_slot(const BatchArgs &a, int b, cudaStream_t s);
+void launch_batch_export_slot(const BatchArgs &a, int b, cudaStream_t s);
 
 void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode);
 void launch_ring_df(const RingArgs &a, const RingDfArgs &t, int R, int maxM, cudaStream_t s, int mode);
