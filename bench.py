@@ -167,7 +167,8 @@ def run_ours(args):
         dist.barrier()
     value = world * args.steps / total
     graph_iters = opts.graph_iters
-    launches_per_solve = [math.ceil(i / graph_iters) * graph_iters * 3 for i in iters]
+    per_iter = P.kernels_per_iteration()
+    launches_per_solve = [math.ceil(i / graph_iters) * graph_iters * per_iter for i in iters]
 
     # SHT pair at full lmax (alm2map + map2alm), events on the stream
     m2 = torch.empty_like(dmap)

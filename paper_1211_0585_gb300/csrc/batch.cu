@@ -34,10 +34,16 @@ size_t Engine::bytes_needed(int nside, int lmax, int nslots) {
   const size_t nalm = nalm_of(lmax), nF = (size_t)(lmax + 1) * RP;
   size_t ntiles = 0;
   for (int m = 0; m <= lmax; ++m) ntiles += (size_t)(lmax - m) / 64 + 1;
-  return nalm * RP * sizeof(float) + 2 * nF * nslots * sizeof(float4) + nalm * nslots * sizeof(float2) +
-         2 * npix * nslots * sizeof(double) + nslots * (size_t)(lmax + 1) * sizeof(double) +
-         nslots * nalm * (sizeof(double2) + sizeof(float4)) + nslots * (size_t)(lmax + 1) * (sizeof(float2) + sizeof(float)) + nslots * R * 2 * sizeof(double) + nslots * ntiles * 3 * sizeof(double) +
-         (ntiles + nF / 32 + 64) * sizeof(int2) + nslots * (sizeof(Ctl) + sizeof(wf_iter_record) + 8);
+  const size_t B = (size_t)nslots, L1 = (size_t)lmax + 1;
+  const size_t tables = nalm * RP * sizeof(float)                    // Lambda table
+                        + sizeof(float2) * (8 * (size_t)nside + 16 * (size_t)nside * nside);  // FP32 FFT tables (bound)
+  const size_t per_slot = 2 * nF * sizeof(float4)                     // FS, FT
+                          + nalm * (sizeof(float2) + sizeof(double2) + sizeof(float4))  // SP, s, sdf
+                          + npix * 2 * (sizeof(double) + sizeof(float))                  // d, w and FP32 copies
+                          + L1 * (sizeof(double) + sizeof(float2) + sizeof(float))       // C_l, filter tables
+                          + R * 2 * sizeof(double) + ntiles * 3 * sizeof(double)         // partials
+                          + sizeof(Ctl) + sizeof(wf_iter_record) + 8;
+  return tables + B * per_slot + (ntiles + nF / 32 + 64) * sizeof(int2);
 }
 
 wf_status Engine::dalloc(void **p, size_t bytes) {
@@ -60,12 +66,16 @@ Engine::~Engine() {
 BatchArgs Engine::args() const {
   BatchArgs a{};
   a.rings = geo->d_rings;
+  a.order = geo->d_order;
+  a.first = 0;
   a.twf = geo->d_twf; a.hsf = geo->d_hsf; a.chf = geo->d_chf; a.Bf = geo->d_Bf;
+  a.tw2 = tw2; a.Bf2 = Bf2;
   a.logMmax = geo->logMmax;
   a.lam = lam;
   a.lmax = geo->lmax; a.RP = geo->RP; a.R = geo->R; a.B = B;
   a.npix = geo->npix; a.nalm = geo->nalm; a.omega = geo->omega;
-  a.d = d; a.w = w; a.cl = cl; a.d32 = d32; a.w32 = w32; a.s = s; a.sdf = sdf; a.fdf = fdf; a.icl = icl; a.FS = FS; a.FT = FT; a.SP = SP;
+  a.d = d; a.w = w; a.cl = cl; a.dw32 = dw32;
+  a.s = s; a.sdf = sdf; a.fdf = fdf; a.icl = icl; a.FS = FS; a.FT = FT; a.SP = SP;
   a.ctl = ctl; a.active = active; a.ring_part = ring_part; a.m_part = m_part;
   a.ntiles = ntiles; a.tiles = tiles; a.stiles = stiles; a.bstate = bstate; a.last = last;
   return a;
@@ -83,10 +93,12 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ntiles = (int)ana.size();
   nstiles = (int)syn.size();
   wf_status st;
-  if ((st = dalloc((void **)&lam, sizeof(float) * nalm * RP)) || (st = dalloc((void **)&FS, sizeof(float4) * nF * B)) ||
+  if ((st = dalloc((void **)&lam, sizeof(float) * nalm * RP)) ||
+      (st = dalloc((void **)&tw2, sizeof(float2) * std::max<long long>(geo->n_tw, 1))) ||
+      (st = dalloc((void **)&Bf2, sizeof(float2) * std::max<long long>(geo->n_B, 1))) || (st = dalloc((void **)&FS, sizeof(float4) * nF * B)) ||
       (st = dalloc((void **)&FT, sizeof(float4) * nF * B)) || (st = dalloc((void **)&SP, sizeof(float2) * nalm * B)) ||
       (st = dalloc((void **)&d, sizeof(double) * npix * B)) || (st = dalloc((void **)&w, sizeof(double) * npix * B)) ||
-      (st = dalloc((void **)&d32, sizeof(float) * npix * B)) || (st = dalloc((void **)&w32, sizeof(float) * npix * B)) ||
+      (st = dalloc((void **)&dw32, sizeof(float2) * npix * B)) ||
       (st = dalloc((void **)&cl, sizeof(double) * (lmax + 1) * B)) ||
       (st = dalloc((void **)&s, sizeof(double2) * nalm * B)) || (st = dalloc((void **)&sdf, sizeof(float4) * nalm * B)) ||
       (st = dalloc((void **)&fdf, sizeof(float2) * (lmax + 1) * B)) || (st = dalloc((void **)&icl, sizeof(float) * (lmax + 1) * B)) || (st = dalloc((void **)&ctl, sizeof(Ctl) * B)) ||
@@ -103,6 +115,8 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   std::fill(h_active, h_active + B, 0);
   ENG_CUDA(cudaMemcpyAsync(tiles, ana.data(), sizeof(int2) * ana.size(), cudaMemcpyHostToDevice, stream));
   ENG_CUDA(cudaMemcpyAsync(stiles, syn.data(), sizeof(int2) * syn.size(), cudaMemcpyHostToDevice, stream));
+  launch_hi_table(geo->d_twf, tw2, geo->n_tw, stream);
+  launch_hi_table(geo->d_Bf, Bf2, geo->n_B, stream);
   ENG_CUDA(cudaMemsetAsync(FS, 0, sizeof(float4) * nF * B, stream));
   ENG_CUDA(cudaMemsetAsync(FT, 0, sizeof(float4) * nF * B, stream));
   ENG_CUDA(cudaMemsetAsync(s, 0, sizeof(double2) * nalm * B, stream));
@@ -176,7 +190,7 @@ wf_status Engine::step() {
   if (!graph) {
     cudaGraph_t g;
     ENG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < graph_iters; ++i) launch_batch_iteration(args(), geo->maxM, nstiles, bstate, stream);
+    for (int i = 0; i < graph_iters; ++i) launch_batch_iteration(args(), geo->rclass.data(), (int)geo->rclass.size(), nstiles, bstate, stream);
     ENG_CUDA(cudaStreamEndCapture(stream, &g));
     cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
     cudaGraphDestroy(g);

@@ -23,10 +23,11 @@ struct Engine {
   std::vector<void *> allocs;
 
   float *lam = nullptr;
+  float2 *tw2 = nullptr, *Bf2 = nullptr;   // FP32 twiddle / Bluestein tables
   float4 *FS = nullptr, *FT = nullptr;
   float2 *SP = nullptr;
   double *d = nullptr, *w = nullptr, *cl = nullptr;
-  float *d32 = nullptr, *w32 = nullptr;
+  float2 *dw32 = nullptr;   // [B][npix] (d, w) in FP32 for the ring stage
   double2 *s = nullptr;      // exported a_lm of finished slots
   float4 *sdf = nullptr;     // double-float state
   float2 *fdf = nullptr;

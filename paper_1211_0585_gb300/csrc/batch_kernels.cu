@@ -13,6 +13,8 @@
 // controller run in double.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ctl.cuh"
 #include "df.cuh"
 #include "fft.cuh"
@@ -65,12 +67,22 @@ __global__ void lam_table_kernel(const double *xk, const LegDfArgs D, int lmax, 
 }
 
 // ---------------------------------------------------------------- ring stage
-// One CTA per (ring, group of G slots): the G slots share every twiddle load
-// and read their Fourier coefficients as one contiguous run of G float4.
+// One CTA per (ring, group of G slots). The ring values of every slot are
+// real, so two slots a, b share one complex FFT: the inverse transform of
+// Z = G_a + i G_b gives f_a + i f_b, and the forward transform of u_a + i u_b
+// gives Z with U_a = (Z_q + conj Z_{n-q}) / 2 and U_b = (Z_q - conj Z_{n-q}) / 2i.
+// The G / 2 packed arrays share every twiddle load, the pixel pass updates
+// them in place (the inverse transform's output order is the forward
+// transform's input order), and the G slots read their Fourier coefficients
+// as one contiguous run of G float4. Four CTAs of 128 threads per SM, so that
+// the FFT passes of one CTA overlap the global loads and stores of another.
+constexpr int kBringThreads = 128;
 template <int G>
-__global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs A) {
+  static_assert(G % 2 == 0, "slots are packed in pairs");
+  constexpr int P = G / 2;
   extern __shared__ float2 bsm[];
-  const int r = blockIdx.x, b0 = blockIdx.y * G;
+  const int r = A.order[A.first + blockIdx.x], b0 = blockIdx.y * G;
   const int B = A.B;
   // slots of this group that iterate (the group's live mask is uniform per CTA)
   bool on[G];
@@ -84,12 +96,11 @@ __global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) 
   if (!any) return;
   const RingDev rg = A.rings[r];
   const int n = rg.n, M = 1 << rg.logM;
-  float2 *buf = bsm;                                          // [G][M]
-  float *ureal = reinterpret_cast<float *>(bsm + G * M);      // [G][n]
-  __shared__ double red[kRingThreads / 32][2 * G];
+  float2 *buf = bsm;                                          // [P][M] (swizzled, px)
+  __shared__ double red[kBringThreads / 32][2 * G];
   const float4 *hs = A.hsf + rg.hs_off;
   const float4 *ch = A.chf + rg.ch_off;
-  const float4 *Bf = A.Bf + rg.B_off;
+  const float2 *Bf = A.Bf2 + rg.B_off;
   const int k = rg.pair, slot = rg.side;
   int Lg[G];
   float lt[G], l1t[G];
@@ -108,7 +119,7 @@ __global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) 
 #pragma unroll
   for (int g = 0; g < G; ++g) Lmax = max(Lmax, Lg[g]);
 
-  // fold F_m onto residues q for the G slots
+  // fold F_m onto residues q for the G slots, packed in pairs
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     float2 acc[G];
 #pragma unroll
@@ -119,7 +130,7 @@ __global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) 
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         if (m > Lg[g]) continue;
-        const float4 f4 = src[g];
+        const float4 f4 = __ldg(src + g);
         float2 f = slot ? make_float2(f4.z, f4.w) : make_float2(f4.x, f4.y);
         if (rg.shifted && (j & 1)) { f.x = -f.x; f.y = -f.y; }
         acc[g] = f2add(acc[g], f);
@@ -131,7 +142,7 @@ __global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) 
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         if (m > Lg[g]) continue;
-        const float4 f4 = src[g];
+        const float4 f4 = __ldg(src + g);
         float2 f = slot ? make_float2(f4.z, -f4.w) : make_float2(f4.x, -f4.y);
         if (rg.shifted && (j & 1)) { f.x = -f.x; f.y = -f.y; }
         acc[g] = f2add(acc[g], f);
@@ -139,41 +150,63 @@ __global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) 
     }
     const float2 h = hi2(hs[q]), cq = rg.blue ? hi2(ch[q]) : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      float2 v = acc[g];
-      if (rg.shifted) v = f2mul(v, h);
-      buf[g * M + q] = rg.blue ? f2mul(f2conj(v), cq) : v;
+    for (int pp = 0; pp < P; ++pp) {
+      float2 va = acc[2 * pp], vb = acc[2 * pp + 1];
+      if (rg.shifted) { va = f2mul(va, h); vb = f2mul(vb, h); }
+      const float2 z = make_float2(va.x - vb.y, va.y + vb.x);    // G_a + i G_b
+      buf[pp * M + px<OpsF32>(q)] = rg.blue ? f2mul(f2conj(z), cq) : z;
     }
   }
   if (rg.blue)
     for (int q = n + threadIdx.x; q < M; q += blockDim.x)
 #pragma unroll
-      for (int g = 0; g < G; ++g) buf[g * M + q] = make_float2(0.f, 0.f);
+      for (int pp = 0; pp < P; ++pp) buf[pp * M + px<OpsF32>(q)] = make_float2(0.f, 0.f);
   __syncthreads();
-  if (rg.blue) bluestein4<OpsF32, G>(buf, M, rg.logM, Bf, A.twf, A.logMmax);
-  else fft_dif4<OpsF32, G>(buf, M, rg.logM, +1, A.twf, A.logMmax);
+  if (rg.blue) bluestein4<OpsF32, P>(buf, M, M, rg.logM, Bf, A.tw2, A.logMmax);
+  else fft_dif4<OpsF32, P>(buf, M, M, rg.logM, +1, A.tw2, A.logMmax);
 
-  // Eq. 3 per pixel and the chi^2 partials in FP32 (per-thread sums of at
-  // most 16 terms, warp sums by shuffles), the sum over warps in double
+  // Eq. 3 per pixel (in place: s_a + i s_b -> u_a + i u_b) and the chi^2
+  // partials in FP32 (per-thread sums, warp sums by shuffles), the sum over
+  // warps in double
   float c2n[G], c2l[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) { c2n[g] = 0.f; c2l[g] = 0.f; }
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const float2 cp = rg.blue ? hi2(ch[p]) : make_float2(0.f, 0.f);
-    const int br = rg.blue ? p : digitrev(p, rg.logM);
+    const int br = px<OpsF32>(rg.blue ? p : digitrev(p, rg.logM));
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      if (!on[g]) { ureal[g * n + p] = 0.f; continue; }
-      const size_t pix = (size_t)(b0 + g) * A.npix + rg.off + p;
-      const float sv = rg.blue ? f2mul(cp, buf[g * M + br]).x : buf[g * M + br].x;
-      const float wp = A.w32[pix];
-      const float res = A.d32[pix] - sv;
-      const float gg = __fdividef(wp, fmaf(l1t[g], wp, 1.f));
-      c2n[g] = fmaf(wp * res, res, c2n[g]);
-      c2l[g] = fmaf(gg * res, res, c2l[g]);
-      ureal[g * n + p] = lt[g] * gg * res;
+    for (int pp = 0; pp < P; ++pp) {
+      const float2 z = buf[pp * M + br];
+      float sv[2];
+      if (rg.blue) {   // the inverse DFT came out conjugated (conj of the DFT of conj Z)
+        const float2 R = f2mul(cp, z);
+        sv[0] = R.x; sv[1] = -R.y;
+      } else {
+        sv[0] = z.x; sv[1] = z.y;
+      }
+      float u[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int g = 2 * pp + e;
+        u[e] = 0.f;
+        if (!on[g]) continue;
+        const size_t pix = (size_t)(b0 + g) * A.npix + rg.off + p;
+        const float2 dw = __ldg(A.dw32 + pix);
+        const float wp = dw.y;
+        const float res = dw.x - sv[e];
+        const float gg = __fdividef(wp, fmaf(l1t[g], wp, 1.f));
+        c2n[g] = fmaf(wp * res, res, c2n[g]);
+        c2l[g] = fmaf(gg * res, res, c2l[g]);
+        u[e] = lt[g] * gg * res;
+      }
+      const float2 uz = make_float2(u[0], u[1]);
+      buf[pp * M + br] = rg.blue ? f2mul(uz, cp) : uz;
     }
   }
+  if (rg.blue)
+    for (int p = n + threadIdx.x; p < M; p += blockDim.x)
+#pragma unroll
+      for (int pp = 0; pp < P; ++pp) buf[pp * M + px<OpsF32>(p)] = make_float2(0.f, 0.f);
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -185,52 +218,46 @@ __global__ void __launch_bounds__(kRingThreads) bring_kernel(const BatchArgs A) 
       }
       if (lane == 0) { red[warp][2 * g] = a; red[warp][2 * g + 1] = bsum; }
     }
-    __syncthreads();
+    __syncthreads();   // also orders the pixel pass before the forward transform
     if (threadIdx.x < G && on[threadIdx.x]) {
       const int g = threadIdx.x;
       double sa = 0.0, sb = 0.0;
-      for (int w2 = 0; w2 < kRingThreads / 32; ++w2) { sa += red[w2][2 * g]; sb += red[w2][2 * g + 1]; }
+      for (int w2 = 0; w2 < kBringThreads / 32; ++w2) { sa += red[w2][2 * g]; sb += red[w2][2 * g + 1]; }
       A.ring_part[((size_t)(b0 + g) * A.R + r) * 2] = sa;
       A.ring_part[((size_t)(b0 + g) * A.R + r) * 2 + 1] = sb;
     }
   }
-  // forward DFT of u (the sync above also ends every read of buf)
-  if (rg.blue) {
-    for (int p = threadIdx.x; p < M; p += blockDim.x) {
-      const float2 cc = p < n ? hi2(ch[p]) : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const float u = p < n ? ureal[g * n + p] : 0.f;
-        buf[g * M + p] = make_float2(u * cc.x, u * cc.y);
-      }
-    }
-    __syncthreads();
-    bluestein4<OpsF32, G>(buf, M, rg.logM, Bf, A.twf, A.logMmax);
-  } else {
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const int br = digitrev(p, rg.logM);
-#pragma unroll
-      for (int g = 0; g < G; ++g) buf[g * M + br] = make_float2(ureal[g * n + p], 0.f);
-    }
-    __syncthreads();
-    fft_dit4<OpsF32, G>(buf, M, rg.logM, -1, A.twf, A.logMmax);
-  }
+  // forward DFT of u_a + i u_b
+  if (rg.blue) bluestein4<OpsF32, P>(buf, M, M, rg.logM, Bf, A.tw2, A.logMmax);
+  else fft_dit4<OpsF32, P>(buf, M, M, rg.logM, -1, A.tw2, A.logMmax);
+  // unpack U_a, U_b and unfold to m = 0 .. Lmax
   const float om = (float)A.omega;
   for (int m = threadIdx.x; m <= Lmax; m += blockDim.x) {
-    const int q = m % n, j = m / n;
-    const float2 cq = rg.blue ? hi2(ch[q]) : make_float2(0.f, 0.f), hq = f2conj(hi2(hs[q]));
+    const int q = m % n, j = m / n, q2 = q == 0 ? 0 : n - q;
+    const float2 cq = rg.blue ? hi2(ch[q]) : make_float2(0.f, 0.f);
+    const float2 cq2 = rg.blue ? hi2(ch[q2]) : make_float2(0.f, 0.f);
+    const float2 hq = f2conj(hi2(hs[q]));
     float4 *dst4 = A.FT + ((size_t)m * A.RP + k) * B + b0;
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      if (m > Lg[g]) continue;
-      float2 U = rg.blue ? f2mul(cq, buf[g * M + q]) : buf[g * M + q];
-      if (rg.shifted) {
-        U = f2mul(U, hq);
-        if (j & 1) { U.x = -U.x; U.y = -U.y; }
+    for (int pp = 0; pp < P; ++pp) {
+      float2 Z1 = buf[pp * M + px<OpsF32>(q)], Z2 = buf[pp * M + px<OpsF32>(q2)];
+      if (rg.blue) { Z1 = f2mul(cq, Z1); Z2 = f2mul(cq2, Z2); }
+      float2 U[2];
+      U[0] = make_float2(0.5f * (Z1.x + Z2.x), 0.5f * (Z1.y - Z2.y));   // (Z_q + conj Z_{n-q}) / 2
+      U[1] = make_float2(0.5f * (Z1.y + Z2.y), 0.5f * (Z2.x - Z1.x));   // (Z_q - conj Z_{n-q}) / 2i
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int g = 2 * pp + e;
+        if (m > Lg[g]) continue;
+        float2 V = U[e];
+        if (rg.shifted) {
+          V = f2mul(V, hq);
+          if (j & 1) { V.x = -V.x; V.y = -V.y; }
+        }
+        float *dst = reinterpret_cast<float *>(dst4 + g) + 2 * slot;
+        dst[0] = om * V.x;
+        dst[1] = om * V.y;
       }
-      float *dst = reinterpret_cast<float *>(dst4 + g) + 2 * slot;
-      dst[0] = om * U.x;
-      dst[1] = om * U.y;
     }
   }
 }
@@ -529,6 +556,17 @@ __global__ void bfilter_kernel(const BatchArgs A) {
   }
 }
 
+// hi parts of a double-float complex table (the FP32 twiddle and Bluestein tables)
+__global__ void hi_table_kernel(const float4 *src, float2 *dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = hi2(src[i]);
+}
+
+void launch_hi_table(const float4 *src, float2 *dst, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  hi_table_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(src, dst, n);
+}
+
 void launch_batch_export_slot(const BatchArgs &a, int b, cudaStream_t s) {
   bexport_slot_kernel<<<256, 256, 0, s>>>(a, b);
 }
@@ -541,8 +579,7 @@ void launch_lam_table(const double *x, const LegDfArgs &D, int lmax, int RP, flo
 // FP32 copies of slot b's data and inverse noise for the ring stage
 __global__ void bconvert_slot_kernel(const BatchArgs A, int b) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.npix; i += (long long)gridDim.x * blockDim.x) {
-    A.d32[(size_t)b * A.npix + i] = (float)A.d[(size_t)b * A.npix + i];
-    A.w32[(size_t)b * A.npix + i] = (float)A.w[(size_t)b * A.npix + i];
+    A.dw32[(size_t)b * A.npix + i] = make_float2((float)A.d[(size_t)b * A.npix + i], (float)A.w[(size_t)b * A.npix + i]);
   }
 }
 
@@ -550,26 +587,37 @@ void launch_batch_convert_slot(const BatchArgs &a, int b, cudaStream_t s) {
   bconvert_slot_kernel<<<512, 256, 0, s>>>(a, b);
 }
 
-// slots per ring-stage CTA: as many as fit the shared memory of the largest ring
-int batch_ring_group(int maxM, int B) {
-  const size_t per = (size_t)maxM * sizeof(float2) + (size_t)maxM * sizeof(float);
-  int G = 4;
-  while (G > 1 && (G * per > 200 * 1024 || G > B)) G >>= 1;
+// shared memory of one packed pair of slots of a class
+static size_t bring_smem_per_pair(int logM) { return ((size_t)1 << logM) * sizeof(float2); }
+
+// slots per ring-stage CTA of a class: 8, 4 or 2 (pairs share one FFT),
+// within a quarter of an SM's shared memory so that four CTAs share each SM
+static int batch_ring_group(int logM, int B) {
+  int G = 8;
+  while (G > 2 && ((G / 2) * bring_smem_per_pair(logM) > 56 * 1024 || G >= 2 * B)) G >>= 1;
   return G;
 }
 
 template <int G>
-static void launch_bring(const BatchArgs &a, int maxM, cudaStream_t s) {
-  const size_t sm = (size_t)G * ((size_t)maxM * sizeof(float2) + (size_t)maxM * sizeof(float));
-  cudaFuncSetAttribute(bring_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  bring_kernel<G><<<dim3(a.R, (a.B + G - 1) / G), kRingThreads, sm, s>>>(a);
+static void launch_bring(const BatchArgs &a, const RingClass &c, cudaStream_t s) {
+  const size_t sm = (size_t)(G / 2) * bring_smem_per_pair(c.logM);
+  BatchArgs ac = a;
+  ac.first = c.first;
+  bring_kernel<G><<<dim3(c.count, (a.B + G - 1) / G), kBringThreads, sm, s>>>(ac);
 }
 
-void launch_batch_iteration(const BatchArgs &a, int maxM, int n_stiles, int *bstate, cudaStream_t s) {
-  const int G = batch_ring_group(maxM, a.B);
-  if (G == 4) launch_bring<4>(a, maxM, s);
-  else if (G == 2) launch_bring<2>(a, maxM, s);
-  else launch_bring<1>(a, maxM, s);
+void launch_batch_iteration(const BatchArgs &a, const RingClass *cls, int ncls, int n_stiles, int *bstate,
+                            cudaStream_t s) {
+  raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<2>));
+  raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<4>));
+  raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<8>));
+  for (int c = 0; c < ncls; ++c) {
+    if (cls[c].count <= 0) continue;
+    const int G = batch_ring_group(cls[c].logM, a.B);
+    if (G == 8) launch_bring<8>(a, cls[c], s);
+    else if (G == 4) launch_bring<4>(a, cls[c], s);
+    else launch_bring<2>(a, cls[c], s);
+  }
   bfilter_kernel<<<a.B, 256, 0, s>>>(a);
   bana_kernel<<<a.ntiles, 256, 0, s>>>(a);
   bsyn_kernel<<<n_stiles, 256, 0, s>>>(a);

@@ -9,6 +9,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -62,6 +64,45 @@ Plan::~Plan() {
 
 cudaStream_t Plan::run_stream() const {
   return opt.stream ? static_cast<cudaStream_t>(opt.stream) : stream;
+}
+
+void raise_smem_cap(const void *func) {
+  static std::mutex mu;
+  static std::set<const void *> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(func)) return;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, func) != cudaSuccess)
+    return;   // the launch itself then reports the error
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) ==
+      cudaSuccess)
+    done.insert(func);
+}
+
+// Rings sorted by FFT class, largest first: the three largest FFT sizes are a
+// class each, every smaller size joins one last class. Within a class the two
+// rings of a pair are adjacent.
+void ring_classes(const RingDev *rings, int R, std::vector<int> &order, std::vector<RingClass> &cls) {
+  int logMmax = 0;
+  for (int r = 0; r < R; ++r) logMmax = std::max(logMmax, rings[r].logM);
+  const int floor_log = std::max(0, logMmax - 3);
+  auto key = [&](int r) { return std::max(rings[r].logM, floor_log); };
+  order.resize(R);
+  for (int r = 0; r < R; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (key(a) != key(b)) return key(a) > key(b);
+    if (rings[a].pair != rings[b].pair) return rings[a].pair < rings[b].pair;
+    return rings[a].side < rings[b].side;
+  });
+  cls.clear();
+  for (int i = 0; i < R; ++i) {
+    const int k = key(order[i]);
+    if (cls.empty() || cls.back().logM != k) cls.push_back(RingClass{k, i, 0});
+    ++cls.back().count;
+  }
 }
 
 static wf_status build_geometry(Plan *P) {
@@ -142,7 +183,11 @@ static wf_status build_geometry(Plan *P) {
     xk[k] = (i < ns) ? 1.0 - (double)i * i / (3.0 * (double)ns * ns) : 4.0 / 3.0 - 2.0 * i / (3.0 * ns);
   }
   wf_status st;
+  std::vector<int> order;
+  ring_classes(rings.data(), R, order, P->rclass);
+  P->rall = RingClass{P->rclass.front().logM, 0, R};
   if ((st = P->dalloc((void **)&P->d_rings, sizeof(RingDev) * R))) return st;
+  if ((st = P->dalloc((void **)&P->d_order, sizeof(int) * R))) return st;
   if ((st = P->dalloc((void **)&P->d_hs, sizeof(double2) * hs.size()))) return st;
   if ((st = P->dalloc((void **)&P->d_chirp, sizeof(double2) * ch.size()))) return st;
   if ((st = P->dalloc((void **)&P->d_B, sizeof(double2) * (B_tot > 0 ? B_tot : 1)))) return st;
@@ -150,6 +195,7 @@ static wf_status build_geometry(Plan *P) {
   if ((st = P->dalloc((void **)&P->d_x, sizeof(double) * P->RP))) return st;
   cudaStream_t s = P->stream;
   WF_CUDA(cudaMemcpyAsync(P->d_rings, rings.data(), sizeof(RingDev) * R, cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_order, order.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_hs, hs.data(), sizeof(double2) * hs.size(), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_chirp, ch.data(), sizeof(double2) * ch.size(), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
@@ -252,7 +298,7 @@ wf_status Plan::ensure_hist(int cap) {
 
 RingArgs Plan::ring_args() const {
   RingArgs a{};
-  a.rings = d_rings; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;
+  a.rings = d_rings; a.order = d_order; a.first = 0; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;
   a.FS = d_FS; a.FT = d_FT; a.RP = RP; a.d = d_d; a.w = d_w; a.ring_part = d_ring_part; a.ctl = d_ctl;
   a.lsht = lmax; a.omega = omega; a.tau = tau; a.gain = d_gain; a.gainlam = d_gainlam;
   return a;
@@ -424,6 +470,14 @@ wf_status wf_plan_info(wf_plan_t plan, int64_t *npix, int64_t *nalm, double *tau
   if (tau) *tau = P->tau;
   if (n_obs) *n_obs = P->n_obs;
   if (device_bytes) *device_bytes = P->device_bytes;
+  return WF_OK;
+}
+
+wf_status wf_plan_kernels_per_iteration(wf_plan_t plan, int *n) {
+  if (!plan || !n) { set_error("wf_plan_kernels_per_iteration: NULL argument"); return WF_EINVAL; }
+  const Plan *P = static_cast<const Plan *>(plan);
+  (void)P;
+  *n = 3;
   return WF_OK;
 }
 

@@ -322,15 +322,15 @@ void launch_legendre(const LegArgs &a, cudaStream_t s, int mode) {
   const int grid = a.lmax + 1;
   switch (mode) {
     case LEG_SYNTH:
-      cudaFuncSetAttribute(legendre_kernel<LEG_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_kernel<LEG_SYNTH>));
       legendre_kernel<LEG_SYNTH><<<grid, kThreads, sm, s>>>(a);
       break;
     case LEG_ANALYSIS:
-      cudaFuncSetAttribute(legendre_kernel<LEG_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_kernel<LEG_ANALYSIS>));
       legendre_kernel<LEG_ANALYSIS><<<grid, kThreads, sm, s>>>(a);
       break;
     default:
-      cudaFuncSetAttribute(legendre_kernel<LEG_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_kernel<LEG_ITER>));
       legendre_kernel<LEG_ITER><<<grid, kThreads, sm, s>>>(a);
       break;
   }

@@ -401,15 +401,15 @@ void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, in
   const int grid = a.lmax + 1;
   switch (mode) {
     case LEG_SYNTH:
-      cudaFuncSetAttribute(legendre_df_kernel<LEG_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_SYNTH>));
       legendre_df_kernel<LEG_SYNTH><<<grid, kThreads, sm, s>>>(a, d);
       break;
     case LEG_ANALYSIS:
-      cudaFuncSetAttribute(legendre_df_kernel<LEG_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_ANALYSIS>));
       legendre_df_kernel<LEG_ANALYSIS><<<grid, kThreads, sm, s>>>(a, d);
       break;
     default:
-      cudaFuncSetAttribute(legendre_df_kernel<LEG_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_ITER>));
       legendre_df_kernel<LEG_ITER><<<grid, kThreads, sm, s>>>(a, d);
       break;
   }

@@ -221,7 +221,8 @@ extern "C" wf_status wf_map2alm_noalloc(int nside, int lmax, const double *map_d
   ra.rings = rings; ra.tw = tw; ra.logMmax = ilog2_up(L.maxM); ra.hs = hs; ra.chirp = chirp; ra.B = B;
   ra.FT = FT; ra.RP = RP; ra.map_in = map_dev; ra.lsht = lmax;
   ra.omega = 4.0 * M_PI / (double)(12LL * nside * nside);
-  launch_ring(ra, R, L.maxM, s, RING_ANALYSIS);
+  const RingClass all{ilog2_up(L.maxM), 0, R};   // one launch over every ring, in ring order
+  launch_ring(ra, &all, 1, s, RING_ANALYSIS);
   LegArgs la{};
   la.x = x; la.rec = rec; la.ls = ls; la.sv = sv; la.FT = FT; la.alm = reinterpret_cast<double2 *>(alm_dev);
   la.lsht = lmax; la.lmax = lmax; la.RP = RP;

@@ -51,12 +51,13 @@ __device__ void block_sum2(double &a, double &b, double *red) {
 template <int MODE>
 __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
   extern __shared__ double2 smem[];
-  const int r = blockIdx.x;
+  const int r = A.order ? A.order[A.first + blockIdx.x] : A.first + blockIdx.x;
   const RingDev rg = A.rings[r];
   const int n = rg.n;
   const int M = 1 << rg.logM;
-  double2 *buf = smem;                          // [M]
-  double *ureal = reinterpret_cast<double *>(smem + M);  // [n]
+  const int Mp = M;
+  double2 *buf = smem;                          // [Mp] (swizzled, px)
+  double *ureal = reinterpret_cast<double *>(smem + Mp);  // [n]
   __shared__ double red[64];
 
   int L = A.lsht;
@@ -92,24 +93,24 @@ __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
       }
       if (rg.shifted) acc = cmul(acc, hs[q]);
       if (rg.blue) {
-        buf[q] = cmul(conjd(acc), ch[q]);   // inverse DFT via conj(DFT(conj(G)))
+        buf[px<OpsF64>(q)] = cmul(conjd(acc), ch[q]);   // inverse DFT via conj(DFT(conj(G)))
       } else {
-        buf[q] = acc;
+        buf[px<OpsF64>(q)] = acc;
       }
     }
     if (rg.blue) {
-      for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[q] = make_double2(0.0, 0.0);
+      for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[px<OpsF64>(q)] = make_double2(0.0, 0.0);
     }
     __syncthreads();
     if (rg.blue) {
-      bluestein4<OpsF64, 1>(buf, M, rg.logM, Bf, A.tw, A.logMmax);
+      bluestein4<OpsF64, 1>(buf, Mp, M, rg.logM, Bf, A.tw, A.logMmax);
     } else {
-      fft_dif4<OpsF64, 1>(buf, M, rg.logM, +1, A.tw, A.logMmax);
+      fft_dif4<OpsF64, 1>(buf, Mp, M, rg.logM, +1, A.tw, A.logMmax);
     }
     // pixel values: Re of the inverse DFT
     if (MODE == RING_SYNTH) {
       for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const double f = rg.blue ? cmul(ch[p], buf[p]).x : buf[digitrev(p, rg.logM)].x;
+        const double f = rg.blue ? cmul(ch[p], buf[px<OpsF64>(p)]).x : buf[px<OpsF64>(digitrev(p, rg.logM))].x;
         A.map_out[rg.off + p] = f;
       }
       return;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
     double c2n = 0.0, c2l = 0.0;
     const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const double s = rg.blue ? cmul(ch[p], buf[p]).x : buf[digitrev(p, rg.logM)].x;
+      const double s = rg.blue ? cmul(ch[p], buf[px<OpsF64>(p)]).x : buf[px<OpsF64>(digitrev(p, rg.logM))].x;
       const double w = A.w[rg.off + p];
       const double res = A.d[rg.off + p] - s;
       const double wr2 = w * res * res;
@@ -141,18 +142,19 @@ __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
   // ---- forward DFT of the real ring values
   if (rg.blue) {
     for (int p = threadIdx.x; p < M; p += blockDim.x)
-      buf[p] = p < n ? make_double2(ureal[p] * ch[p].x, ureal[p] * ch[p].y) : make_double2(0.0, 0.0);
+      buf[px<OpsF64>(p)] = p < n ? make_double2(ureal[p] * ch[p].x, ureal[p] * ch[p].y) : make_double2(0.0, 0.0);
     __syncthreads();
-    bluestein4<OpsF64, 1>(buf, M, rg.logM, Bf, A.tw, A.logMmax);
+    bluestein4<OpsF64, 1>(buf, Mp, M, rg.logM, Bf, A.tw, A.logMmax);
   } else {
-    for (int p = threadIdx.x; p < n; p += blockDim.x) buf[digitrev(p, rg.logM)] = make_double2(ureal[p], 0.0);
+    for (int p = threadIdx.x; p < n; p += blockDim.x)
+      buf[px<OpsF64>(digitrev(p, rg.logM))] = make_double2(ureal[p], 0.0);
     __syncthreads();
-    fft_dit4<OpsF64, 1>(buf, M, rg.logM, -1, A.tw, A.logMmax);
+    fft_dit4<OpsF64, 1>(buf, Mp, M, rg.logM, -1, A.tw, A.logMmax);
   }
   // ---- unfold residues to m = 0 .. L, apply e^{-i m phi0} and Omega
   for (int m = threadIdx.x; m <= L; m += blockDim.x) {
     const int q = m % n, j = m / n;
-    double2 U = rg.blue ? cmul(ch[q], buf[q]) : buf[q];
+    double2 U = rg.blue ? cmul(ch[q], buf[px<OpsF64>(q)]) : buf[px<OpsF64>(q)];
     if (rg.shifted) {
       U = cmul(U, conjd(hs[q]));
       if (j & 1) { U.x = -U.x; U.y = -U.y; }
@@ -179,40 +181,44 @@ __global__ void __launch_bounds__(kRingThreads) bluestein_setup_kernel(const Rin
     double2 v = make_double2(0.0, 0.0);
     if (q < n) v = conjd(ch[q]);
     else if (q > M - n) v = conjd(ch[M - q]);
-    smem[q] = v;
+    smem[px<OpsF64>(q)] = v;
   }
   __syncthreads();
-  fft_dif4<OpsF64, 1>(smem, M, rg.logM, -1, tw, logMmax);
+  fft_dif4<OpsF64, 1>(smem, M, M, rg.logM, -1, tw, logMmax);
   const double inv = 1.0 / (double)M;
   for (int q = threadIdx.x; q < M; q += blockDim.x)
-    B[rg.B_off + q] = make_double2(smem[q].x * inv, smem[q].y * inv);
+    B[rg.B_off + q] = make_double2(smem[px<OpsF64>(q)].x * inv, smem[px<OpsF64>(q)].y * inv);
 }
 
-static size_t ring_smem(int maxM, int maxN) { return (size_t)maxM * sizeof(double2) + (size_t)maxN * sizeof(double); }
+// Shared memory of a class: the FFT buffer plus the real ring values (n <= M).
+static size_t ring_smem(int logM) {
+  return ((size_t)1 << logM) * sizeof(double2) + ((size_t)1 << logM) * sizeof(double);
+}
 
-void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode) {
-  // the largest ring has at most maxM / 2 pixels when maxM comes from Bluestein, maxM otherwise
-  const size_t sm = ring_smem(maxM, maxM);
+template <int MODE>
+static void launch_ring_mode(const RingArgs &a, const RingClass *cls, int ncls, cudaStream_t s) {
+  raise_smem_cap(reinterpret_cast<const void *>(ring_kernel<MODE>));
+  for (int c = 0; c < ncls; ++c) {
+    if (cls[c].count <= 0) continue;
+    const size_t sm = ring_smem(cls[c].logM);
+    RingArgs ac = a;
+    ac.first = cls[c].first;
+    ring_kernel<MODE><<<cls[c].count, kRingThreads, sm, s>>>(ac);
+  }
+}
+
+void launch_ring(const RingArgs &a, const RingClass *cls, int ncls, cudaStream_t s, int mode) {
   switch (mode) {
-    case RING_SYNTH:
-      cudaFuncSetAttribute(ring_kernel<RING_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_kernel<RING_SYNTH><<<R, kRingThreads, sm, s>>>(a);
-      break;
-    case RING_ANALYSIS:
-      cudaFuncSetAttribute(ring_kernel<RING_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_kernel<RING_ANALYSIS><<<R, kRingThreads, sm, s>>>(a);
-      break;
-    default:
-      cudaFuncSetAttribute(ring_kernel<RING_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_kernel<RING_ITER><<<R, kRingThreads, sm, s>>>(a);
-      break;
+    case RING_SYNTH: launch_ring_mode<RING_SYNTH>(a, cls, ncls, s); break;
+    case RING_ANALYSIS: launch_ring_mode<RING_ANALYSIS>(a, cls, ncls, s); break;
+    default: launch_ring_mode<RING_ITER>(a, cls, ncls, s); break;
   }
 }
 
 void launch_bluestein_setup(const RingDev *rings, int R, const double2 *tw, int logMmax, const double2 *chirp,
                             double2 *B, int maxM, cudaStream_t s) {
   const size_t sm = (size_t)maxM * sizeof(double2);
-  cudaFuncSetAttribute(bluestein_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_cap(reinterpret_cast<const void *>(bluestein_setup_kernel));
   bluestein_setup_kernel<<<R, kRingThreads, sm, s>>>(rings, tw, logMmax, chirp, B);
 }
 

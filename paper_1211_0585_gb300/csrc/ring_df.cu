@@ -79,12 +79,13 @@ __device__ void block_sum2(double &a, double &b, double *red) {
 template <int MODE>
 __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A, const RingDfArgs T) {
   extern __shared__ float4 rsm[];
-  const int r = blockIdx.x;
+  const int r = A.order ? A.order[A.first + blockIdx.x] : A.first + blockIdx.x;
   const RingDev rg = A.rings[r];
   const int n = rg.n;
   const int M = 1 << rg.logM;
-  float4 *buf = rsm;                                        // [M]
-  double *ureal = reinterpret_cast<double *>(rsm + M);      // [n]
+  const int Mp = M;
+  float4 *buf = rsm;                                        // [Mp] (swizzled, px)
+  double *ureal = reinterpret_cast<double *>(rsm + Mp);     // [n]
   __shared__ double red[64];
 
   int L = A.lsht;
@@ -119,17 +120,17 @@ __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A,
       }
       float4 acc = pack(mk(ar), mk(ai));
       if (rg.shifted) acc = cmul(acc, hs[q]);
-      buf[q] = rg.blue ? cmul(cconj(acc), ch[q]) : acc;
+      buf[px<OpsDF>(q)] = rg.blue ? cmul(cconj(acc), ch[q]) : acc;
     }
     if (rg.blue) {
-      for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[px<OpsDF>(q)] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    if (rg.blue) bluestein4<OpsDF, 1>(buf, M, rg.logM, Bf, T.tw, A.logMmax);
-    else fft_dif4<OpsDF, 1>(buf, M, rg.logM, +1, T.tw, A.logMmax);
+    if (rg.blue) bluestein4<OpsDF, 1>(buf, Mp, M, rg.logM, Bf, T.tw, A.logMmax);
+    else fft_dif4<OpsDF, 1>(buf, Mp, M, rg.logM, +1, T.tw, A.logMmax);
     if (MODE == RING_SYNTH) {
       for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const dd f = rg.blue ? RE(cmul(ch[p], buf[p])) : RE(buf[digitrev(p, rg.logM)]);
+        const dd f = rg.blue ? RE(cmul(ch[p], buf[px<OpsDF>(p)])) : RE(buf[px<OpsDF>(digitrev(p, rg.logM))]);
         A.map_out[rg.off + p] = todbl(f);
       }
       return;
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A,
     const bool fresh = A.gainlam[r] == lam;   // gains of this ring already at this lambda
     const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const dd sdf = rg.blue ? RE(cmul(ch[p], buf[p])) : RE(buf[digitrev(p, rg.logM)]);
+      const dd sdf = rg.blue ? RE(cmul(ch[p], buf[px<OpsDF>(p)])) : RE(buf[px<OpsDF>(digitrev(p, rg.logM))]);
       const double s = todbl(sdf);
       const double w = A.w[rg.off + p];
       const double res = A.d[rg.off + p] - s;
@@ -165,24 +166,24 @@ __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A,
       if (p < n) {
         const dd u = mk(ureal[p]);
         const float4 c = ch[p];
-        buf[p] = pack(dmul(u, RE(c)), dmul(u, IM(c)));
+        buf[px<OpsDF>(p)] = pack(dmul(u, RE(c)), dmul(u, IM(c)));
       } else {
-        buf[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        buf[px<OpsDF>(p)] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     __syncthreads();
-    bluestein4<OpsDF, 1>(buf, M, rg.logM, Bf, T.tw, A.logMmax);
+    bluestein4<OpsDF, 1>(buf, Mp, M, rg.logM, Bf, T.tw, A.logMmax);
   } else {
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
       const dd u = mk(ureal[p]);
-      buf[digitrev(p, rg.logM)] = make_float4(u.h, u.l, 0.f, 0.f);
+      buf[px<OpsDF>(digitrev(p, rg.logM))] = make_float4(u.h, u.l, 0.f, 0.f);
     }
     __syncthreads();
-    fft_dit4<OpsDF, 1>(buf, M, rg.logM, -1, T.tw, A.logMmax);
+    fft_dit4<OpsDF, 1>(buf, Mp, M, rg.logM, -1, T.tw, A.logMmax);
   }
   for (int m = threadIdx.x; m <= L; m += blockDim.x) {
     const int q = m % n, j = m / n;
-    float4 U = rg.blue ? cmul(ch[q], buf[q]) : buf[q];
+    float4 U = rg.blue ? cmul(ch[q], buf[px<OpsDF>(q)]) : buf[px<OpsDF>(q)];
     if (rg.shifted) {
       U = cmul(U, cconj(hs[q]));
       if (j & 1) U = cneg(U);
@@ -208,21 +209,28 @@ void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s) 
   to_df_kernel<<<(int)blocks, 256, 0, s>>>(src, dst, n);
 }
 
-void launch_ring_df(const RingArgs &a, const RingDfArgs &t, int R, int maxM, cudaStream_t s, int mode) {
-  const size_t sm = (size_t)maxM * sizeof(float4) + (size_t)maxM * sizeof(double);
+template <int MODE>
+static void launch_ring_df_mode(const RingArgs &a, const RingDfArgs &t, const RingClass *cls, int ncls,
+                                cudaStream_t s) {
+  auto smem = [](int logM) {
+    return ((size_t)1 << logM) * sizeof(float4) + ((size_t)1 << logM) * sizeof(double);
+  };
+  raise_smem_cap(reinterpret_cast<const void *>(ring_df_kernel<MODE>));
+  for (int c = 0; c < ncls; ++c) {
+    if (cls[c].count <= 0) continue;
+    const size_t sm = smem(cls[c].logM);
+    RingArgs ac = a;
+    ac.first = cls[c].first;
+    ring_df_kernel<MODE><<<cls[c].count, kRingThreads, sm, s>>>(ac, t);
+  }
+}
+
+void launch_ring_df(const RingArgs &a, const RingDfArgs &t, const RingClass *cls, int ncls, cudaStream_t s,
+                    int mode) {
   switch (mode) {
-    case RING_SYNTH:
-      cudaFuncSetAttribute(ring_df_kernel<RING_SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_df_kernel<RING_SYNTH><<<R, kRingThreads, sm, s>>>(a, t);
-      break;
-    case RING_ANALYSIS:
-      cudaFuncSetAttribute(ring_df_kernel<RING_ANALYSIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_df_kernel<RING_ANALYSIS><<<R, kRingThreads, sm, s>>>(a, t);
-      break;
-    default:
-      cudaFuncSetAttribute(ring_df_kernel<RING_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      ring_df_kernel<RING_ITER><<<R, kRingThreads, sm, s>>>(a, t);
-      break;
+    case RING_SYNTH: launch_ring_df_mode<RING_SYNTH>(a, t, cls, ncls, s); break;
+    case RING_ANALYSIS: launch_ring_df_mode<RING_ANALYSIS>(a, t, cls, ncls, s); break;
+    default: launch_ring_df_mode<RING_ITER>(a, t, cls, ncls, s); break;
   }
 }
 

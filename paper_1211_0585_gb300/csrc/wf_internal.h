@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/wf.h"
 
@@ -37,6 +38,18 @@ struct RingDev {
   long long hs_off;   // offset of this ring length's half-shift table e^{i pi q / n}
   long long ch_off;   // offset of this ring length's chirp e^{-i pi j^2 / n} (Bluestein only)
   long long B_off;    // offset of this ring length's Bluestein filter (bit-reversed, / M)
+};
+
+// Rings grouped by FFT size for the ring-stage launches: each class is one
+// launch whose shared memory is sized for its own largest FFT (instead of the
+// plan's largest), so the many rings with small or power-of-two FFTs run more
+// CTAs per SM. order[first .. first + count) lists the class's rings, the two
+// rings of a pair next to each other so that the halves of each Fourier
+// coefficient record are read and written close together in time.
+struct RingClass {
+  int logM;    // the largest log2 FFT size in the class
+  int first;   // offset into the ring order
+  int count;   // rings in the class
 };
 
 // Iteration controller state, resident on the device (Sect. 3 schedule).
@@ -69,6 +82,8 @@ enum { LEG_SYNTH = 0, LEG_ANALYSIS = 1, LEG_ITER = 2 };
 
 struct RingArgs {
   const RingDev *rings;
+  const int *order;       // ring of CTA i is order[first + i] (nullptr: first + i)
+  int first;
   const double2 *tw;      // e^{-2 pi i k / Mmax}, k < Mmax / 2
   int logMmax;
   const double2 *hs, *chirp, *B;
@@ -121,19 +136,22 @@ constexpr int kBatchMax = 64;
 
 struct BatchArgs {
   const RingDev *rings;
+  const int *order;          // ring of ring-stage CTA i is order[first + i]
+  int first;
   const float4 *twf, *hsf, *chf, *Bf;
+  const float2 *tw2, *Bf2;   // FP32 twiddle and Bluestein filter tables (hi parts of twf, Bf)
   int logMmax;
   const float *lam;          // [nalm][RP] lambda_lm(x_k), FP32
   int lmax, RP, R, B;
   long long npix, nalm;
   double omega;
   const double *d, *w, *cl;  // [B][npix], [B][npix], [B][lmax+1]
-  float *d32, *w32;          // [B][npix] FP32 copies read by the mixed-precision ring stage
+  float2 *dw32;              // [B][npix] (d, w) in FP32, read by the mixed-precision ring stage
   double2 *s;                // [B][nalm] exported a_lm of finished slots
   float4 *sdf;               // [B][nalm] state, double-float (re hi, re lo, im hi, im lo)
   float2 *fdf;               // [B][lmax+1] Eq. 4 filter f_l(lambda_b) of this iteration, double-float
   float *icl;                // [B][lmax+1] 1 / C_l (0 where C_l = 0)
-  float4 *FS, *FT;        // [(m RP + k) B + b] (north re, north im, south re, south im)
+  float4 *FS, *FT;           // [(m RP + k) B + b] (north re, north im, south re, south im)
   float2 *SP;                // [nalm][B] synthesis coefficients
   Ctl *ctl;                  // [B]
   const int *active;         // [B]
@@ -147,14 +165,19 @@ struct BatchArgs {
 };
 
 void launch_lam_table(const double *x, const LegDfArgs &D, int lmax, int RP, float *lam, cudaStream_t s);
-void launch_batch_iteration(const BatchArgs &a, int maxM, int n_stiles, int *bstate, cudaStream_t s);
+void launch_batch_iteration(const BatchArgs &a, const RingClass *cls, int ncls, int n_stiles, int *bstate,
+                            cudaStream_t s);
 void launch_batch_state(const BatchArgs &a, int *bstate, cudaStream_t s);
 void launch_batch_zero_slot(const BatchArgs &a, int b, cudaStream_t s);
 void launch_batch_convert_slot(const BatchArgs &a, int b, cudaStream_t s);
 void launch_batch_export_slot(const BatchArgs &a, int b, cudaStream_t s);
+void launch_hi_table(const float4 *src, float2 *dst, long long n, cudaStream_t s);
 
-void launch_ring(const RingArgs &a, int R, int maxM, cudaStream_t s, int mode);
-void launch_ring_df(const RingArgs &a, const RingDfArgs &t, int R, int maxM, cudaStream_t s, int mode);
+void launch_ring(const RingArgs &a, const RingClass *cls, int ncls, cudaStream_t s, int mode);
+void launch_ring_df(const RingArgs &a, const RingDfArgs &t, const RingClass *cls, int ncls, cudaStream_t s,
+                    int mode);
+// ring order and classes of a ring table (host; rings as built for the plan)
+void ring_classes(const RingDev *rings, int R, std::vector<int> &order, std::vector<RingClass> &cls);
 void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s);
 void launch_legendre(const LegArgs &a, cudaStream_t s, int mode);
 void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode);
@@ -166,6 +189,13 @@ void launch_bluestein_setup(const RingDev *rings, int R, const double2 *tw, int 
                             const double2 *chirp, double2 *B, int maxM, cudaStream_t s);
 void launch_control(Ctl *ctl, const double *ring_part, int R, const double *m_part, int lmax,
                     const double *cl, wf_iter_record *hist, int hist_cap, cudaStream_t s);
+
+// Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum
+// (once per function). The cap is an attribute of the function, read when a
+// launch or a captured graph node runs, so launches of one kernel with
+// different shared-memory sizes (ring classes, plans of different shapes)
+// must never lower it under one another.
+void raise_smem_cap(const void *func);
 
 // error plumbing
 void set_error(const std::string &msg);

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "W
                 5: "WF_ENUMERIC", 6: "WF_ETIMEOUT", 7: "WF_EBUSY", 8: "WF_ECANCELLED", 9: "WF_ENOTFOUND"}
 
 EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_info", "wf_plan_legendre_terms",
-            "wf_plan_set_options",
+            "wf_plan_kernels_per_iteration", "wf_plan_set_options",
             "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
             "wf_solve_history", "wf_solve_batch",
             "wf_server_create", "wf_submit", "wf_poll", "wf_server_drain", "wf_server_stats",
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t)],
         "wf_plan_set_options": [_vp, ctypes.POINTER(Options)],
         "wf_plan_legendre_terms": [_vp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+        "wf_plan_kernels_per_iteration": [_vp, ctypes.POINTER(_i)],
         "wf_alm2map": [_vp, _i, _vp, _vp],
         "wf_map2alm": [_vp, _i, _vp, _vp],
         "wf_map2alm_noalloc": [_i, _i, _vp, _vp, _vp],
@@ -193,6 +194,11 @@ class Plan:
         ev, full = ctypes.c_int64(), ctypes.c_int64()
         _check(load().wf_plan_legendre_terms(self.handle, lsht, ctypes.byref(ev), ctypes.byref(full)))
         return ev.value, full.value
+
+    def kernels_per_iteration(self):
+        n = _i()
+        _check(load().wf_plan_kernels_per_iteration(self.handle, ctypes.byref(n)))
+        return n.value
 
     def set_options(self, opts: Options):
         _check(load().wf_plan_set_options(self.handle, ctypes.byref(opts)))

@@ -118,4 +118,5 @@ def test_masked_pixels_may_hold_anything(lib):
 def test_null_arguments(lib):
     assert lib.wf_solve(None, None, 0, None, 0, None, None) == wf.WF_EINVAL
     assert lib.wf_alm2map(None, 0, None, None) == wf.WF_EINVAL
+    assert lib.wf_plan_kernels_per_iteration(None, None) == wf.WF_EINVAL
     assert lib.wf_plan_destroy(None) == wf.WF_OK

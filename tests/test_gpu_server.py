@@ -53,13 +53,14 @@ def test_server_mixed_and_fp64_requests():
         ref = O.solve(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"], r["d"], opts)
         bar = 1e-10 if r["tol"] <= 1e-7 else 1e-6
         assert O.rel_l2(alm, ref.alm, r["lmax"]) <= bar
-        # the same request alone: bitwise for the mixed engine, parity for FP64
+        # the same request alone: within the mixed bar for the batched engine
+        # (slots share FP32 ring FFTs in pairs), parity for FP64
         prec = wf.WF_PREC_FP64 if r["tol"] <= 1e-7 else wf.WF_PREC_MIXED
         P = wf.Plan(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"],
                     wf.options(precision=prec, tol=r["tol"], batch_slots=1))
         alone, _, _, _ = P.solve(r["d"])
         if prec == wf.WF_PREC_MIXED:
-            assert np.array_equal(alone, alm)
+            assert O.rel_l2(alm, alone, r["lmax"]) <= 1e-6
         else:
             assert O.rel_l2(alm, alone, r["lmax"]) < 1e-12
     with pytest.raises(wf.WFError):
