@@ -290,7 +290,9 @@ def mixed_batched(prob, dmap, P64, out64, flush, nrhs=64):
     Pm.close()
     return {"solves_per_s": round(nrhs / dt, 4), "nrhs": nrhs, "seconds": round(dt, 3), "status": status,
             "iterations_mean": round(float(np.mean(iters)), 1), "rel_l2_vs_fp64_rhs0": err,
-            "precision": "FP32 ring FFTs and Legendre GEMMs (FP32 Lambda table), double state/updates/reductions",
+            "precision": "FP32 ring FFTs (two slots per complex FFT) and Legendre GEMMs over an FP32 Lambda "
+                         "table with double-float chunk sums; double-float state and Eq. 4; FP32 Eq. 3; "
+                         "double reductions and controller",
             "timing": "host wall clock around wf_solve_batch with device-resident inputs"}
 
 
