@@ -121,8 +121,9 @@ wf_status wf_options_default(wf_options *opt);
 /* Create a plan for one (nside, lmax, C_l, noise, mask) problem: builds the
  * ring geometry, FFT tables, Legendre recurrence tables, tau = min over
  * observed pixels of noise_var (Sect. 2), and allocates all device buffers.
- *   nside      : power of two, 1 .. 1024 (the ring FFTs keep a whole ring in shared memory)
- *   lmax       : 0 .. 4 nside
+ *   nside      : power of two, 1 .. 2048 (rings whose FFT buffers do not fit shared memory
+ *                use a global scratch array)
+ *   lmax       : 0 .. min(4 nside, 4096) (the range over which the rescaled recurrence is pinned)
  *   cl         : host [lmax+1], beam folded in, >= 0 and finite (C_l = 0: mode not solved for)
  *   noise_var  : host [Npix] sigma_p^2, finite and > 0 on observed pixels
  *   mask       : host [Npix] 1 = observed, 0 = masked (N^-1 = 0); NULL = all observed

@@ -100,7 +100,7 @@ void ring_classes(const RingDev *rings, int R, std::vector<int> &order, std::vec
   cls.clear();
   for (int i = 0; i < R; ++i) {
     const int k = key(order[i]);
-    if (cls.empty() || cls.back().logM != k) cls.push_back(RingClass{k, i, 0});
+    if (cls.empty() || cls.back().logM != k) cls.push_back(RingClass{k, i, 0, 0});
     ++cls.back().count;
   }
 }
@@ -185,9 +185,28 @@ static wf_status build_geometry(Plan *P) {
   wf_status st;
   std::vector<int> order;
   ring_classes(rings.data(), R, order, P->rclass);
-  P->rall = RingClass{P->rclass.front().logM, 0, R};
+  // single-solve launches: a class whose FFT buffer (16-byte elements) and real
+  // ring values (8 bytes) exceed the shared-memory limit runs on a global
+  // scratch array, one launch per such class; all other rings form one launch
+  size_t scratch_elems = 0;
+  int next = 0;
+  P->rsingle.clear();
+  for (const RingClass &c : P->rclass) {
+    if (((size_t)1 << c.logM) * 24 <= kRingSmemLimit) break;
+    RingClass g = c;
+    g.global = 1;
+    P->rsingle.push_back(g);
+    scratch_elems = std::max(scratch_elems, (size_t)c.count << c.logM);
+    next = c.first + c.count;
+  }
+  if (next < R) {
+    int lg = 0;
+    for (int i = next; i < R; ++i) lg = std::max(lg, rings[order[i]].logM);
+    P->rsingle.push_back(RingClass{lg, next, R - next, 0});
+  }
   if ((st = P->dalloc((void **)&P->d_rings, sizeof(RingDev) * R))) return st;
   if ((st = P->dalloc((void **)&P->d_order, sizeof(int) * R))) return st;
+  if (scratch_elems > 0 && (st = P->dalloc(&P->d_ring_scratch, 16 * scratch_elems))) return st;
   if ((st = P->dalloc((void **)&P->d_hs, sizeof(double2) * hs.size()))) return st;
   if ((st = P->dalloc((void **)&P->d_chirp, sizeof(double2) * ch.size()))) return st;
   if ((st = P->dalloc((void **)&P->d_B, sizeof(double2) * (B_tot > 0 ? B_tot : 1)))) return st;
@@ -200,7 +219,9 @@ static wf_status build_geometry(Plan *P) {
   WF_CUDA(cudaMemcpyAsync(P->d_chirp, ch.data(), sizeof(double2) * ch.size(), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_x, xk.data(), sizeof(double) * P->RP, cudaMemcpyHostToDevice, s));
-  if (B_tot > 0) launch_bluestein_setup(P->d_rings, R, P->d_tw, P->logMmax, P->d_chirp, P->d_B, maxM, s);
+  if (B_tot > 0)
+    launch_bluestein_setup(P->d_rings, P->d_order, P->rsingle.data(), (int)P->rsingle.size(), P->d_ring_scratch,
+                           P->d_tw, P->logMmax, P->d_chirp, P->d_B, s);
   // double-float copies for the ring_df kernels
   P->n_tw = (long long)tw.size();
   P->n_hs = (long long)hs.size();
@@ -298,7 +319,7 @@ wf_status Plan::ensure_hist(int cap) {
 
 RingArgs Plan::ring_args() const {
   RingArgs a{};
-  a.rings = d_rings; a.order = d_order; a.first = 0; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;
+  a.rings = d_rings; a.order = d_order; a.first = 0; a.scratch = d_ring_scratch; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;
   a.FS = d_FS; a.FT = d_FT; a.RP = RP; a.d = d_d; a.w = d_w; a.ring_part = d_ring_part; a.ctl = d_ctl;
   a.lsht = lmax; a.omega = omega; a.tau = tau; a.gain = d_gain; a.gainlam = d_gainlam;
   return a;
@@ -395,12 +416,12 @@ wf_status wf_plan_create(int nside, int lmax, const double *cl, const double *no
                          const wf_options *opt, wf_plan_t *out) {
   if (!out || !cl || !noise_var) { set_error("wf_plan_create: NULL argument"); return WF_EINVAL; }
   *out = nullptr;
-  if (nside < 1 || nside > 1024 || (nside & (nside - 1)) != 0) {
-    set_error("wf_plan_create: nside must be a power of two in [1, 1024]");
+  if (nside < 1 || nside > 2048 || (nside & (nside - 1)) != 0) {
+    set_error("wf_plan_create: nside must be a power of two in [1, 2048]");
     return WF_EINVAL;
   }
-  if (lmax < 0 || lmax > 4 * nside || lmax > 8192) {
-    set_error("wf_plan_create: lmax must be in [0, 4 nside]");
+  if (lmax < 0 || lmax > 4 * nside || lmax > 4096) {
+    set_error("wf_plan_create: lmax must be in [0, min(4 nside, 4096)]");
     return WF_EINVAL;
   }
   wf_options o;

@@ -31,6 +31,7 @@
 namespace wfk {
 
 constexpr int kNoStartD = 1 << 30;
+constexpr int kAnaChunk = 1024;   // ring pairs whose analysis state is held in shared memory at once
 
 __device__ __forceinline__ size_t alm_idx_d(int lmax, int l, int m) {
   return (size_t)m * (2 * lmax + 1 - m) / 2 + l;
@@ -218,55 +219,61 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
 
   if (MODE == LEG_ANALYSIS || MODE == LEG_ITER) {
     // per ring pair state in shared memory: the thread's sums then cover all of
-    // its ring pairs before one reduction per block of kLB values of l
-    float4 *stE = ss;                            // (Er, Ei) as hi/lo
-    float4 *stO = stE + RP;                      // (Or, Oi)
-    float4 *stP = stO + RP;                      // (p1, p2)
-    float2 *stX = reinterpret_cast<float2 *>(stP + RP);  // x as double-float
-    for (int k = threadIdx.x; k < RP; k += blockDim.x) {
-      const double4_32a t = A.FT[(size_t)m * RP + k];
-      const dfl er = df_from(t.x + t.z), ei = df_from(t.y + t.w);
-      const dfl orr = df_from(t.x - t.z), oi = df_from(t.y - t.w);
-      stE[k] = make_float4(er.h, er.l, ei.h, ei.l);
-      stO[k] = make_float4(orr.h, orr.l, oi.h, oi.l);
-      stP[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      const dfl xk = df_from(A.x[k]);
-      stX[k] = make_float2(xk.h, xk.l);
-    }
-    __syncthreads();
-    for (int l0 = m; l0 <= L; l0 += kLB) {
-      float S[32], C[32];
+    // its ring pairs of a chunk before one reduction per block of kLB values of
+    // l; chunks of kAnaChunk ring pairs run one after another (one chunk up to
+    // Nside 512), each adding its share to t_l
+    for (int k0 = 0; k0 < RP; k0 += kAnaChunk) {
+      const int nk = min(kAnaChunk, RP - k0);
+      float4 *stE = ss;                            // (Er, Ei) as hi/lo
+      float4 *stO = stE + nk;                      // (Or, Oi)
+      float4 *stP = stO + nk;                      // (p1, p2)
+      float2 *stX = reinterpret_cast<float2 *>(stP + nk);  // x as double-float
+      for (int kk = threadIdx.x; kk < nk; kk += blockDim.x) {
+        const int k = k0 + kk;
+        const double4_32a t = A.FT[(size_t)m * RP + k];
+        const dfl er = df_from(t.x + t.z), ei = df_from(t.y + t.w);
+        const dfl orr = df_from(t.x - t.z), oi = df_from(t.y - t.w);
+        stE[kk] = make_float4(er.h, er.l, ei.h, ei.l);
+        stO[kk] = make_float4(orr.h, orr.l, oi.h, oi.l);
+        stP[kk] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const dfl xk = df_from(A.x[k]);
+        stX[kk] = make_float2(xk.h, xk.l);
+      }
+      __syncthreads();
+      for (int l0 = m; l0 <= L; l0 += kLB) {
+        float S[32], C[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) { S[j] = 0.f; C[j] = 0.f; }
-      for (int k = threadIdx.x; k < RP; k += blockDim.x) {
-        const size_t mk = (size_t)m * RP + k;
-        const int ls = D.ls[mk];
-        if (ls >= l0 + kLB) continue;            // no evaluated term yet in this block
-        const float2 x2 = stX[k];
-        const dfl x = dfl{x2.x, x2.y};
-        const float4 e4 = stE[k], o4 = stO[k], q4 = stP[k];
-        dfl p1 = dfl{q4.x, q4.y}, p2 = dfl{q4.z, q4.w};
-        if (ls + 1 >= l0) {                      // a start value falls in this block
-          const float4 s4 = D.sv[mk];
-          analysis_block<true>(l0, m, sA, x, p1, p2, ls, dfl{s4.x, s4.y}, dfl{s4.z, s4.w}, dfl{e4.x, e4.y},
-                               dfl{e4.z, e4.w}, dfl{o4.x, o4.y}, dfl{o4.z, o4.w}, S, C);
-        } else {
-          analysis_block<false>(l0, m, sA, x, p1, p2, ls, dfl{0.f, 0.f}, dfl{0.f, 0.f}, dfl{e4.x, e4.y},
-                                dfl{e4.z, e4.w}, dfl{o4.x, o4.y}, dfl{o4.z, o4.w}, S, C);
+        for (int j = 0; j < 32; ++j) { S[j] = 0.f; C[j] = 0.f; }
+        for (int kk = threadIdx.x; kk < nk; kk += blockDim.x) {
+          const size_t mk = (size_t)m * RP + k0 + kk;
+          const int ls = D.ls[mk];
+          if (ls >= l0 + kLB) continue;            // no evaluated term yet in this block
+          const float2 x2 = stX[kk];
+          const dfl x = dfl{x2.x, x2.y};
+          const float4 e4 = stE[kk], o4 = stO[kk], q4 = stP[kk];
+          dfl p1 = dfl{q4.x, q4.y}, p2 = dfl{q4.z, q4.w};
+          if (ls + 1 >= l0) {                      // a start value falls in this block
+            const float4 s4 = D.sv[mk];
+            analysis_block<true>(l0, m, sA, x, p1, p2, ls, dfl{s4.x, s4.y}, dfl{s4.z, s4.w}, dfl{e4.x, e4.y},
+                                 dfl{e4.z, e4.w}, dfl{o4.x, o4.y}, dfl{o4.z, o4.w}, S, C);
+          } else {
+            analysis_block<false>(l0, m, sA, x, p1, p2, ls, dfl{0.f, 0.f}, dfl{0.f, 0.f}, dfl{e4.x, e4.y},
+                                  dfl{e4.z, e4.w}, dfl{o4.x, o4.y}, dfl{o4.z, o4.w}, S, C);
+          }
+          stP[kk] = make_float4(p1.h, p1.l, p2.h, p2.l);
         }
-        stP[k] = make_float4(p1.h, p1.l, p2.h, p2.l);
-      }
-      const double s = warp_transpose_sum_df(S, C);
-      red[warp][lane] = s;
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        double t = 0.0;
+        const double s = warp_transpose_sum_df(S, C);
+        red[warp][lane] = s;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
-        double *dst = reinterpret_cast<double *>(&tl[l0 - m + (threadIdx.x >> 1)]);
-        dst[threadIdx.x & 1] += t;
+          for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
+          double *dst = reinterpret_cast<double *>(&tl[l0 - m + (threadIdx.x >> 1)]);
+          dst[threadIdx.x & 1] += t;
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
     // undo the rescaling: lambda = g mu
     for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
@@ -387,11 +394,12 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
   }
 }
 
-// tl [Lp] double2 | sA [Lp (+1)] float2 | max(Lp, 3 RP) float4 (synthesis
-// coefficients, or the per-ring-pair analysis state)
+// tl [Lp] double2 | sA [Lp (+1)] float2 | max(Lp, 3.5 chunk) float4 (synthesis
+// coefficients, or the per-ring-pair analysis state of one chunk)
 static size_t leg_df_smem(int lmax, int RP) {
   const size_t Lp = (size_t)lmax + 1 + kLB;
-  const size_t st = 3 * (size_t)RP + ((size_t)RP + 1) / 2;
+  const size_t nk = RP < kAnaChunk ? (size_t)RP : (size_t)kAnaChunk;
+  const size_t st = 3 * nk + (nk + 1) / 2;
   const size_t q = Lp > st ? Lp : st;
   return Lp * sizeof(double2) + (Lp + 1) * sizeof(float2) + q * sizeof(float4) + 16;
 }

@@ -215,13 +215,13 @@ extern "C" wf_status wf_map2alm_noalloc(int nside, int lmax, const double *map_d
   if (e != cudaSuccess) return cuda_status(e, "cudaMemsetAsync");
   noalloc_geometry_kernel<<<64, 256, 0, s>>>(nside, L.maxM, rings, hs, chirp, tw, x);
   noalloc_rec_kernel<<<lmax + 1, 128, 0, s>>>(lmax, rec);
-  if (L.B_n > 0) launch_bluestein_setup(rings, R, tw, ilog2_up(L.maxM), chirp, B, L.maxM, s);
+  const RingClass all{ilog2_up(L.maxM), 0, R, 0};   // one launch over every ring, in ring order
+  if (L.B_n > 0) launch_bluestein_setup(rings, nullptr, &all, 1, nullptr, tw, ilog2_up(L.maxM), chirp, B, s);
   launch_start_values(x, rec, lmax, RP, ls, sv, s);
   RingArgs ra{};
   ra.rings = rings; ra.tw = tw; ra.logMmax = ilog2_up(L.maxM); ra.hs = hs; ra.chirp = chirp; ra.B = B;
   ra.FT = FT; ra.RP = RP; ra.map_in = map_dev; ra.lsht = lmax;
   ra.omega = 4.0 * M_PI / (double)(12LL * nside * nside);
-  const RingClass all{ilog2_up(L.maxM), 0, R};   // one launch over every ring, in ring order
   launch_ring(ra, &all, 1, s, RING_ANALYSIS);
   LegArgs la{};
   la.x = x; la.rec = rec; la.ls = ls; la.sv = sv; la.FT = FT; la.alm = reinterpret_cast<double2 *>(alm_dev);

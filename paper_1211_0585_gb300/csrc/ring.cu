@@ -56,8 +56,9 @@ __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
   const int n = rg.n;
   const int M = 1 << rg.logM;
   const int Mp = M;
-  double2 *buf = smem;                          // [Mp] (swizzled, px)
-  double *ureal = reinterpret_cast<double *>(smem + Mp);  // [n]
+  // [Mp] (swizzled, px): shared memory, or this CTA's part of the global scratch
+  double2 *buf = A.scratch ? reinterpret_cast<double2 *>(A.scratch) + (size_t)blockIdx.x * M : smem;
+  double *ureal = reinterpret_cast<double *>(A.scratch ? smem : smem + Mp);  // [n]
   __shared__ double red[64];
 
   int L = A.lsht;
@@ -167,32 +168,35 @@ __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
 
 // Bluestein filter spectrum per ring length: b_q = conj(c_q) for |q| < n
 // (wrapped into [0, M)), transformed by the DIF FFT (so stored digit-reversed)
-// and scaled by 1/M. One CTA per ring; only the first ring of each length
-// (the north ring of a polar pair) writes.
-__global__ void __launch_bounds__(kRingThreads) bluestein_setup_kernel(const RingDev *rings, const double2 *tw,
-                                                                   int logMmax, const double2 *chirp,
-                                                                   double2 *B) {
+// and scaled by 1/M. One CTA per ring of a class; only the first ring of each
+// length (the north ring of a polar pair) writes. Classes whose buffers do not
+// fit shared memory work in the global scratch, as the ring kernels do.
+__global__ void __launch_bounds__(kRingThreads) bluestein_setup_kernel(const RingDev *rings, const int *order,
+                                                                   int first, double2 *scratch,
+                                                                   const double2 *tw, int logMmax,
+                                                                   const double2 *chirp, double2 *B) {
   extern __shared__ double2 smem[];
-  const RingDev rg = rings[blockIdx.x];
+  const RingDev rg = rings[order ? order[first + blockIdx.x] : first + blockIdx.x];
   if (!rg.blue || rg.side != 0) return;
   const int n = rg.n, M = 1 << rg.logM;
+  double2 *buf = scratch ? scratch + (size_t)blockIdx.x * M : smem;
   const double2 *ch = chirp + rg.ch_off;
   for (int q = threadIdx.x; q < M; q += blockDim.x) {
     double2 v = make_double2(0.0, 0.0);
     if (q < n) v = conjd(ch[q]);
     else if (q > M - n) v = conjd(ch[M - q]);
-    smem[px<OpsF64>(q)] = v;
+    buf[px<OpsF64>(q)] = v;
   }
   __syncthreads();
-  fft_dif4<OpsF64, 1>(smem, M, M, rg.logM, -1, tw, logMmax);
+  fft_dif4<OpsF64, 1>(buf, M, M, rg.logM, -1, tw, logMmax);
   const double inv = 1.0 / (double)M;
   for (int q = threadIdx.x; q < M; q += blockDim.x)
-    B[rg.B_off + q] = make_double2(smem[px<OpsF64>(q)].x * inv, smem[px<OpsF64>(q)].y * inv);
+    B[rg.B_off + q] = make_double2(buf[px<OpsF64>(q)].x * inv, buf[px<OpsF64>(q)].y * inv);
 }
 
 // Shared memory of a class: the FFT buffer plus the real ring values (n <= M).
-static size_t ring_smem(int logM) {
-  return ((size_t)1 << logM) * sizeof(double2) + ((size_t)1 << logM) * sizeof(double);
+static size_t ring_smem(const RingClass &c) {
+  return (c.global ? 0 : ((size_t)1 << c.logM) * sizeof(double2)) + ((size_t)1 << c.logM) * sizeof(double);
 }
 
 template <int MODE>
@@ -200,9 +204,10 @@ static void launch_ring_mode(const RingArgs &a, const RingClass *cls, int ncls, 
   raise_smem_cap(reinterpret_cast<const void *>(ring_kernel<MODE>));
   for (int c = 0; c < ncls; ++c) {
     if (cls[c].count <= 0) continue;
-    const size_t sm = ring_smem(cls[c].logM);
+    const size_t sm = ring_smem(cls[c]);
     RingArgs ac = a;
     ac.first = cls[c].first;
+    ac.scratch = cls[c].global ? a.scratch : nullptr;
     ring_kernel<MODE><<<cls[c].count, kRingThreads, sm, s>>>(ac);
   }
 }
@@ -215,11 +220,16 @@ void launch_ring(const RingArgs &a, const RingClass *cls, int ncls, cudaStream_t
   }
 }
 
-void launch_bluestein_setup(const RingDev *rings, int R, const double2 *tw, int logMmax, const double2 *chirp,
-                            double2 *B, int maxM, cudaStream_t s) {
-  const size_t sm = (size_t)maxM * sizeof(double2);
+void launch_bluestein_setup(const RingDev *rings, const int *order, const RingClass *cls, int ncls, void *scratch,
+                            const double2 *tw, int logMmax, const double2 *chirp, double2 *B, cudaStream_t s) {
   raise_smem_cap(reinterpret_cast<const void *>(bluestein_setup_kernel));
-  bluestein_setup_kernel<<<R, kRingThreads, sm, s>>>(rings, tw, logMmax, chirp, B);
+  for (int c = 0; c < ncls; ++c) {
+    if (cls[c].count <= 0) continue;
+    const size_t sm = cls[c].global ? 0 : ((size_t)1 << cls[c].logM) * sizeof(double2);
+    bluestein_setup_kernel<<<cls[c].count, kRingThreads, sm, s>>>(
+        rings, order, cls[c].first, cls[c].global ? reinterpret_cast<double2 *>(scratch) : nullptr, tw, logMmax,
+        chirp, B);
+  }
 }
 
 }  // namespace wfk

@@ -84,8 +84,9 @@ __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A,
   const int n = rg.n;
   const int M = 1 << rg.logM;
   const int Mp = M;
-  float4 *buf = rsm;                                        // [Mp] (swizzled, px)
-  double *ureal = reinterpret_cast<double *>(rsm + Mp);     // [n]
+  // [Mp] (swizzled, px): shared memory, or this CTA's part of the global scratch
+  float4 *buf = A.scratch ? reinterpret_cast<float4 *>(A.scratch) + (size_t)blockIdx.x * M : rsm;
+  double *ureal = reinterpret_cast<double *>(A.scratch ? rsm : rsm + Mp);   // [n]
   __shared__ double red[64];
 
   int L = A.lsht;
@@ -212,15 +213,16 @@ void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s) 
 template <int MODE>
 static void launch_ring_df_mode(const RingArgs &a, const RingDfArgs &t, const RingClass *cls, int ncls,
                                 cudaStream_t s) {
-  auto smem = [](int logM) {
-    return ((size_t)1 << logM) * sizeof(float4) + ((size_t)1 << logM) * sizeof(double);
+  auto smem = [](const RingClass &c) {
+    return (c.global ? 0 : ((size_t)1 << c.logM) * sizeof(float4)) + ((size_t)1 << c.logM) * sizeof(double);
   };
   raise_smem_cap(reinterpret_cast<const void *>(ring_df_kernel<MODE>));
   for (int c = 0; c < ncls; ++c) {
     if (cls[c].count <= 0) continue;
-    const size_t sm = smem(cls[c].logM);
+    const size_t sm = smem(cls[c]);
     RingArgs ac = a;
     ac.first = cls[c].first;
+    ac.scratch = cls[c].global ? a.scratch : nullptr;
     ring_df_kernel<MODE><<<cls[c].count, kRingThreads, sm, s>>>(ac, t);
   }
 }

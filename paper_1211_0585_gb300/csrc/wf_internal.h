@@ -50,7 +50,13 @@ struct RingClass {
   int logM;    // the largest log2 FFT size in the class
   int first;   // offset into the ring order
   int count;   // rings in the class
+  int global;  // 1: the class's FFT buffers do not fit shared memory and live in a global
+               //    scratch array, 2^logM 16-byte elements per CTA (CTA i of the class at i 2^logM)
 };
+
+// Largest dynamic shared memory a ring-stage CTA asks for (of the 227 KB a CTA
+// may use on this GPU; the rest is left for static arrays).
+constexpr size_t kRingSmemLimit = 200 * 1024;
 
 // Iteration controller state, resident on the device (Sect. 3 schedule).
 struct Ctl {
@@ -84,6 +90,7 @@ struct RingArgs {
   const RingDev *rings;
   const int *order;       // ring of CTA i is order[first + i] (nullptr: first + i)
   int first;
+  void *scratch;          // global FFT buffers of a class that does not fit shared memory (else nullptr)
   const double2 *tw;      // e^{-2 pi i k / Mmax}, k < Mmax / 2
   int logMmax;
   const double2 *hs, *chirp, *B;
@@ -185,8 +192,8 @@ void launch_df_tables(const double *x, const double2 *rec, int lmax, int RP, dou
                       float4 *sv, cudaStream_t s);
 void launch_start_values(const double *x, const double2 *rec, int lmax, int RP, int *ls,
                          double2 *sv, cudaStream_t s);
-void launch_bluestein_setup(const RingDev *rings, int R, const double2 *tw, int logMmax,
-                            const double2 *chirp, double2 *B, int maxM, cudaStream_t s);
+void launch_bluestein_setup(const RingDev *rings, const int *order, const RingClass *cls, int ncls, void *scratch,
+                            const double2 *tw, int logMmax, const double2 *chirp, double2 *B, cudaStream_t s);
 void launch_control(Ctl *ctl, const double *ring_part, int R, const double *m_part, int lmax,
                     const double *cl, wf_iter_record *hist, int hist_cap, cudaStream_t s);
 

@@ -32,7 +32,9 @@ struct Plan : wf_plan_s {
   RingDev *d_rings = nullptr;
   int *d_order = nullptr;               // rings sorted by FFT class (RingClass), largest first
   std::vector<RingClass> rclass;        // the classes (batched ring stage: one launch each)
-  RingClass rall{0, 0, 0};              // every ring in that order (single-solve ring stage: one launch)
+  std::vector<RingClass> rsingle;       // single-solve ring stage: the classes whose 16-byte FFT buffers
+                                        // do not fit shared memory (global scratch), then every other ring
+  void *d_ring_scratch = nullptr;       // their FFT buffers
   double2 *d_tw = nullptr, *d_hs = nullptr, *d_chirp = nullptr, *d_B = nullptr;
   double *d_x = nullptr;
   double2 *d_rec = nullptr, *d_sv = nullptr;
@@ -72,8 +74,8 @@ struct Plan : wf_plan_s {
   RingDfArgs ringdf_args() const { return RingDfArgs{d_twf, d_hsf, d_chf, d_Bf}; }
   // the ring stage of the plan's precision
   void launch_rng(const RingArgs &a, cudaStream_t s, int mode) const {
-    if (opt.precision == WF_PREC_FP64_NATIVE) launch_ring(a, &rall, 1, s, mode);
-    else launch_ring_df(a, ringdf_args(), &rall, 1, s, mode);
+    if (opt.precision == WF_PREC_FP64_NATIVE) launch_ring(a, rsingle.data(), (int)rsingle.size(), s, mode);
+    else launch_ring_df(a, ringdf_args(), rsingle.data(), (int)rsingle.size(), s, mode);
   }
   // the Legendre stage of the plan's precision
   void launch_leg(const LegArgs &a, cudaStream_t s, int mode) const {

@@ -99,3 +99,40 @@ def test_sampled_full_size_nside512(prec):
     refa = O.map2alm_modes(nside, lmax, f, ls, ms)
     got = host_alm(a)[O.alm_index(lmax, ls, ms)]
     assert np.max(np.abs(got - refa)) <= 1e-11 * np.max(np.abs(host_alm(a)))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_sampled_full_size_nside2048(prec):
+    """At the Planck-shaped size (Nside 2048, lmax 4096), where the polar rings
+    with Bluestein buffers of 16384 points run their FFTs in global scratch and
+    the analysis state is split into ring-pair chunks: sampled pixels (among
+    them pixels of those rings, in both caps) and sampled modes up to m = 4096,
+    each computed one by one by the oracle. Bar: the FP64 path's 1e-10,
+    relative to the largest value (the recurrence runs to l = 4096 and its
+    rounding grows with l; it is largest at the poles, where lambda_l0 peaks)."""
+    import torch
+    nside, lmax = 2048, 4096
+    npix = 12 * nside * nside
+    rng = np.random.default_rng(2048)
+    cl = I.cl_lcdm_like(lmax, 5.0)
+    alm = I.draw_alm(cl, rng)
+    P = plan_for(nside, lmax, prec)
+    m = torch.empty(npix, dtype=torch.float64, device="cuda")
+    P.alm2map(lmax, dev(alm).data_ptr(), m.data_ptr())
+    f = rng.standard_normal(npix)
+    a = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
+    P.map2alm(lmax, dev(f).data_ptr(), a.data_ptr())
+    torch.cuda.synchronize()
+    got_map = m.cpu().numpy()
+    # ring i (1-based, north cap) starts at pixel 2 i (i - 1); rings 1025 .. 2047 use global scratch
+    big_north = [2 * i * (i - 1) + j for i, j in ((1025, 3), (1500, 100), (2047, 8187))]
+    big_south = [npix - 1 - p for p in big_north]
+    pix = np.concatenate([rng.integers(0, npix, 16), big_north, big_south, [0, 1, npix - 1, npix // 2]])
+    ref = O.alm2map_pixels(nside, lmax, alm, pix)
+    scale = np.max(np.abs(got_map))
+    assert np.max(np.abs(got_map[pix] - ref)) <= 1e-10 * scale
+    ls = np.array([0, 2, 100, 4096, 4096, 3000, 2049, 4000, 37, 1500])
+    ms = np.array([0, 2, 50, 0, 4096, 2999, 1, 3999, 30, 1024])
+    refa = O.map2alm_modes(nside, lmax, f, ls, ms)
+    got = host_alm(a)[O.alm_index(lmax, ls, ms)]
+    assert np.max(np.abs(got - refa)) <= 1e-10 * np.max(np.abs(host_alm(a)))
