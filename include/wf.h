@@ -145,9 +145,10 @@ wf_status wf_plan_info(wf_plan_t plan, int64_t *npix, int64_t *nalm, double *tau
 wf_status wf_plan_legendre_terms(wf_plan_t plan, int lsht, int64_t *evaluated, int64_t *full);
 
 /* Kernel launches in one messenger iteration of the plan's single-solve path
- * (WF_PREC_FP64 or WF_PREC_FP64_NATIVE): the ring stage, the Legendre stage and
- * the controller, one launch each. Used to count device launches; *n must not
- * be NULL. */
+ * (WF_PREC_FP64 or WF_PREC_FP64_NATIVE): the ring stage (one launch, or at
+ * Nside 2048 two: the rings whose FFT buffers exceed shared memory run apart),
+ * the Legendre stage and the controller. Used to count device launches; *n
+ * must not be NULL. */
 wf_status wf_plan_kernels_per_iteration(wf_plan_t plan, int *n);
 
 /* Replace the plan's options (precision, tolerances, schedule knobs, stream). */

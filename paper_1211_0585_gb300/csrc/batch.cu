@@ -20,30 +20,53 @@ namespace wfk {
 
 static size_t nalm_of(int lmax) { return (size_t)(lmax + 1) * (lmax + 2) / 2; }
 
-static void make_tiles(int lmax, int RP, std::vector<int2> &ana, std::vector<int2> &syn) {
+static int n_par(int m, int p, int L) { return L >= m + p ? (L - m - p) / 2 + 1 : 0; }
+
+// Work lists and offsets of the tensor-core Legendre stage: analysis tiles
+// (m, parity, first i, first lamA row of (m, parity)), synthesis tiles (m,
+// first ring pair), and the first 32-wide chunk of i of every (m, parity).
+static void make_tc_lists(int lmax, int RPp, std::vector<int4> &ana, std::vector<int2> &syn, std::vector<int> &offTc,
+                          int &nchunks) {
   ana.clear();
   syn.clear();
-  for (int m = 0; m <= lmax; ++m)
-    for (int l0 = m; l0 <= lmax; l0 += 64) ana.push_back(make_int2(m, l0));
-  for (int m = 0; m <= lmax; ++m)
-    for (int k0 = 0; k0 < RP; k0 += 32) syn.push_back(make_int2(m, k0));
+  offTc.assign(2 * (size_t)(lmax + 1), 0);
+  nchunks = 0;
+  size_t row = 0;
+  for (int m = 0; m <= lmax; ++m) {
+    for (int p = 0; p < 2; ++p) {
+      const int np = n_par(m, p, lmax);
+      offTc[2 * m + p] = nchunks;
+      nchunks += (np + 31) / 32;
+      for (int i0 = 0; i0 < np; i0 += 128) ana.push_back(make_int4(m, p, i0, (int)row));
+      row += np;
+    }
+    for (int k0 = 0; k0 < RPp; k0 += 128) syn.push_back(make_int2(m, k0));
+  }
 }
+
+static int round_up(int v, int q) { return (v + q - 1) / q * q; }
 
 size_t Engine::bytes_needed(int nside, int lmax, int nslots) {
   const size_t RP = 2 * (size_t)nside, R = 4 * (size_t)nside - 1, npix = 12 * (size_t)nside * nside;
+  const size_t RPp = (size_t)round_up((int)RP, 32);
   const size_t nalm = nalm_of(lmax), nF = (size_t)(lmax + 1) * RP;
-  size_t ntiles = 0;
-  for (int m = 0; m <= lmax; ++m) ntiles += (size_t)(lmax - m) / 64 + 1;
-  const size_t B = (size_t)nslots, L1 = (size_t)lmax + 1;
-  const size_t tables = nalm * RP * sizeof(float)                    // Lambda table
-                        + sizeof(float2) * (8 * (size_t)nside + 16 * (size_t)nside * nside);  // FP32 FFT tables (bound)
-  const size_t per_slot = 2 * nF * sizeof(float4)                     // FS, FT
-                          + nalm * (sizeof(float2) + sizeof(double2) + sizeof(float4))  // SP, s, sdf
-                          + npix * 2 * (sizeof(double) + sizeof(float))                  // d, w and FP32 copies
-                          + L1 * (sizeof(double) + sizeof(float2) + sizeof(float))       // C_l, filter tables
-                          + R * 2 * sizeof(double) + ntiles * 3 * sizeof(double)         // partials
+  size_t ntiles = 0, nchunks = 0;
+  for (int m = 0; m <= lmax; ++m)
+    for (int p = 0; p < 2; ++p) {
+      ntiles += (size_t)(n_par(m, p, lmax) + 127) / 128;
+      nchunks += (size_t)(n_par(m, p, lmax) + 31) / 32;
+    }
+  const size_t B = (size_t)round_up(nslots, 8), L1 = (size_t)lmax + 1, Nc = 2 * B;
+  const size_t tables = (nalm + 32 * nchunks) * RPp * sizeof(float)                            // lamA, lamT
+                        + sizeof(float2) * (8 * (size_t)nside + 16 * (size_t)nside * nside);  // FP32 FFT tables
+  const size_t operands = (L1 * 2 * RPp + 32 * nchunks) * Nc * sizeof(float);                 // XT, SPT
+  const size_t per_slot = 2 * nF * sizeof(float4)                                             // FS, FT
+                          + nalm * (sizeof(double2) + sizeof(float4))                          // s, sdf
+                          + npix * 2 * (sizeof(double) + sizeof(float))                         // d, w, FP32 copies
+                          + L1 * (sizeof(double) + sizeof(float2) + sizeof(float))              // C_l, filter tables
+                          + R * 2 * sizeof(double) + ntiles * 3 * sizeof(double)                // partials
                           + sizeof(Ctl) + sizeof(wf_iter_record) + 8;
-  return tables + B * per_slot + (ntiles + nF / 32 + 64) * sizeof(int2);
+  return tables + operands + B * per_slot + (ntiles + L1 * RPp / 128 + 2 * L1) * 16;
 }
 
 wf_status Engine::dalloc(void **p, size_t bytes) {
@@ -58,6 +81,7 @@ Engine::~Engine() {
   if (stream) cudaStreamSynchronize(stream);
   if (graph) cudaGraphExecDestroy(graph);
   for (void *p : allocs) cudaFree(p);
+  if (h_err) cudaFreeHost(h_err);
   if (h_ctl) cudaFreeHost(h_ctl);
   if (h_active) cudaFreeHost(h_active);
   if (h_last) cudaFreeHost(h_last);
@@ -71,52 +95,88 @@ BatchArgs Engine::args() const {
   a.twf = geo->d_twf; a.hsf = geo->d_hsf; a.chf = geo->d_chf; a.Bf = geo->d_Bf;
   a.tw2 = tw2; a.Bf2 = Bf2;
   a.logMmax = geo->logMmax;
-  a.lam = lam;
   a.lmax = geo->lmax; a.RP = geo->RP; a.R = geo->R; a.B = B;
   a.npix = geo->npix; a.nalm = geo->nalm; a.omega = geo->omega;
   a.d = d; a.w = w; a.cl = cl; a.dw32 = dw32;
-  a.s = s; a.sdf = sdf; a.fdf = fdf; a.icl = icl; a.FS = FS; a.FT = FT; a.SP = SP;
+  a.s = s; a.sdf = sdf; a.fdf = fdf; a.icl = icl; a.FS = FS; a.FT = FT;
   a.ctl = ctl; a.active = active; a.ring_part = ring_part; a.m_part = m_part;
-  a.ntiles = ntiles; a.tiles = tiles; a.stiles = stiles; a.bstate = bstate; a.last = last;
+  a.ntiles = natiles; a.bstate = bstate; a.last = last;
   return a;
 }
 
+TcArgs Engine::tc_args() const {
+  TcArgs t{};
+  t.Nc = 2 * B;
+  t.RPp = RPp;
+  t.nkc = RPp / 32;
+  t.atiles = atiles;
+  t.natiles = natiles;
+  t.stiles = tstiles;
+  t.nstiles = ntstiles;
+  t.offTc = offTc;
+  t.XT = XT;
+  t.SPT = SPT;
+  t.err = err;
+  return t;
+}
+
+
 wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   geo = shape_plan;
-  B = nslots;
   stream = s_;
-  if (B < 1 || B > kBatchMax) { set_error("batched engine: slots must be in [1, 64]"); return WF_EINVAL; }
+  if (nslots < 1 || nslots > kBatchMax) { set_error("batched engine: slots must be in [1, 64]"); return WF_EINVAL; }
+  B = round_up(nslots, 8);   // GEMM columns 2 B: a multiple of 16
   const int lmax = geo->lmax, RP = geo->RP, R = geo->R;
   const size_t nalm = geo->nalm, npix = geo->npix, nF = (size_t)(lmax + 1) * RP;
-  std::vector<int2> ana, syn;
-  make_tiles(lmax, RP, ana, syn);
-  ntiles = (int)ana.size();
-  nstiles = (int)syn.size();
+  RPp = round_up(RP, 32);
+  const size_t Nc = 2 * (size_t)B;
+  std::vector<int4> ana;
+  std::vector<int2> syn;
+  std::vector<int> off;
+  make_tc_lists(lmax, RPp, ana, syn, off, nchunks);
+  natiles = (int)ana.size();
+  ntstiles = (int)syn.size();
+  const size_t nXT = (size_t)(lmax + 1) * 2 * RPp * Nc, nSPT = (size_t)nchunks * 32 * Nc;
   wf_status st;
-  if ((st = dalloc((void **)&lam, sizeof(float) * nalm * RP)) ||
+  if ((st = dalloc((void **)&lamA, sizeof(float) * nalm * RPp)) ||
+      (st = dalloc((void **)&lamT, sizeof(float) * (size_t)nchunks * 32 * RPp)) ||
+      (st = dalloc((void **)&XT, sizeof(float) * nXT)) || (st = dalloc((void **)&SPT, sizeof(float) * nSPT)) ||
+      (st = dalloc((void **)&atiles, sizeof(int4) * ana.size())) ||
+      (st = dalloc((void **)&tstiles, sizeof(int2) * syn.size())) ||
+      (st = dalloc((void **)&offTc, sizeof(int) * off.size())) || (st = dalloc((void **)&err, sizeof(int))) ||
       (st = dalloc((void **)&tw2, sizeof(float2) * std::max<long long>(geo->n_tw, 1))) ||
-      (st = dalloc((void **)&Bf2, sizeof(float2) * std::max<long long>(geo->n_B, 1))) || (st = dalloc((void **)&FS, sizeof(float4) * nF * B)) ||
-      (st = dalloc((void **)&FT, sizeof(float4) * nF * B)) || (st = dalloc((void **)&SP, sizeof(float2) * nalm * B)) ||
+      (st = dalloc((void **)&Bf2, sizeof(float2) * std::max<long long>(geo->n_B, 1))) ||
+      (st = dalloc((void **)&FS, sizeof(float4) * nF * B)) || (st = dalloc((void **)&FT, sizeof(float4) * nF * B)) ||
       (st = dalloc((void **)&d, sizeof(double) * npix * B)) || (st = dalloc((void **)&w, sizeof(double) * npix * B)) ||
       (st = dalloc((void **)&dw32, sizeof(float2) * npix * B)) ||
       (st = dalloc((void **)&cl, sizeof(double) * (lmax + 1) * B)) ||
       (st = dalloc((void **)&s, sizeof(double2) * nalm * B)) || (st = dalloc((void **)&sdf, sizeof(float4) * nalm * B)) ||
-      (st = dalloc((void **)&fdf, sizeof(float2) * (lmax + 1) * B)) || (st = dalloc((void **)&icl, sizeof(float) * (lmax + 1) * B)) || (st = dalloc((void **)&ctl, sizeof(Ctl) * B)) ||
+      (st = dalloc((void **)&fdf, sizeof(float2) * (lmax + 1) * B)) ||
+      (st = dalloc((void **)&icl, sizeof(float) * (lmax + 1) * B)) || (st = dalloc((void **)&ctl, sizeof(Ctl) * B)) ||
       (st = dalloc((void **)&active, sizeof(int) * B)) ||
       (st = dalloc((void **)&ring_part, sizeof(double) * 2 * R * B)) ||
-      (st = dalloc((void **)&m_part, sizeof(double) * 3 * (size_t)ntiles * B)) ||
-      (st = dalloc((void **)&tiles, sizeof(int2) * ana.size())) ||
-      (st = dalloc((void **)&stiles, sizeof(int2) * syn.size())) || (st = dalloc((void **)&bstate, sizeof(int) * 2)) ||
-      (st = dalloc((void **)&last, sizeof(wf_iter_record) * B)))
+      (st = dalloc((void **)&m_part, sizeof(double) * 3 * (size_t)natiles * B)) ||
+      (st = dalloc((void **)&bstate, sizeof(int) * 2)) || (st = dalloc((void **)&last, sizeof(wf_iter_record) * B)))
     return st;
+  if (!make_tc_map(&maps.A, lamA, RPp, nalm, 128) || !make_tc_map(&maps.X, XT, 32, nXT / 32, (unsigned)Nc) ||
+      !make_tc_map(&maps.T, lamT, 32, (size_t)nchunks * RPp, 128) ||
+      !make_tc_map(&maps.S, SPT, 32, (size_t)nchunks * Nc, (unsigned)Nc)) {
+    set_error("batched engine: cuTensorMapEncodeTiled failed");
+    return WF_ECUDA;
+  }
   ENG_CUDA(cudaMallocHost((void **)&h_ctl, sizeof(Ctl) * B));
   ENG_CUDA(cudaMallocHost((void **)&h_active, sizeof(int) * B));
   ENG_CUDA(cudaMallocHost((void **)&h_last, sizeof(wf_iter_record) * B));
+  ENG_CUDA(cudaMallocHost((void **)&h_err, sizeof(int)));
   std::fill(h_active, h_active + B, 0);
-  ENG_CUDA(cudaMemcpyAsync(tiles, ana.data(), sizeof(int2) * ana.size(), cudaMemcpyHostToDevice, stream));
-  ENG_CUDA(cudaMemcpyAsync(stiles, syn.data(), sizeof(int2) * syn.size(), cudaMemcpyHostToDevice, stream));
+  *h_err = 0;
+  ENG_CUDA(cudaMemcpyAsync(atiles, ana.data(), sizeof(int4) * ana.size(), cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(tstiles, syn.data(), sizeof(int2) * syn.size(), cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(offTc, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, stream));
   launch_hi_table(geo->d_twf, tw2, geo->n_tw, stream);
   launch_hi_table(geo->d_Bf, Bf2, geo->n_B, stream);
+  ENG_CUDA(cudaMemsetAsync(SPT, 0, sizeof(float) * nSPT, stream));
+  ENG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), stream));
   ENG_CUDA(cudaMemsetAsync(FS, 0, sizeof(float4) * nF * B, stream));
   ENG_CUDA(cudaMemsetAsync(FT, 0, sizeof(float4) * nF * B, stream));
   ENG_CUDA(cudaMemsetAsync(s, 0, sizeof(double2) * nalm * B, stream));
@@ -126,7 +186,7 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ENG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) * B, stream));
   ENG_CUDA(cudaMemsetAsync(active, 0, sizeof(int) * B, stream));
   ENG_CUDA(cudaMemsetAsync(last, 0, sizeof(wf_iter_record) * B, stream));
-  launch_lam_table(geo->d_x, geo->legdf_args(), lmax, RP, lam, stream);
+  launch_lam_tc_tables(geo->d_x, geo->legdf_args(), lmax, RP, RPp, offTc, lamA, lamT, stream);
   launch_batch_state(args(), bstate, stream);
   ENG_CUDA(cudaGetLastError());
   ENG_CUDA(cudaStreamSynchronize(stream));
@@ -137,7 +197,7 @@ wf_status Engine::load_slot(int b, const double *dsrc, int d_on_device, const do
                             const Ctl &c) {
   const int lmax = geo->lmax;
   const size_t npix = geo->npix;
-  launch_batch_zero_slot(args(), b, stream);
+  launch_batch_zero_slot(args(), tc_args(), nchunks, b, stream);
   ENG_CUDA(cudaMemcpyAsync(d + b * npix, dsrc, sizeof(double) * npix,
                            d_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
   ENG_CUDA(cudaMemcpyAsync(w + b * npix, wsrc_dev, sizeof(double) * npix, cudaMemcpyDeviceToDevice, stream));
@@ -155,7 +215,7 @@ wf_status Engine::load_slot_host(int b, const double *d_host, const double *w_ho
                                  const Ctl &c) {
   const int lmax = geo->lmax;
   const size_t npix = geo->npix;
-  launch_batch_zero_slot(args(), b, stream);
+  launch_batch_zero_slot(args(), tc_args(), nchunks, b, stream);
   ENG_CUDA(cudaMemcpyAsync(d + b * npix, d_host, sizeof(double) * npix, cudaMemcpyHostToDevice, stream));
   ENG_CUDA(cudaMemcpyAsync(w + b * npix, w_host, sizeof(double) * npix, cudaMemcpyHostToDevice, stream));
   launch_batch_convert_slot(args(), b, stream);
@@ -190,7 +250,8 @@ wf_status Engine::step() {
   if (!graph) {
     cudaGraph_t g;
     ENG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < graph_iters; ++i) launch_batch_iteration(args(), geo->rclass.data(), (int)geo->rclass.size(), nstiles, bstate, stream);
+    for (int i = 0; i < graph_iters; ++i)
+      launch_batch_iteration(args(), tc_args(), maps, geo->rclass.data(), (int)geo->rclass.size(), bstate, stream);
     ENG_CUDA(cudaStreamEndCapture(stream, &g));
     cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
     cudaGraphDestroy(g);
@@ -199,11 +260,16 @@ wf_status Engine::step() {
   ENG_CUDA(cudaGraphLaunch(graph, stream));
   ENG_CUDA(cudaMemcpyAsync(h_ctl, ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost, stream));
   ENG_CUDA(cudaMemcpyAsync(h_last, last, sizeof(wf_iter_record) * B, cudaMemcpyDeviceToHost, stream));
+  ENG_CUDA(cudaMemcpyAsync(h_err, err, sizeof(int), cudaMemcpyDeviceToHost, stream));
   return WF_OK;
 }
 
 wf_status Engine::sync_host() {
   ENG_CUDA(cudaStreamSynchronize(stream));
+  if (*h_err) {
+    set_error("batched engine: a tensor-core pipeline wait timed out");
+    return WF_ECUDA;
+  }
   return WF_OK;
 }
 

@@ -5,6 +5,7 @@
 // iterating (continuous batching).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -14,6 +15,16 @@
 
 namespace wfk {
 
+// TMA descriptors of the tensor-core Legendre stage (batch_tc.cu)
+struct TcMaps {
+  CUtensorMap A, X, T, S;    // lamA, XT, lamT, SPT
+};
+
+bool make_tc_map(CUtensorMap *map, const float *base, unsigned long long inner, unsigned long long rows,
+                 unsigned box_rows);
+// which = 0: FT -> XT and the analysis GEMM with Eq. 4; 1: the synthesis GEMM
+void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which);
+
 struct Engine {
   Plan *geo = nullptr;  // tables of the shape (not owned)
   int B = 0;
@@ -22,10 +33,16 @@ struct Engine {
   size_t device_bytes = 0;
   std::vector<void *> allocs;
 
-  float *lam = nullptr;
   float2 *tw2 = nullptr, *Bf2 = nullptr;   // FP32 twiddle / Bluestein tables
+  // tensor-core Legendre stage
+  float *lamA = nullptr, *lamT = nullptr, *XT = nullptr, *SPT = nullptr;
+  int4 *atiles = nullptr;
+  int2 *tstiles = nullptr;
+  int *offTc = nullptr;
+  int *err = nullptr, *h_err = nullptr;
+  int natiles = 0, ntstiles = 0, nchunks = 0, RPp = 0;
+  TcMaps maps{};
   float4 *FS = nullptr, *FT = nullptr;
-  float2 *SP = nullptr;
   double *d = nullptr, *w = nullptr, *cl = nullptr;
   float2 *dw32 = nullptr;   // [B][npix] (d, w) in FP32 for the ring stage
   double2 *s = nullptr;      // exported a_lm of finished slots
@@ -35,8 +52,6 @@ struct Engine {
   Ctl *ctl = nullptr;
   int *active = nullptr;
   double *ring_part = nullptr, *m_part = nullptr;
-  int2 *tiles = nullptr, *stiles = nullptr;
-  int ntiles = 0, nstiles = 0;
   int *bstate = nullptr;
   wf_iter_record *last = nullptr;
   // pinned host mirrors
@@ -48,6 +63,7 @@ struct Engine {
   ~Engine();
   wf_status create(Plan *shape_plan, int nslots, cudaStream_t s);
   BatchArgs args() const;
+  TcArgs tc_args() const;
   wf_status dalloc(void **p, size_t bytes);
   // Load one problem into slot b (device state zeroed, controller initialised).
   //   dsrc: [npix] data (host or device), wsrc: [npix] inverse noise (device),

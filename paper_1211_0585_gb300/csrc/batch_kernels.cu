@@ -15,6 +15,7 @@
 
 #include <algorithm>
 
+#include "batch_engine.h"
 #include "ctl.cuh"
 #include "df.cuh"
 #include "fft.cuh"
@@ -24,10 +25,7 @@ namespace wfk {
 
 namespace {
 
-__device__ __forceinline__ size_t aidx(int lmax, int l, int m) { return (size_t)m * (2 * lmax + 1 - m) / 2 + l; }
-
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -35,36 +33,6 @@ __device__ __forceinline__ float2 f2conj(float2 a) { return make_float2(a.x, -a.
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.x, v.z); }  // hi parts of a df complex
 
 }  // namespace
-
-// Lambda table: one thread per (m, k) runs the double-float recurrence from
-// its start values and writes lambda_lm(x_k) for every l (0 below l_start).
-__global__ void lam_table_kernel(const double *xk, const LegDfArgs D, int lmax, int RP, float *lam) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (long long)(lmax + 1) * RP) return;
-  const int m = (int)(id / RP), k = (int)(id % RP);
-  const size_t mk = (size_t)m * RP + k;
-  const int ls = D.ls[mk];
-  const float4 s4 = D.sv[mk];
-  const dfl x = df_from(xk[k]);
-  const size_t base = aidx(lmax, m, m);
-  dfl p1 = {0.f, 0.f}, p2 = {0.f, 0.f};
-  for (int l = m; l <= lmax; ++l) {
-    float v = 0.f;
-    if (l >= ls) {
-      dfl mu;
-      if (l == ls) mu = dfl{s4.x, s4.y};
-      else if (l == ls + 1) mu = dfl{s4.z, s4.w};
-      else {
-        const float2 a2 = D.A[base + (l - m)];
-        mu = df_step(dfl{a2.x, a2.y}, x, p1, p2);
-      }
-      p2 = p1;
-      p1 = mu;
-      v = (float)(D.g[base + (l - m)] * df_to(mu));
-    }
-    lam[(base + (l - m)) * (size_t)RP + k] = v;
-  }
-}
 
 // ---------------------------------------------------------------- ring stage
 // One CTA per (ring, group of G slots). The ring values of every slot are
@@ -262,222 +230,6 @@ __global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs
   }
 }
 
-// ---------------------------------------------------------------- analysis GEMM + Eq. 4
-// Tile: 64 values of l (32 of each parity of l - m) x all slots, reduced over
-// every ring pair in chunks of 32. Thread (par, rg, cg): rows par + 2 (4 rg + i),
-// i < 4, columns 8 cg .. 8 cg + 7 of the 2 B (re, im) columns.
-constexpr int kAT = 64, kKC = 32;
-
-__global__ void __launch_bounds__(256) bana_kernel(const BatchArgs A) {
-  __shared__ __align__(16) float Lt[kKC][2][32];           // [k][parity][row]
-  __shared__ __align__(16) float XEO[2][kKC][2 * kBatchMax];  // E / O: [k][2 b + re/im]
-  float(*XE)[2 * kBatchMax] = XEO[0];
-  float(*XO)[2 * kBatchMax] = XEO[1];
-  // after the k loop the X tiles are dead; the epilogue partials reuse them
-  double(*part)[16][3] = reinterpret_cast<double(*)[16][3]>(&XEO[0][0][0]);
-  const int2 tile = A.tiles[blockIdx.x];
-  const int m = tile.x, l0 = tile.y;
-  const int Lact = A.bstate[0];
-  const int B = A.B, RP = A.RP, lmax = A.lmax;
-  const int t = threadIdx.x;
-  const int cg = t & 15, rgp = t >> 4;          // column group, row group (0..15)
-  const int par = rgp & 1, rg = rgp >> 1;       // parity, row group within parity (0..7)
-  const bool live = m <= Lact && l0 <= Lact;
-  // chunk sums folded into double-float accumulators (two_sum on the FP32 pipe)
-  float ah[4][8], al[4][8];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) { ah[i][j] = 0.f; al[i][j] = 0.f; }
-  if (live) {
-    const size_t base = aidx(lmax, m, m);
-    for (int k0 = 0; k0 < RP; k0 += kKC) {
-      for (int e = t; e < kAT * kKC; e += 256) {
-        const int row = e / kKC, kk = e % kKC;
-        const int l = l0 + row, k = k0 + kk;
-        float v = 0.f;
-        if (l <= lmax && l <= Lact && k < RP) v = A.lam[(base + (l - m)) * (size_t)RP + k];
-        Lt[kk][row & 1][row >> 1] = v;
-      }
-      for (int e = t; e < kKC * B; e += 256) {
-        const int kk = e / B, bb = e % B, k = k0 + kk;
-        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < RP) f = A.FT[((size_t)m * RP + k) * B + bb];
-        XE[kk][2 * bb] = f.x + f.z;
-        XE[kk][2 * bb + 1] = f.y + f.w;
-        XO[kk][2 * bb] = f.x - f.z;
-        XO[kk][2 * bb + 1] = f.y - f.w;
-      }
-      __syncthreads();
-      if (8 * cg < 2 * B) {
-        float pa[4][8];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) pa[i][j] = 0.f;
-        const float(*X)[2 * kBatchMax] = par ? XO : XE;
-#pragma unroll 8
-        for (int kk = 0; kk < kKC; ++kk) {
-          const float4 a = *reinterpret_cast<const float4 *>(&Lt[kk][par][4 * rg]);
-          const float4 x0 = *reinterpret_cast<const float4 *>(&X[kk][8 * cg]);
-          const float4 x1 = *reinterpret_cast<const float4 *>(&X[kk][8 * cg + 4]);
-          const float av[4] = {a.x, a.y, a.z, a.w};
-          const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) pa[i][j] = fmaf(av[i], xv[j], pa[i][j]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float s = ah[i][j] + pa[i][j];
-            const float bb = s - ah[i][j];
-            al[i][j] += (ah[i][j] - (s - bb)) + (pa[i][j] - bb);
-            ah[i][j] = s;
-          }
-      }
-      __syncthreads();
-    }
-  }
-  // epilogue: Eq. 4 per (l, slot) on the double-float state (f_l from the
-  // per-iteration table, 0 above the slot's band limit and where C_l = 0),
-  // prior chi^2 / increment / norm partials in FP32 (all on the FP32 pipe)
-#pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
-    const int bb = 4 * cg + jj;      // slot of columns 8 cg + 2 jj, + 1
-    float c2 = 0.f, inc = 0.f, nrm = 0.f;
-    if (bb < B && A.active[bb] && !A.ctl[bb].done) {
-      const float2 *fb = A.fdf + (size_t)bb * (lmax + 1);
-      const float *ib = A.icl + (size_t)bb * (lmax + 1);
-      float4 *sb = A.sdf + (size_t)bb * A.nalm;
-      const float wgt = (m == 0) ? 1.f : 2.f;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int l = l0 + par + 2 * (4 * rg + i);
-        if (l > lmax) continue;
-        const size_t idx = aidx(lmax, l, m);
-        const float4 so = sb[idx];
-        float4 sn = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (live) {
-          const float2 f2 = fb[l];
-          const dfl f = dfl{f2.x, f2.y};
-          const dfl re = df_mul(f, df_add(dfl{so.x, so.y}, dfl{ah[i][2 * jj], al[i][2 * jj]}));
-          const dfl im = df_mul(f, df_add(dfl{so.z, so.w}, dfl{ah[i][2 * jj + 1], al[i][2 * jj + 1]}));
-          sn = make_float4(re.h, re.l, im.h, im.l);
-        }
-        c2 += wgt * (so.x * so.x + so.z * so.z) * ib[l];
-        const float dx = (sn.x - so.x) + (sn.y - so.y), dy = (sn.z - so.z) + (sn.w - so.w);
-        inc += wgt * (dx * dx + dy * dy);
-        nrm += wgt * (sn.x * sn.x + sn.z * sn.z);
-        sb[idx] = sn;
-        A.SP[idx * B + bb] = make_float2(sn.x, sn.z);
-      }
-    }
-    if (bb < kBatchMax) {
-      part[bb][rgp][0] = c2;
-      part[bb][rgp][1] = inc;
-      part[bb][rgp][2] = nrm;
-    }
-  }
-  __syncthreads();
-  for (int bb = t; bb < B; bb += 256) {
-    double a = 0.0, bsum = 0.0, cs = 0.0;
-    for (int q = 0; q < 16; ++q) { a += part[bb][q][0]; bsum += part[bb][q][1]; cs += part[bb][q][2]; }
-    double *dst = A.m_part + ((size_t)bb * A.ntiles + blockIdx.x) * 3;
-    dst[0] = a;
-    dst[1] = bsum;
-    dst[2] = cs;
-  }
-}
-
-// ---------------------------------------------------------------- synthesis GEMM
-// Tile: 32 ring pairs x all slots; E (l - m even) and O (odd) accumulated by
-// separate thread halves over l = m .. Lact in chunks of 32.
-constexpr int kST = 32, kLC = 32;
-
-__global__ void __launch_bounds__(256) bsyn_kernel(const BatchArgs A) {
-  __shared__ __align__(16) float Ls[kLC][kST];              // [l][k]
-  __shared__ __align__(16) float Ss[kLC][2 * kBatchMax];    // [l][2 b + re/im]
-  __shared__ __align__(16) float OutE[kST][2 * kBatchMax];  // E sums, read by the O half
-  const int2 tile = A.stiles[blockIdx.x];
-  const int m = tile.x, k0 = tile.y;
-  const int Lact = A.bstate[0];
-  const int B = A.B, RP = A.RP, lmax = A.lmax;
-  const int t = threadIdx.x;
-  if (m > Lact) {
-    for (int e = t; e < kST * B; e += 256) {
-      const int kk = e / B, bb = e % B, k = k0 + kk;
-      if (k < RP) A.FS[((size_t)m * RP + k) * B + bb] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    return;
-  }
-  const int eo = t >> 7;                  // 0: E (even l - m), 1: O
-  const int tt = t & 127;
-  const int cg = tt & 15, kg = tt >> 4;   // column group (8 columns), ring group (4 rings)
-  const size_t base = aidx(lmax, m, m);
-  float acc[4][8];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  for (int lc = m; lc <= Lact; lc += kLC) {
-    for (int e = t; e < kLC * kST; e += 256) {
-      const int ll = e / kST, kk = e % kST;
-      const int l = lc + ll, k = k0 + kk;
-      float v = 0.f;
-      if (l <= Lact && k < RP) v = A.lam[(base + (l - m)) * (size_t)RP + k];
-      Ls[ll][kk] = v;
-    }
-    for (int e = t; e < kLC * B; e += 256) {
-      const int ll = e / B, bb = e % B, l = lc + ll;
-      float2 v = make_float2(0.f, 0.f);
-      if (l <= Lact) v = A.SP[(base + (l - m)) * B + bb];
-      Ss[ll][2 * bb] = v.x;
-      Ss[ll][2 * bb + 1] = v.y;
-    }
-    __syncthreads();
-    if (8 * cg < 2 * B) {
-#pragma unroll 4
-      for (int ll = eo; ll < kLC; ll += 2) {
-        const float4 a = *reinterpret_cast<const float4 *>(&Ls[ll][4 * kg]);
-        const float4 x0 = *reinterpret_cast<const float4 *>(&Ss[ll][8 * cg]);
-        const float4 x1 = *reinterpret_cast<const float4 *>(&Ss[ll][8 * cg + 4]);
-        const float av[4] = {a.x, a.y, a.z, a.w};
-        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
-      }
-    }
-    __syncthreads();
-  }
-  if (eo == 0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) OutE[4 * kg + i][8 * cg + j] = acc[i][j];
-  }
-  __syncthreads();
-  if (eo == 1 && 8 * cg < 2 * B) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int k = k0 + 4 * kg + i;
-      if (k >= RP) continue;
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int bb = 4 * cg + jj;
-        if (bb >= B) continue;
-        const float er = OutE[4 * kg + i][2 * bb], ei = OutE[4 * kg + i][2 * bb + 1];
-        const float orr = acc[i][2 * jj], oi = acc[i][2 * jj + 1];
-        A.FS[((size_t)m * RP + k) * B + bb] = make_float4(er + orr, ei + oi, er - orr, ei - oi);
-      }
-    }
-  }
-}
-
 // ---------------------------------------------------------------- control
 __global__ void __launch_bounds__(256) bctl_kernel(const BatchArgs A) {
   __shared__ double sh[5][256];
@@ -522,13 +274,19 @@ __global__ void bstate_kernel(const BatchArgs A, int *bstate) {
   }
 }
 
-// reset slot b: zero its state and its synthesis coefficients
-__global__ void bzero_slot_kernel(const BatchArgs A, int b) {
+// reset slot b: zero its state, its Fourier coefficients and its columns of
+// the synthesis operand (2 b, 2 b + 1 of every 32-wide chunk)
+__global__ void bzero_slot_kernel(const BatchArgs A, const TcArgs T, long long nchunks, int b) {
   const long long nF = (long long)(A.lmax + 1) * A.RP;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += (long long)gridDim.x * blockDim.x)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += stride)
     A.FS[i * A.B + b] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nalm; i += (long long)gridDim.x * blockDim.x)
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nalm; i += stride)
     A.sdf[(size_t)b * A.nalm + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nchunks * 64; i += stride) {
+    const long long q = i >> 6, e = i & 63;   // chunk, (column 2 b or 2 b + 1, i within the chunk)
+    T.SPT[(q * T.Nc + 2 * b + (e >> 5)) * 32 + (e & 31)] = 0.f;
+  }
 }
 
 // the double-float state of slot b as double a_lm (export of a finished solve)
@@ -571,10 +329,6 @@ void launch_batch_export_slot(const BatchArgs &a, int b, cudaStream_t s) {
   bexport_slot_kernel<<<256, 256, 0, s>>>(a, b);
 }
 
-void launch_lam_table(const double *x, const LegDfArgs &D, int lmax, int RP, float *lam, cudaStream_t s) {
-  const long long n = (long long)(lmax + 1) * RP;
-  lam_table_kernel<<<(int)((n + 127) / 128), 128, 0, s>>>(x, D, lmax, RP, lam);
-}
 
 // FP32 copies of slot b's data and inverse noise for the ring stage
 __global__ void bconvert_slot_kernel(const BatchArgs A, int b) {
@@ -606,8 +360,8 @@ static void launch_bring(const BatchArgs &a, const RingClass &c, cudaStream_t s)
   bring_kernel<G><<<dim3(c.count, (a.B + G - 1) / G), kBringThreads, sm, s>>>(ac);
 }
 
-void launch_batch_iteration(const BatchArgs &a, const RingClass *cls, int ncls, int n_stiles, int *bstate,
-                            cudaStream_t s) {
+void launch_batch_iteration(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, const RingClass *cls, int ncls,
+                            int *bstate, cudaStream_t s) {
   raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<2>));
   raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<4>));
   raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<8>));
@@ -619,8 +373,8 @@ void launch_batch_iteration(const BatchArgs &a, const RingClass *cls, int ncls, 
     else launch_bring<2>(a, cls[c], s);
   }
   bfilter_kernel<<<a.B, 256, 0, s>>>(a);
-  bana_kernel<<<a.ntiles, 256, 0, s>>>(a);
-  bsyn_kernel<<<n_stiles, 256, 0, s>>>(a);
+  launch_batch_gemms_tc(a, t, maps, s, 0);   // FT -> XT, analysis GEMM, Eq. 4
+  launch_batch_gemms_tc(a, t, maps, s, 1);   // synthesis GEMM
   bctl_kernel<<<a.B, 256, 0, s>>>(a);
   bstate_kernel<<<1, kBatchMax, 0, s>>>(a, bstate);
 }
@@ -629,8 +383,8 @@ void launch_batch_state(const BatchArgs &a, int *bstate, cudaStream_t s) {
   bstate_kernel<<<1, kBatchMax, 0, s>>>(a, bstate);
 }
 
-void launch_batch_zero_slot(const BatchArgs &a, int b, cudaStream_t s) {
-  bzero_slot_kernel<<<512, 256, 0, s>>>(a, b);
+void launch_batch_zero_slot(const BatchArgs &a, const TcArgs &t, long long nchunks, int b, cudaStream_t s) {
+  bzero_slot_kernel<<<512, 256, 0, s>>>(a, t, nchunks, b);
 }
 
 }  // namespace wfk

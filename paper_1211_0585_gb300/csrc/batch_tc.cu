@@ -1,0 +1,637 @@
+// Tensor-core Legendre stage of the batched engine (tcgen05, kind::tf32).
+//
+// Per m, the two contractions of the messenger iteration are GEMMs over the
+// shape's Legendre table Lambda_m[l][k] = lambda_lm(x_k) (Sect. 2: the basis
+// change between pixel and harmonic space, its Legendre half):
+//   analysis   t_p[i][c] = sum_k  Lambda[l_i][k] X_p[k][c]   (X_0 = N + S, X_1 = N - S)
+//   synthesis  D_p[k][c] = sum_i  Lambda[l_i][k] s[l_i][c]   (E = D_0, O = D_1; N = E + O, S = E - O)
+// with l_i = m + p + 2 i (parity p of l - m), c = 2 b + (re, im) over the slots.
+// The Legendre tables hold lambda rounded to 22 significant bits, so that a
+// table value is exactly the sum of two tf32 numbers, th + tl; the data operand
+// (X or s, FP32) is split exactly into three, ah + am + al (11 + 11 + 2 bits).
+// The tensor cores form th ah + th am + tl ah + tl am + th al (every partial
+// product at or above 2^-24 of the whole; the one dropped, tl al, is 2^-33) with
+// fp32 accumulation in tensor memory: FP32-level products from tf32 inputs.
+//
+// Tables (built once per shape from the double-float recurrence):
+//   lamA  rows (m, p, i) in that order, ring pairs k contiguous (padded to RPp, a
+//         multiple of 32): the analysis A operand, one TMA box = 128 rows x 32 k;
+//   lamT  rows (m, p, chunk of 32 i, k), 32 values of i contiguous: the synthesis
+//         A operand, one TMA box = 128 ring pairs x 32 i.
+// Per-iteration operands (written by the engine's own kernels):
+//   XT    rows (m, p, chunk of 32 k, c), 32 values of k contiguous (from FT);
+//   SPT   rows (m, p, chunk of 32 i, c), 32 values of i contiguous (written by the
+//         analysis epilogue for the next synthesis).
+//
+// Each GEMM CTA is warp-specialised: warp 0 issues the TMA loads of a 3-stage
+// pipeline, warp 1 owns the tensor memory and issues the MMAs, warps 2-5 split
+// each landed tile into its tf32 parts and then run the epilogue.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "batch_engine.h"
+#include "df.cuh"
+#include "tc.cuh"
+#include "wf_internal.h"
+
+namespace wfk {
+
+namespace {
+
+constexpr int kStages = 2;
+constexpr int kTileRows = 128;                       // M of every MMA
+constexpr int kTileBytes = kTileRows * 128;          // 128 rows x 32 fp32
+constexpr int kGemmThreads = 192;
+constexpr uint32_t kWaitLimit = 1u << 22;            // polls of one bounded mbarrier wait
+
+__device__ __forceinline__ size_t aidx(int lmax, int l, int m) { return (size_t)m * (2 * lmax + 1 - m) / 2 + l; }
+
+// number of l in [m, L] with l - m = p (mod 2)
+__host__ __device__ __forceinline__ int n_par(int m, int p, int L) { return L >= m + p ? (L - m - p) / 2 + 1 : 0; }
+
+enum { kTA = 0, kTAlo = 1, kTB = 2, kTBmid = 3, kTBlo = 4, kTiles = 5 };
+
+struct Smem {
+  // per stage: table hi (landed raw), table lo, data hi (landed raw), data mid,
+  // data lo; every tile 1024-byte aligned
+  __device__ static uint8_t *tile(uint8_t *base, int s, int which) {
+    return base + ((size_t)s * kTiles + which) * kTileBytes;
+  }
+};
+
+// table tile (22-bit values): th in place, tl = v - th (exact)
+__device__ __forceinline__ void split_table(uint8_t *hi, uint8_t *lo, int nbytes, int t, int nt) {
+  float4 *h4 = reinterpret_cast<float4 *>(hi);
+  float4 *l4 = reinterpret_cast<float4 *>(lo);
+  for (int e = t; e < nbytes / 16; e += nt) {
+    const float4 v = h4[e];
+    float4 h, l;
+    h.x = tc::to_tf32(v.x); l.x = tc::to_tf32(v.x - h.x);
+    h.y = tc::to_tf32(v.y); l.y = tc::to_tf32(v.y - h.y);
+    h.z = tc::to_tf32(v.z); l.z = tc::to_tf32(v.z - h.z);
+    h.w = tc::to_tf32(v.w); l.w = tc::to_tf32(v.w - h.w);
+    h4[e] = h;
+    l4[e] = l;
+  }
+}
+
+__device__ __forceinline__ void split3(float v, float &h, float &m, float &l) {
+  h = tc::to_tf32(v);
+  const float r = v - h;   // exact
+  m = tc::to_tf32(r);
+  l = tc::to_tf32(r - m);  // exact: at most 2 significant bits remain
+}
+
+// data tile (FP32): ah in place, am, al (ah + am + al = v exactly)
+__device__ __forceinline__ void split_data(uint8_t *hi, uint8_t *mid, uint8_t *lo, int nbytes, int t, int nt) {
+  float4 *h4 = reinterpret_cast<float4 *>(hi);
+  float4 *m4 = reinterpret_cast<float4 *>(mid);
+  float4 *l4 = reinterpret_cast<float4 *>(lo);
+  for (int e = t; e < nbytes / 16; e += nt) {
+    const float4 v = h4[e];
+    float4 h, m, l;
+    split3(v.x, h.x, m.x, l.x);
+    split3(v.y, h.y, m.y, l.y);
+    split3(v.z, h.z, m.z, l.z);
+    split3(v.w, h.w, m.w, l.w);
+    h4[e] = h;
+    m4[e] = m;
+    l4[e] = l;
+  }
+}
+
+// 4 k-steps of 8 over one 32-wide chunk of stage tiles, five products per
+// step. The leading product th ah accumulates alone in `dmain`; the four
+// correction products (2^-11 and less of it) accumulate in `dcorr`, so the
+// rounding of the tensor-core accumulation stays relative to each sum's own
+// size (the leading sum is not perturbed by the many small additions).
+// REV runs the k-steps from the end of the chunk to its start.
+template <bool REV = false>
+__device__ __forceinline__ void mma_chunk(uint32_t dmain, uint32_t dcorr, uint8_t *stage, uint32_t idesc,
+                                          bool acc_main, bool acc_corr) {
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const int ks = REV ? 3 - kk : kk;
+    const uint64_t off = (uint64_t)((ks * 32) >> 4);   // 32 bytes along K inside the swizzle atom
+    const uint64_t th = tc::sw128_desc(stage + kTA * kTileBytes) + off;
+    const uint64_t tl = tc::sw128_desc(stage + kTAlo * kTileBytes) + off;
+    const uint64_t ah = tc::sw128_desc(stage + kTB * kTileBytes) + off;
+    const uint64_t am = tc::sw128_desc(stage + kTBmid * kTileBytes) + off;
+    const uint64_t al = tc::sw128_desc(stage + kTBlo * kTileBytes) + off;
+    tc::mma_tf32(dmain, th, ah, idesc, acc_main || kk > 0);
+    tc::mma_tf32(dcorr, th, am, idesc, acc_corr || kk > 0);
+    tc::mma_tf32(dcorr, tl, ah, idesc, true);
+    tc::mma_tf32(dcorr, tl, am, idesc, true);
+    tc::mma_tf32(dcorr, th, al, idesc, true);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- tables
+// One thread per (m, k): the double-float recurrence from the start values
+// writes lambda_lm(x_k) (rounded to 22 bits, 0 below l_start) into both table
+// layouts; rows of the transposed layout are written 32 values at a time from
+// registers.
+__global__ void lam_tc_tables_kernel(const double *xk, const LegDfArgs D, int lmax, int RP, int RPp,
+                                     const int *offTc, float *lamA, float *lamT) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)(lmax + 1) * RPp) return;
+  const int m = (int)(id / RPp), k = (int)(id % RPp);
+  const size_t base = aidx(lmax, m, m);
+  const int n0 = n_par(m, 0, lmax);
+  float buf[2][32];
+  if (k >= RP) {   // padding ring pairs: zeros
+    for (int p = 0; p < 2; ++p) {
+      const int np = n_par(m, p, lmax);
+      for (int i = 0; i < np; ++i) lamA[(base + (p ? n0 + i : i)) * (size_t)RPp + k] = 0.f;
+      for (int ic = 0; ic < (np + 31) / 32; ++ic) {
+        float4 *dst = reinterpret_cast<float4 *>(lamT + ((size_t)(offTc[2 * m + p] + ic) * RPp + k) * 32);
+        for (int j = 0; j < 8; ++j) dst[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    return;
+  }
+  const size_t mk = (size_t)m * RP + k;
+  const int ls = D.ls[mk];
+  const float4 s4 = D.sv[mk];
+  const dfl x = df_from(xk[k]);
+  dfl p1 = {0.f, 0.f}, p2 = {0.f, 0.f};
+  for (int l = m; l <= lmax; ++l) {
+    float v = 0.f;
+    if (l >= ls) {
+      dfl mu;
+      if (l == ls) mu = dfl{s4.x, s4.y};
+      else if (l == ls + 1) mu = dfl{s4.z, s4.w};
+      else {
+        const float2 a2 = D.A[base + (l - m)];
+        mu = df_step(dfl{a2.x, a2.y}, x, p1, p2);
+      }
+      p2 = p1;
+      p1 = mu;
+      // lambda rounded to 22 significant bits: the sum of two tf32 numbers
+      const double lam = D.g[base + (l - m)] * df_to(mu);
+      const float h = tc::to_tf32((float)lam);
+      v = h + tc::to_tf32((float)(lam - (double)h));
+    }
+    const int p = (l - m) & 1, i = (l - m) >> 1;
+    lamA[(base + (p ? n0 + i : i)) * (size_t)RPp + k] = v;
+    buf[p][i & 31] = v;
+    const int np = n_par(m, p, lmax);
+    if ((i & 31) == 31 || i == np - 1) {   // a chunk of 32 values of i is complete: write its row
+      for (int j = (i & 31) + 1; j < 32; ++j) buf[p][j] = 0.f;
+      float4 *dst = reinterpret_cast<float4 *>(lamT + ((size_t)(offTc[2 * m + p] + (i >> 5)) * RPp + k) * 32);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) dst[j] = make_float4(buf[p][4 * j], buf[p][4 * j + 1], buf[p][4 * j + 2], buf[p][4 * j + 3]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- FT -> XT
+// One CTA per (m, chunk of 32 ring pairs): the Fourier coefficients of every
+// slot, (N re, N im, S re, S im), become the analysis B operand of both
+// parities, X_0 = N + S and X_1 = N - S, with ring pairs contiguous.
+__global__ void __launch_bounds__(256) xt_kernel(const BatchArgs A, const TcArgs T) {
+  __shared__ float4 sF[32][kBatchMax + 1];
+  const int m = blockIdx.y, kc = blockIdx.x;
+  if (m > A.bstate[0]) return;
+  const int B = A.B, RP = A.RP;
+  for (int e = threadIdx.x; e < 32 * B; e += blockDim.x) {
+    const int kk = e / B, b = e % B, k = 32 * kc + kk;
+    sF[kk][b] = k < RP ? A.FT[((size_t)m * RP + k) * B + b] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int row = warp; row < 2 * T.Nc; row += blockDim.x / 32) {
+    const int p = row / T.Nc, c = row % T.Nc, b = c >> 1;
+    float v = 0.f;
+    if (b < B) {
+      const float4 f = sF[lane][b];
+      const float n = (c & 1) ? f.y : f.x, s = (c & 1) ? f.w : f.z;
+      v = p ? n - s : n + s;
+    }
+    T.XT[((((size_t)m * 2 + p) * T.nkc + kc) * T.Nc + c) * 32 + lane] = v;
+  }
+}
+
+// ---------------------------------------------------------------- analysis GEMM + Eq. 4
+// One CTA per (m, parity p, 128 values of i): t_p = Lambda X_p over every ring
+// pair, then Eq. 4 on the double-float state, the prior chi^2 / increment /
+// norm partials, and the next synthesis operand SPT.
+//
+// The leading products of every 32-wide chunk of ring pairs accumulate in one
+// of two tensor-memory blocks (ping-pong), and eight folding warps add each
+// finished chunk into a double-float accumulator: hi in tensor memory, lo in
+// the folding threads' registers, as the FP32 path folded its chunk sums. The
+// correction products accumulate over all chunks in a third block. Warps: 0
+// TMA, 1 MMA (and tensor memory), 2-5 tf32 split, 6-13 folding and the
+// epilogue (warp w: TMEM lanes 32 (w % 4) .., columns 64 ((w - 6) / 4) ..).
+// Tiles wholly above the live band limit hold zero state (band limits only
+// grow within a solve and new slots start from zero): they only report zero
+// partials.
+constexpr int kAnaThreads = 448;
+constexpr int kFoldThreads = 256;
+constexpr uint32_t kColSeg0 = 0, kColSeg1 = 128, kColCorr = 256, kColHi = 384;
+
+__global__ void __launch_bounds__(kAnaThreads, 1)
+    bana_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX,
+                   const BatchArgs A, const TcArgs T) {
+  extern __shared__ __align__(1024) uint8_t tsm_raw[];
+  uint8_t *tsm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], segf[2], segfree[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int4 tile = T.atiles[blockIdx.x];
+  const int m = tile.x, p = tile.y, i0 = tile.z, rowA = tile.w;
+  const int lmax = A.lmax, B = A.B, Nc = T.Nc;
+  const int Lact = A.bstate[0];
+  const bool live = m <= Lact && m + p + 2 * i0 <= Lact;
+  if (!live) {
+    for (int qb = threadIdx.x; qb < 3 * B; qb += blockDim.x)
+      A.m_part[((size_t)(qb % B) * A.ntiles + blockIdx.x) * 3 + qb / B] = 0.0;
+    return;
+  }
+  const int nkc = T.nkc;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&conv[s], 128);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int j = 0; j < 2; ++j) {
+      tc::mbar_init(&segf[j], 1);
+      tc::mbar_init(&segfree[j], kFoldThreads);
+    }
+    tc::fence_mbar_init();
+    abort_flag = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = tc::tf32_idesc(kTileRows, Nc);
+  const uint32_t bbytes = (uint32_t)Nc * 128;
+  int issued = 0;   // TMA stages issued by the producer (for the drain on abort)
+
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tensormap(&mapA);
+    tc::prefetch_tensormap(&mapX);
+    for (int kc = 0; kc < nkc; ++kc) {
+      const int s = kc % kStages;
+      if (kc >= kStages && !tc::mbar_wait(&empty[s], ((kc / kStages) - 1) & 1, kWaitLimit)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (*(volatile int *)&abort_flag) break;
+      tc::mbar_arrive_expect_tx(&full[s], kTileBytes + bbytes);
+      tc::tma_load_2d(Smem::tile(tsm, s, kTA), &mapA, 32 * kc, rowA + i0, &full[s]);
+      tc::tma_load_2d(Smem::tile(tsm, s, kTB), &mapX, 0, (int)((((size_t)m * 2 + p) * T.nkc + kc) * Nc), &full[s]);
+      issued = kc + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    for (int kc = 0; kc < nkc; ++kc) {
+      const int s = kc % kStages;
+      const uint32_t seg = tmem + ((kc & 1) ? kColSeg1 : kColSeg0);
+      // a chunk block is reused once the folding warps have read it
+      if (kc >= 2 &&
+          (*(volatile int *)&abort_flag || !tc::mbar_wait(&segfree[kc & 1], ((kc - 2) >> 1) & 1, kWaitLimit))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&conv[s], (kc / kStages) & 1, kWaitLimit)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      tc::tc_fence_after();
+      mma_chunk(seg, tmem + kColCorr, Smem::tile(tsm, s, 0), idesc, false, kc > 0);
+      tc::mma_commit(&empty[s]);
+      tc::mma_commit(&segf[kc & 1]);
+    }
+  } else if (warp >= 2 && warp < 6) {
+    const int t = threadIdx.x - 64;
+    for (int kc = 0; kc < nkc; ++kc) {
+      const int s = kc % kStages;
+      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&full[s], (kc / kStages) & 1, kWaitLimit)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      split_table(Smem::tile(tsm, s, kTA), Smem::tile(tsm, s, kTAlo), kTileBytes, t, 128);
+      split_data(Smem::tile(tsm, s, kTB), Smem::tile(tsm, s, kTBmid), Smem::tile(tsm, s, kTBlo), (int)bbytes, t, 128);
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&conv[s]);
+    }
+  }
+  // folding warps: chunk sums into (hi in TMEM, lo in registers)
+  const int fq = warp & 3, fh = (warp - 6) >> 2;      // lane quadrant, column half
+  const uint32_t flanes = (uint32_t)(32 * fq) << 16;
+  float lo[64];
+#pragma unroll
+  for (int e = 0; e < 64; ++e) lo[e] = 0.f;
+  if (warp >= 6) {
+    for (int kc = 0; kc < nkc; ++kc) {
+      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&segf[kc & 1], (kc >> 1) & 1, kWaitLimit)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t seg = tmem + flanes + ((kc & 1) ? kColSeg1 : kColSeg0);
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) {
+        const int cb = 4 * fh + bb;
+        if (16 * cb >= Nc) break;
+        float v[16], h[16];
+        tc::tmem_ld16(seg + 16 * cb, v);
+        if (kc == 0) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) h[e] = v[e];
+        } else {
+          tc::tmem_ld16(tmem + flanes + kColHi + 16 * cb, h);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {   // two_sum(h, v): the rounding error goes to lo
+            const float sum = h[e] + v[e];
+            const float bv = sum - h[e];
+            lo[16 * bb + e] += (h[e] - (sum - bv)) + (v[e] - bv);
+            h[e] = sum;
+          }
+        }
+        tc::tmem_st16(tmem + flanes + kColHi + 16 * cb, h);
+      }
+      tc::tmem_wait_st();
+      tc::tc_fence_before();
+      tc::mbar_arrive(&segfree[kc & 1]);
+    }
+  }
+
+  // ---- epilogue (warps 6-13)
+  __syncthreads();   // every chunk is folded, the stage buffers are free, abort_flag is final
+  tc::tc_fence_after();
+  const bool ok_acc = abort_flag == 0;   // uniform over the CTA
+  float *red = reinterpret_cast<float *>(tsm);    // [3][Bp][128] partials
+  if (warp >= 6) {
+    const int r = 32 * fq + lane;
+    const int i = i0 + r;
+    const int np = n_par(m, p, lmax);
+    const bool row_ok = i < np;
+    const int l = m + p + 2 * i;
+    const size_t idx = row_ok ? aidx(lmax, l, m) : 0;
+    const float wgt = (m == 0) ? 1.f : 2.f;
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) {
+      const int cb = 4 * fh + bb;
+      if (16 * cb >= Nc) break;
+      float th[16], tl[16];
+      if (ok_acc) {   // t = hi + (lo + corrections)
+        tc::tmem_ld16(tmem + flanes + kColHi + 16 * cb, th);
+        tc::tmem_ld16(tmem + flanes + kColCorr + 16 * cb, tl);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) tl[e] += lo[16 * bb + e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) { th[e] = 0.f; tl[e] = 0.f; }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int b = 8 * cb + jj;
+        float c2 = 0.f, inc = 0.f, nrm = 0.f;
+        if (row_ok && b < B && A.active[b] && !A.ctl[b].done) {
+          float4 *sb = A.sdf + (size_t)b * A.nalm;
+          const float4 so = sb[idx];
+          const float2 f2 = A.fdf[(size_t)b * (lmax + 1) + l];
+          const dfl f = dfl{f2.x, f2.y};
+          const dfl re = df_mul(f, df_add(dfl{so.x, so.y}, dfl{th[2 * jj], tl[2 * jj]}));
+          const dfl im = df_mul(f, df_add(dfl{so.z, so.w}, dfl{th[2 * jj + 1], tl[2 * jj + 1]}));
+          const float4 sn = make_float4(re.h, re.l, im.h, im.l);
+          c2 = wgt * (so.x * so.x + so.z * so.z) * A.icl[(size_t)b * (lmax + 1) + l];
+          const float dx = (sn.x - so.x) + (sn.y - so.y), dy = (sn.z - so.z) + (sn.w - so.w);
+          inc = wgt * (dx * dx + dy * dy);
+          nrm = wgt * (sn.x * sn.x + sn.z * sn.z);
+          sb[idx] = sn;
+          float *spt = T.SPT + (((size_t)T.offTc[2 * m + p] + (i >> 5)) * Nc + 2 * b) * 32 + (i & 31);
+          spt[0] = sn.x;
+          spt[32] = sn.z;
+        }
+        red[(0 * B + b) * 128 + r] = c2;
+        red[(1 * B + b) * 128 + r] = inc;
+        red[(2 * B + b) * 128 + r] = nrm;
+      }
+    }
+  }
+  __syncthreads();
+  // fixed-order sums over the 128 rows, one (quantity, slot) per thread
+  for (int qb = threadIdx.x; qb < 3 * B; qb += blockDim.x) {
+    const int qq = qb / B, b = qb % B;
+    double sum = 0.0;
+    for (int rr = 0; rr < 128; ++rr) sum += (double)red[qb * 128 + rr];
+    A.m_part[((size_t)b * A.ntiles + blockIdx.x) * 3 + qq] = sum;
+  }
+  // drain: every TMA this CTA issued has landed before its shared memory is released
+  if (warp == 0 && lane == 0 && *(volatile int *)&abort_flag) {
+    for (int kc = std::max(0, issued - kStages); kc < issued; ++kc)
+      tc::mbar_wait(&full[kc % kStages], (kc / kStages) & 1, kWaitLimit);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc::tmem_dealloc(tmem, 512);
+  }
+  if (threadIdx.x == 0 && abort_flag) atomicExch(T.err, 1);
+}
+
+// ---------------------------------------------------------------- synthesis GEMM
+// One CTA per (m, 128 ring pairs): E and O accumulate in two tensor-memory
+// blocks over the chunks of 32 values of i of each parity up to the live band
+// limit; the epilogue writes FS = (E + O, E - O) for every slot.
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    bsyn_tc_kernel(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapS,
+                   const BatchArgs A, const TcArgs T) {
+  extern __shared__ __align__(1024) uint8_t tsm_raw[];
+  uint8_t *tsm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], accf;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int2 tile = T.stiles[blockIdx.x];
+  const int m = tile.x, k0 = tile.y;
+  const int B = A.B, RP = A.RP, Nc = T.Nc;
+  const int Lact = A.bstate[0];
+  if (m > Lact) return;
+  const int nc0 = (n_par(m, 0, Lact) + 31) / 32, nc1 = (n_par(m, 1, Lact) + 31) / 32;
+  const int nq = nc0 + nc1;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&conv[s], 128);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&accf, 1);
+    tc::fence_mbar_init();
+    abort_flag = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = tc::tf32_idesc(kTileRows, Nc);
+  const uint32_t bbytes = (uint32_t)Nc * 128;
+  int issued = 0;
+
+  if (warp == 0 && lane == 0) {
+    if (nq > 0) {
+      tc::prefetch_tensormap(&mapT);
+      tc::prefetch_tensormap(&mapS);
+    }
+    for (int qi = 0; qi < nq; ++qi) {
+      const int s = qi % kStages;
+      if (qi >= kStages && !tc::mbar_wait(&empty[s], ((qi / kStages) - 1) & 1, kWaitLimit)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (*(volatile int *)&abort_flag) break;
+      // within a parity the chunks run from high l to low l: the large low-l
+      // terms enter the fp32 accumulator last
+      const int p = qi < nc0 ? 0 : 1, ic = p ? nc0 + nc1 - 1 - qi : nc0 - 1 - qi;
+      const long long q = (long long)T.offTc[2 * m + p] + ic;
+      tc::mbar_arrive_expect_tx(&full[s], kTileBytes + bbytes);
+      tc::tma_load_2d(Smem::tile(tsm, s, kTA), &mapT, 0, (int)(q * T.RPp + k0), &full[s]);
+      tc::tma_load_2d(Smem::tile(tsm, s, kTB), &mapS, 0, (int)(q * Nc), &full[s]);
+      issued = qi + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    for (int qi = 0; qi < nq; ++qi) {
+      const int s = qi % kStages;
+      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&conv[s], (qi / kStages) & 1, kWaitLimit)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      tc::tc_fence_after();
+      const int p = qi < nc0 ? 0 : 1, first = p ? qi == nc0 : qi == 0;
+      // leading products of parity p in columns 128 p, corrections in 256 + 128 p
+      mma_chunk<true>(tmem + (uint32_t)(128 * p), tmem + (uint32_t)(256 + 128 * p), Smem::tile(tsm, s, 0), idesc,
+                      !first, !first);
+      tc::mma_commit(&empty[s]);
+    }
+    if (nq > 0) tc::mma_commit(&accf);
+  } else if (warp >= 2) {
+    const int t = threadIdx.x - 64;
+    for (int qi = 0; qi < nq; ++qi) {
+      const int s = qi % kStages;
+      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&full[s], (qi / kStages) & 1, kWaitLimit)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      split_table(Smem::tile(tsm, s, kTA), Smem::tile(tsm, s, kTAlo), kTileBytes, t, 128);
+      split_data(Smem::tile(tsm, s, kTB), Smem::tile(tsm, s, kTBmid), Smem::tile(tsm, s, kTBlo), (int)bbytes, t, 128);
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&conv[s]);
+    }
+  }
+  // ---- epilogue (warps 2-5): row k0 + r of E (columns 0 .. Nc) and O (Nc .. 2 Nc)
+  if (warp >= 2 && nq > 0 && !*(volatile int *)&abort_flag && !tc::mbar_wait(&accf, 0, kWaitLimit))
+    atomicExch(&abort_flag, 1);
+  __syncthreads();   // abort_flag is final from here on
+  tc::tc_fence_after();
+  const bool have = nq > 0 && abort_flag == 0;   // uniform over the CTA
+  if (warp >= 2) {
+    const int qd = warp & 3;
+    const int k = k0 + 32 * qd + lane;
+    const uint32_t lanes = (uint32_t)(32 * qd) << 16;
+    for (int cb = 0; cb < Nc / 16; ++cb) {
+      float e[16], o[16], ce[16], co[16];
+      if (have && nc0 > 0) {
+        tc::tmem_ld16(tmem + lanes + 16 * cb, e);
+        tc::tmem_ld16(tmem + lanes + 256 + 16 * cb, ce);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) e[j] += ce[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) e[j] = 0.f;
+      }
+      if (have && nc1 > 0) {
+        tc::tmem_ld16(tmem + lanes + 128 + 16 * cb, o);
+        tc::tmem_ld16(tmem + lanes + 384 + 16 * cb, co);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[j] += co[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[j] = 0.f;
+      }
+      if (k < RP) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int b = 8 * cb + jj;
+          if (b < B)
+            A.FS[((size_t)m * RP + k) * B + b] = make_float4(e[2 * jj] + o[2 * jj], e[2 * jj + 1] + o[2 * jj + 1],
+                                                             e[2 * jj] - o[2 * jj], e[2 * jj + 1] - o[2 * jj + 1]);
+        }
+      }
+    }
+  }
+  if (warp == 0 && lane == 0 && *(volatile int *)&abort_flag) {
+    for (int qi = std::max(0, issued - kStages); qi < issued; ++qi)
+      tc::mbar_wait(&full[qi % kStages], (qi / kStages) & 1, kWaitLimit);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc::tmem_dealloc(tmem, 512);
+  }
+  if (threadIdx.x == 0 && abort_flag) atomicExch(T.err, 1);
+}
+
+// ---------------------------------------------------------------- host side
+static size_t gemm_smem() { return (size_t)kStages * kTiles * kTileBytes + 1024; }
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D fp32 tensor of `rows` rows of `inner` values (inner * 4 bytes apart),
+// boxes of box_rows x 32 values, 128-byte swizzle
+bool make_tc_map(CUtensorMap *map, const float *base, unsigned long long inner, unsigned long long rows,
+                 unsigned box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * sizeof(float)};
+  cuuint32_t box[2] = {32, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void launch_lam_tc_tables(const double *x, const LegDfArgs &D, int lmax, int RP, int RPp, const int *offTc,
+                          float *lamA, float *lamT, cudaStream_t s) {
+  const long long n = (long long)(lmax + 1) * RPp;
+  lam_tc_tables_kernel<<<(int)((n + 127) / 128), 128, 0, s>>>(x, D, lmax, RP, RPp, offTc, lamA, lamT);
+}
+
+void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which) {
+  raise_smem_cap(reinterpret_cast<const void *>(bana_tc_kernel));
+  raise_smem_cap(reinterpret_cast<const void *>(bsyn_tc_kernel));
+  if (which == 0) {
+    xt_kernel<<<dim3(t.nkc, a.lmax + 1), 256, 0, s>>>(a, t);
+    bana_tc_kernel<<<t.natiles, kAnaThreads, gemm_smem(), s>>>(maps.A, maps.X, a, t);
+  } else {
+    bsyn_tc_kernel<<<t.nstiles, kGemmThreads, gemm_smem(), s>>>(maps.T, maps.S, a, t);
+  }
+}
+
+}  // namespace wfk

@@ -496,9 +496,8 @@ wf_status wf_plan_info(wf_plan_t plan, int64_t *npix, int64_t *nalm, double *tau
 
 wf_status wf_plan_kernels_per_iteration(wf_plan_t plan, int *n) {
   if (!plan || !n) { set_error("wf_plan_kernels_per_iteration: NULL argument"); return WF_EINVAL; }
-  const Plan *P = static_cast<const Plan *>(plan);
-  (void)P;
-  *n = 3;
+  // the ring stage (one launch per single-solve ring class), Legendre stage, controller
+  *n = (int)static_cast<const Plan *>(plan)->rsingle.size() + 2;
   return WF_OK;
 }
 

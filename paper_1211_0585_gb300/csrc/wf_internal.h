@@ -148,7 +148,6 @@ struct BatchArgs {
   const float4 *twf, *hsf, *chf, *Bf;
   const float2 *tw2, *Bf2;   // FP32 twiddle and Bluestein filter tables (hi parts of twf, Bf)
   int logMmax;
-  const float *lam;          // [nalm][RP] lambda_lm(x_k), FP32
   int lmax, RP, R, B;
   long long npix, nalm;
   double omega;
@@ -159,23 +158,36 @@ struct BatchArgs {
   float2 *fdf;               // [B][lmax+1] Eq. 4 filter f_l(lambda_b) of this iteration, double-float
   float *icl;                // [B][lmax+1] 1 / C_l (0 where C_l = 0)
   float4 *FS, *FT;           // [(m RP + k) B + b] (north re, north im, south re, south im)
-  float2 *SP;                // [nalm][B] synthesis coefficients
   Ctl *ctl;                  // [B]
   const int *active;         // [B]
   double *ring_part;         // [B][R][2]
   double *m_part;            // [B][ntiles][3]
-  int ntiles;
-  const int2 *tiles;         // analysis tiles (m, l0), 64 l each
-  const int2 *stiles;        // synthesis tiles (m, k0), 32 ring pairs each
+  int ntiles;                // analysis tiles (partials per slot)
   const int *bstate;         // [0] largest live band limit, [1] live slots
   wf_iter_record *last;      // [B]
 };
 
-void launch_lam_table(const double *x, const LegDfArgs &D, int lmax, int RP, float *lam, cudaStream_t s);
-void launch_batch_iteration(const BatchArgs &a, const RingClass *cls, int ncls, int n_stiles, int *bstate,
-                            cudaStream_t s);
+// Tensor-core Legendre stage of the batched engine (batch_tc.cu): work lists,
+// per-iteration operands and the error flag of the bounded pipeline waits.
+struct TcArgs {
+  int Nc;                    // GEMM columns: 2 B (re, im of every slot), a multiple of 16
+  int RPp, nkc;              // ring pairs padded to a multiple of 32, and RPp / 32
+  const int4 *atiles;        // analysis tiles (m, parity, first i, first lamA row of (m, parity))
+  int natiles;
+  const int2 *stiles;        // synthesis tiles (m, first ring pair)
+  int nstiles;
+  const int *offTc;          // [2 (lmax+1)] first 32-wide i chunk of (m, parity)
+  float *XT, *SPT;           // analysis / synthesis B operands
+  int *err;                  // set when a pipeline wait gave up
+};
+
+void launch_lam_tc_tables(const double *x, const LegDfArgs &D, int lmax, int RP, int RPp, const int *offTc,
+                          float *lamA, float *lamT, cudaStream_t s);
+struct TcMaps;
+void launch_batch_iteration(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, const RingClass *cls, int ncls,
+                            int *bstate, cudaStream_t s);
 void launch_batch_state(const BatchArgs &a, int *bstate, cudaStream_t s);
-void launch_batch_zero_slot(const BatchArgs &a, int b, cudaStream_t s);
+void launch_batch_zero_slot(const BatchArgs &a, const TcArgs &t, long long nchunks, int b, cudaStream_t s);
 void launch_batch_convert_slot(const BatchArgs &a, int b, cudaStream_t s);
 void launch_batch_export_slot(const BatchArgs &a, int b, cudaStream_t s);
 void launch_hi_table(const float4 *src, float2 *dst, long long n, cudaStream_t s);
