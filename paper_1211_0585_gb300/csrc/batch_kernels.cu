@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs
   const int n = rg.n, M = 1 << rg.logM;
   float2 *buf = bsm;                                          // [P][M] (swizzled, px)
   __shared__ double red[kBringThreads / 32][2 * G];
+  __shared__ float2 fpart[kBringThreads][G];   // alias partial sums of short rings
   const float4 *hs = A.hsf + rg.hs_off;
   const float4 *ch = A.chf + rg.ch_off;
   const float2 *Bf = A.Bf2 + rg.B_off;
@@ -87,13 +88,13 @@ __global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs
 #pragma unroll
   for (int g = 0; g < G; ++g) Lmax = max(Lmax, Lg[g]);
 
-  // fold F_m onto residues q for the G slots, packed in pairs
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    float2 acc[G];
+  // fold F_m onto residues q for the G slots (m-aliasing), packed in pairs;
+  // on rings shorter than the block each residue's alias series is split over
+  // several threads (partial sums added in a fixed order)
+  auto alias_sum = [&](int q, int j0, int dj, float2 (&acc)[G]) {
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float2(0.f, 0.f);
-    int j = 0;
-    for (int m = q; m <= Lmax; m += n, ++j) {
+    for (int j = j0, m = q + n * j0; m <= Lmax; j += dj, m += n * dj) {
       const float4 *src = A.FS + ((size_t)m * A.RP + k) * B + b0;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
@@ -104,8 +105,7 @@ __global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs
         acc[g] = f2add(acc[g], f);
       }
     }
-    j = 1;
-    for (int m = (q == 0 ? n : n - q); m <= Lmax; m += n, ++j) {
+    for (int j = 1 + j0, m = n * (1 + j0) - q; m <= Lmax; j += dj, m += n * dj) {
       const float4 *src = A.FS + ((size_t)m * A.RP + k) * B + b0;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs
         acc[g] = f2add(acc[g], f);
       }
     }
+  };
+  auto store_residue = [&](int q, const float2 (&acc)[G]) {
     const float2 h = hi2(hs[q]), cq = rg.blue ? hi2(ch[q]) : make_float2(0.f, 0.f);
 #pragma unroll
     for (int pp = 0; pp < P; ++pp) {
@@ -123,6 +125,31 @@ __global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs
       if (rg.shifted) { va = f2mul(va, h); vb = f2mul(vb, h); }
       const float2 z = make_float2(va.x - vb.y, va.y + vb.x);    // G_a + i G_b
       buf[pp * M + px<OpsF32>(q)] = rg.blue ? f2mul(f2conj(z), cq) : z;
+    }
+  };
+  if (n >= kBringThreads) {
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      float2 acc[G];
+      alias_sum(q, 0, 1, acc);
+      store_residue(q, acc);
+    }
+  } else {
+    const int nj = kBringThreads / n, t = threadIdx.x;
+    if (t < n * nj) {
+      float2 acc[G];
+      alias_sum(t % n, t / n, nj, acc);
+#pragma unroll
+      for (int g = 0; g < G; ++g) fpart[t][g] = acc[g];
+    }
+    __syncthreads();
+    if (t < n) {
+      float2 acc[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) acc[g] = make_float2(0.f, 0.f);
+      for (int jg = 0; jg < nj; ++jg)
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = f2add(acc[g], fpart[jg * n + t][g]);
+      store_residue(t, acc);
     }
   }
   if (rg.blue)

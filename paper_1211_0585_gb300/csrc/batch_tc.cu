@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
   __syncthreads();   // every chunk is folded, the stage buffers are free, abort_flag is final
   tc::tc_fence_after();
   const bool ok_acc = abort_flag == 0;   // uniform over the CTA
-  float *red = reinterpret_cast<float *>(tsm);    // [3][Bp][128] partials
+  float *red = reinterpret_cast<float *>(tsm);    // [3][Bp][129] partials (row stride 129: no bank conflicts)
   if (warp >= 6) {
     const int r = 32 * fq + lane;
     const int i = i0 + r;
@@ -415,9 +415,9 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
           spt[0] = sn.x;
           spt[32] = sn.z;
         }
-        red[(0 * B + b) * 128 + r] = c2;
-        red[(1 * B + b) * 128 + r] = inc;
-        red[(2 * B + b) * 128 + r] = nrm;
+        red[(0 * B + b) * 129 + r] = c2;
+        red[(1 * B + b) * 129 + r] = inc;
+        red[(2 * B + b) * 129 + r] = nrm;
       }
     }
   }
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
   for (int qb = threadIdx.x; qb < 3 * B; qb += blockDim.x) {
     const int qq = qb / B, b = qb % B;
     double sum = 0.0;
-    for (int rr = 0; rr < 128; ++rr) sum += (double)red[qb * 128 + rr];
+    for (int rr = 0; rr < 128; ++rr) sum += (double)red[qb * 129 + rr];
     A.m_part[((size_t)b * A.ntiles + blockIdx.x) * 3 + qq] = sum;
   }
   // drain: every TMA this CTA issued has landed before its shared memory is released

@@ -1,0 +1,60 @@
+// Folding of a ring's azimuthal Fourier coefficients onto the residues of its
+// DFT (m-aliasing): for a ring of n pixels,
+//   G_q = sum_{j >= 0} s^j F_{q + n j} + sum_{j >= 1} s^j conj(F_{n j - q}),
+// m <= L, with s = -1 on rings whose first pixel sits half a pixel off
+// (the phase e^{i m phi0} changes sign with each alias) and s = 1 otherwise.
+// On rings shorter than the thread block, each residue's alias series is split
+// over several threads and their partial sums are added in a fixed order.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wf_internal.h"
+
+namespace wfk {
+
+// The share j = j0, j0 + dj, ... of residue q's series, from F stored as
+// double4 (north re, north im, south re, south im) at [m RP + k].
+__device__ __forceinline__ double2 fold_alias_sum(const double4_32a *FS, int RP, int k, int slot, int shifted,
+                                                  int n, int q, int L, int j0, int dj) {
+  double ar = 0.0, ai = 0.0;
+  for (int j = j0, m = q + n * j0; m <= L; j += dj, m += n * dj) {
+    const double4_32a f4 = FS[(size_t)m * RP + k];
+    double fr = slot ? f4.z : f4.x, fi = slot ? f4.w : f4.y;
+    if (shifted && (j & 1)) { fr = -fr; fi = -fi; }
+    ar += fr; ai += fi;
+  }
+  for (int j = 1 + j0, m = n * (1 + j0) - q; m <= L; j += dj, m += n * dj) {
+    const double4_32a f4 = FS[(size_t)m * RP + k];
+    double fr = slot ? f4.z : f4.x, fi = slot ? -f4.w : -f4.y;
+    if (shifted && (j & 1)) { fr = -fr; fi = -fi; }
+    ar += fr; ai += fi;
+  }
+  return make_double2(ar, ai);
+}
+
+// G_q for every residue, passed to store(q, G_q) by one thread each.
+// part: shared scratch of blockDim.x double2. Contains a __syncthreads when
+// the ring is shorter than the block (uniform over the CTA).
+template <class Store>
+__device__ __forceinline__ void fold_ring(const double4_32a *FS, int RP, int k, int slot, int shifted, int n, int L,
+                                          double2 *part, Store store) {
+  const int nt = blockDim.x;
+  if (n >= nt) {
+    for (int q = threadIdx.x; q < n; q += nt) store(q, fold_alias_sum(FS, RP, k, slot, shifted, n, q, L, 0, 1));
+    return;
+  }
+  const int nj = nt / n, t = threadIdx.x;
+  if (t < n * nj) part[t] = fold_alias_sum(FS, RP, k, slot, shifted, n, t % n, L, t / n, nj);
+  __syncthreads();
+  if (t < n) {
+    double2 g = make_double2(0.0, 0.0);
+    for (int jg = 0; jg < nj; ++jg) {
+      g.x += part[jg * n + t].x;
+      g.y += part[jg * n + t].y;
+    }
+    store(t, g);
+  }
+}
+
+}  // namespace wfk

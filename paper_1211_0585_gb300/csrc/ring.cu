@@ -21,12 +21,11 @@
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
+#include "fold.cuh"
 #include "wf_internal.h"
 
 namespace wfk {
 
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
@@ -60,6 +59,7 @@ __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
   double2 *buf = A.scratch ? reinterpret_cast<double2 *>(A.scratch) + (size_t)blockIdx.x * M : smem;
   double *ureal = reinterpret_cast<double *>(A.scratch ? smem : smem + Mp);  // [n]
   __shared__ double red[64];
+  __shared__ double2 fold_part[kRingThreads];
 
   int L = A.lsht;
   double lam = 1.0;
@@ -76,29 +76,11 @@ __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
 
   if (MODE == RING_SYNTH || MODE == RING_ITER) {
     // ---- fold F_m onto residues q (m-aliasing) with the half-pixel shift
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-      double2 acc = make_double2(0.0, 0.0);
-      int j = 0;
-      for (int m = q; m <= L; m += n, ++j) {
-        const double4_32a f4 = A.FS[(size_t)m * A.RP + k];
-        double2 f = slot ? make_double2(f4.z, f4.w) : make_double2(f4.x, f4.y);
-        if (rg.shifted && (j & 1)) { f.x = -f.x; f.y = -f.y; }
-        acc = cadd(acc, f);
-      }
-      j = 1;
-      for (int m = (q == 0 ? n : n - q); m <= L; m += n, ++j) {
-        const double4_32a f4 = A.FS[(size_t)m * A.RP + k];
-        double2 f = slot ? make_double2(f4.z, -f4.w) : make_double2(f4.x, -f4.y);
-        if (rg.shifted && (j & 1)) { f.x = -f.x; f.y = -f.y; }
-        acc = cadd(acc, f);
-      }
+    fold_ring(A.FS, A.RP, k, slot, rg.shifted, n, L, fold_part, [&](int q, double2 acc) {
       if (rg.shifted) acc = cmul(acc, hs[q]);
-      if (rg.blue) {
-        buf[px<OpsF64>(q)] = cmul(conjd(acc), ch[q]);   // inverse DFT via conj(DFT(conj(G)))
-      } else {
-        buf[px<OpsF64>(q)] = acc;
-      }
-    }
+      // Bluestein: the inverse DFT via conj(DFT(conj(G)))
+      buf[px<OpsF64>(q)] = rg.blue ? cmul(conjd(acc), ch[q]) : acc;
+    });
     if (rg.blue) {
       for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[px<OpsF64>(q)] = make_double2(0.0, 0.0);
     }

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
+#include "fold.cuh"
 #include "wf_internal.h"
 
 namespace wfk {
@@ -47,10 +48,6 @@ __device__ __forceinline__ dd dmul(dd a, dd b) {
 __device__ __forceinline__ float4 pack(dd re, dd im) { return make_float4(re.h, re.l, im.h, im.l); }
 __device__ __forceinline__ dd RE(float4 v) { return {v.x, v.y}; }
 __device__ __forceinline__ dd IM(float4 v) { return {v.z, v.w}; }
-__device__ __forceinline__ float4 cadd(float4 a, float4 b) { return pack(dadd(RE(a), RE(b)), dadd(IM(a), IM(b))); }
-__device__ __forceinline__ float4 csub(float4 a, float4 b) {
-  return pack(dadd(RE(a), dneg(RE(b))), dadd(IM(a), dneg(IM(b))));
-}
 __device__ __forceinline__ float4 cmul(float4 a, float4 b) {
   const dd re = dadd(dmul(RE(a), RE(b)), dneg(dmul(IM(a), IM(b))));
   const dd im = dadd(dmul(RE(a), IM(b)), dmul(IM(a), RE(b)));
@@ -88,6 +85,7 @@ __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A,
   float4 *buf = A.scratch ? reinterpret_cast<float4 *>(A.scratch) + (size_t)blockIdx.x * M : rsm;
   double *ureal = reinterpret_cast<double *>(A.scratch ? rsm : rsm + Mp);   // [n]
   __shared__ double red[64];
+  __shared__ double2 fold_part[kRingThreads];
 
   int L = A.lsht;
   double lam = 1.0;
@@ -103,26 +101,12 @@ __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A,
   const int slot = rg.side;
 
   if (MODE == RING_SYNTH || MODE == RING_ITER) {
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-      double ar = 0.0, ai = 0.0;  // folding is a handful of additions: done in double
-      int j = 0;
-      for (int m = q; m <= L; m += n, ++j) {
-        const double4_32a f4 = A.FS[(size_t)m * A.RP + k];
-        double fr = slot ? f4.z : f4.x, fi = slot ? f4.w : f4.y;
-        if (rg.shifted && (j & 1)) { fr = -fr; fi = -fi; }
-        ar += fr; ai += fi;
-      }
-      j = 1;
-      for (int m = (q == 0 ? n : n - q); m <= L; m += n, ++j) {
-        const double4_32a f4 = A.FS[(size_t)m * A.RP + k];
-        double fr = slot ? f4.z : f4.x, fi = slot ? -f4.w : -f4.y;
-        if (rg.shifted && (j & 1)) { fr = -fr; fi = -fi; }
-        ar += fr; ai += fi;
-      }
-      float4 acc = pack(mk(ar), mk(ai));
+    // folding is a handful of additions: done in double
+    fold_ring(A.FS, A.RP, k, slot, rg.shifted, n, L, fold_part, [&](int q, double2 g) {
+      float4 acc = pack(mk(g.x), mk(g.y));
       if (rg.shifted) acc = cmul(acc, hs[q]);
       buf[px<OpsDF>(q)] = rg.blue ? cmul(cconj(acc), ch[q]) : acc;
-    }
+    });
     if (rg.blue) {
       for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[px<OpsDF>(q)] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
