@@ -290,9 +290,10 @@ def mixed_batched(prob, dmap, P64, out64, flush, nrhs=64):
     Pm.close()
     return {"solves_per_s": round(nrhs / dt, 4), "nrhs": nrhs, "seconds": round(dt, 3), "status": status,
             "iterations_mean": round(float(np.mean(iters)), 1), "rel_l2_vs_fp64_rhs0": err,
-            "precision": "FP32 ring FFTs (two slots per complex FFT) and Legendre GEMMs over an FP32 Lambda "
-                         "table with double-float chunk sums; double-float state and Eq. 4; FP32 Eq. 3; "
-                         "double reductions and controller",
+            "precision": "FP32 ring FFTs (two slots per complex FFT); Legendre GEMMs on tcgen05 tensor cores "
+                         "(kind::tf32, 22-bit tables, exact 3-way split of the FP32 data, five products, "
+                         "double-float chunk sums); double-float state and Eq. 4; FP32 Eq. 3; double "
+                         "reductions and controller",
             "timing": "host wall clock around wf_solve_batch with device-resident inputs"}
 
 

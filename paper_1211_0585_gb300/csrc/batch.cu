@@ -98,7 +98,7 @@ BatchArgs Engine::args() const {
   a.lmax = geo->lmax; a.RP = geo->RP; a.R = geo->R; a.B = B;
   a.npix = geo->npix; a.nalm = geo->nalm; a.omega = geo->omega;
   a.d = d; a.w = w; a.cl = cl; a.dw32 = dw32;
-  a.s = s; a.sdf = sdf; a.fdf = fdf; a.icl = icl; a.FS = FS; a.FT = FT;
+  a.s = s; a.sdf = sdf; a.alm_of_row = alm_of_row; a.fdf = fdf; a.icl = icl; a.FS = FS; a.FT = FT;
   a.ctl = ctl; a.active = active; a.ring_part = ring_part; a.m_part = m_part;
   a.ntiles = natiles; a.bstate = bstate; a.last = last;
   return a;
@@ -144,6 +144,7 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
       (st = dalloc((void **)&atiles, sizeof(int4) * ana.size())) ||
       (st = dalloc((void **)&tstiles, sizeof(int2) * syn.size())) ||
       (st = dalloc((void **)&offTc, sizeof(int) * off.size())) || (st = dalloc((void **)&err, sizeof(int))) ||
+      (st = dalloc((void **)&alm_of_row, sizeof(int) * nalm)) ||
       (st = dalloc((void **)&tw2, sizeof(float2) * std::max<long long>(geo->n_tw, 1))) ||
       (st = dalloc((void **)&Bf2, sizeof(float2) * std::max<long long>(geo->n_B, 1))) ||
       (st = dalloc((void **)&FS, sizeof(float4) * nF * B)) || (st = dalloc((void **)&FT, sizeof(float4) * nF * B)) ||
@@ -173,9 +174,20 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ENG_CUDA(cudaMemcpyAsync(atiles, ana.data(), sizeof(int4) * ana.size(), cudaMemcpyHostToDevice, stream));
   ENG_CUDA(cudaMemcpyAsync(tstiles, syn.data(), sizeof(int2) * syn.size(), cudaMemcpyHostToDevice, stream));
   ENG_CUDA(cudaMemcpyAsync(offTc, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, stream));
+  {
+    // state rows in the analysis table's order: (m, parity of l - m, (l - m) / 2)
+    std::vector<int> a_of_r(nalm);
+    size_t r = 0;
+    for (int m = 0; m <= lmax; ++m)
+      for (int p = 0; p < 2; ++p)
+        for (int l = m + p; l <= lmax; l += 2) a_of_r[r++] = (int)((size_t)m * (2 * lmax + 1 - m) / 2 + l);
+    ENG_CUDA(cudaMemcpyAsync(alm_of_row, a_of_r.data(), sizeof(int) * nalm, cudaMemcpyHostToDevice, stream));
+    ENG_CUDA(cudaStreamSynchronize(stream));   // a_of_r is released at the end of this block
+  }
   launch_hi_table(geo->d_twf, tw2, geo->n_tw, stream);
   launch_hi_table(geo->d_Bf, Bf2, geo->n_B, stream);
   ENG_CUDA(cudaMemsetAsync(SPT, 0, sizeof(float) * nSPT, stream));
+  ENG_CUDA(cudaMemsetAsync(dw32, 0, sizeof(float2) * npix * B, stream));
   ENG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), stream));
   ENG_CUDA(cudaMemsetAsync(FS, 0, sizeof(float4) * nF * B, stream));
   ENG_CUDA(cudaMemsetAsync(FT, 0, sizeof(float4) * nF * B, stream));
@@ -187,6 +199,47 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ENG_CUDA(cudaMemsetAsync(active, 0, sizeof(int) * B, stream));
   ENG_CUDA(cudaMemsetAsync(last, 0, sizeof(wf_iter_record) * B, stream));
   launch_lam_tc_tables(geo->d_x, geo->legdf_args(), lmax, RP, RPp, offTc, lamA, lamT, stream);
+  launch_batch_state(args(), bstate, stream);
+  ENG_CUDA(cudaGetLastError());
+  ENG_CUDA(cudaStreamSynchronize(stream));
+  return autotune();
+}
+
+wf_status Engine::autotune() {
+  const int ncls = (int)geo->rclass.size();
+  ring_groups.assign(ncls, 0);
+  // every slot active on a full-band step (the data are zero)
+  const Ctl c = geo->make_ctl(1, 1.0, geo->lmax, 0);
+  for (int b = 0; b < B; ++b) { h_ctl[b] = c; h_active[b] = 1; }
+  ENG_CUDA(cudaMemcpyAsync(ctl, h_ctl, sizeof(Ctl) * B, cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(active, h_active, sizeof(int) * B, cudaMemcpyHostToDevice, stream));
+  launch_batch_state(args(), bstate, stream);
+  cudaEvent_t e0, e1;
+  ENG_CUDA(cudaEventCreate(&e0));
+  ENG_CUDA(cudaEventCreate(&e1));
+  const BatchArgs a = args();
+  for (int k = 0; k < ncls; ++k) {
+    const RingClass &rc = geo->rclass[k];
+    float best = 0.f;
+    for (int G = 2; G <= 8; G *= 2) {
+      if (!batch_ring_group_ok(rc.logM, G)) continue;
+      launch_batch_ring_class(a, rc, G, stream);   // warm-up
+      cudaEventRecord(e0, stream);
+      for (int r = 0; r < 3; ++r) launch_batch_ring_class(a, rc, G, stream);
+      cudaEventRecord(e1, stream);
+      ENG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ring_groups[k] == 0 || ms < best) { best = ms; ring_groups[k] = G; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // back to empty slots
+  for (int b = 0; b < B; ++b) h_active[b] = 0;
+  ENG_CUDA(cudaMemcpyAsync(active, h_active, sizeof(int) * B, cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) * B, stream));
+  ENG_CUDA(cudaMemsetAsync(FT, 0, sizeof(float4) * (size_t)(geo->lmax + 1) * geo->RP * B, stream));
   launch_batch_state(args(), bstate, stream);
   ENG_CUDA(cudaGetLastError());
   ENG_CUDA(cudaStreamSynchronize(stream));
@@ -251,7 +304,8 @@ wf_status Engine::step() {
     cudaGraph_t g;
     ENG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < graph_iters; ++i)
-      launch_batch_iteration(args(), tc_args(), maps, geo->rclass.data(), (int)geo->rclass.size(), bstate, stream);
+      launch_batch_iteration(args(), tc_args(), maps, geo->rclass.data(), (int)geo->rclass.size(),
+                             ring_groups.empty() ? nullptr : ring_groups.data(), bstate, stream);
     ENG_CUDA(cudaStreamEndCapture(stream, &g));
     cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
     cudaGraphDestroy(g);

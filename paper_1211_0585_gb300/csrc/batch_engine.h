@@ -39,9 +39,11 @@ struct Engine {
   int4 *atiles = nullptr;
   int2 *tstiles = nullptr;
   int *offTc = nullptr;
+  int *alm_of_row = nullptr;
   int *err = nullptr, *h_err = nullptr;
   int natiles = 0, ntstiles = 0, nchunks = 0, RPp = 0;
   TcMaps maps{};
+  std::vector<int> ring_groups;   // slots per ring-stage CTA of each ring class (autotuned)
   float4 *FS = nullptr, *FT = nullptr;
   double *d = nullptr, *w = nullptr, *cl = nullptr;
   float2 *dw32 = nullptr;   // [B][npix] (d, w) in FP32 for the ring stage
@@ -73,6 +75,9 @@ struct Engine {
   // As load_slot, with the inverse noise given on the host (serving).
   wf_status load_slot_host(int b, const double *d_host, const double *w_host, const double *cl_host, const Ctl &c);
   wf_status refresh_state();           // recompute the live band limit after slots changed
+  // Time every admissible slot group of each ring class on a full-band step of
+  // all slots (zero data) and keep the fastest; the slots are reset after.
+  wf_status autotune();
   wf_status step();                    // one graph launch (graph_iters iterations), then mirror ctl to host
   wf_status sync_host();               // wait for the last step's mirrors
   wf_status release_slot(int b);

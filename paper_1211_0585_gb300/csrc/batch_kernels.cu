@@ -46,7 +46,7 @@ __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.x, v.z); 
 // the FFT passes of one CTA overlap the global loads and stores of another.
 constexpr int kBringThreads = 128;
 template <int G>
-__global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kBringThreads, 6) bring_kernel(const BatchArgs A) {
   static_assert(G % 2 == 0, "slots are packed in pairs");
   constexpr int P = G / 2;
   extern __shared__ float2 bsm[];
@@ -320,7 +320,7 @@ __global__ void bzero_slot_kernel(const BatchArgs A, const TcArgs T, long long n
 __global__ void bexport_slot_kernel(const BatchArgs A, int b) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nalm; i += (long long)gridDim.x * blockDim.x) {
     const float4 v = A.sdf[(size_t)b * A.nalm + i];
-    A.s[(size_t)b * A.nalm + i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    A.s[(size_t)b * A.nalm + A.alm_of_row[i]] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
   }
 }
 
@@ -336,8 +336,8 @@ __global__ void bfilter_kernel(const BatchArgs A) {
     const double cl = clb[l];
     const double f = (cl > 0.0 && l <= c.lsht) ? cl / (cl + lto) : 0.0;
     const dfl fd = df_from(f);
-    A.fdf[(size_t)b * (A.lmax + 1) + l] = make_float2(fd.h, fd.l);
-    A.icl[(size_t)b * (A.lmax + 1) + l] = cl > 0.0 ? (float)(1.0 / cl) : 0.f;
+    A.fdf[(size_t)l * A.B + b] = make_float2(fd.h, fd.l);
+    A.icl[(size_t)l * A.B + b] = cl > 0.0 ? (float)(1.0 / cl) : 0.f;
   }
 }
 
@@ -387,18 +387,26 @@ static void launch_bring(const BatchArgs &a, const RingClass &c, cudaStream_t s)
   bring_kernel<G><<<dim3(c.count, (a.B + G - 1) / G), kBringThreads, sm, s>>>(ac);
 }
 
-void launch_batch_iteration(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, const RingClass *cls, int ncls,
-                            int *bstate, cudaStream_t s) {
+// slots per CTA that a ring class may use: even, at most 8, the packed FFT
+// buffers within the shared memory of one CTA
+bool batch_ring_group_ok(int logM, int G) {
+  return (G == 2 || G == 4 || G == 8) && (size_t)(G / 2) * bring_smem_per_pair(logM) <= 200 * 1024;
+}
+
+void launch_batch_ring_class(const BatchArgs &a, const RingClass &c, int G, cudaStream_t s) {
   raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<2>));
   raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<4>));
   raise_smem_cap(reinterpret_cast<const void *>(bring_kernel<8>));
-  for (int c = 0; c < ncls; ++c) {
-    if (cls[c].count <= 0) continue;
-    const int G = batch_ring_group(cls[c].logM, a.B);
-    if (G == 8) launch_bring<8>(a, cls[c], s);
-    else if (G == 4) launch_bring<4>(a, cls[c], s);
-    else launch_bring<2>(a, cls[c], s);
-  }
+  if (c.count <= 0) return;
+  if (G <= 0 || !batch_ring_group_ok(c.logM, G)) G = batch_ring_group(c.logM, a.B);
+  if (G == 8) launch_bring<8>(a, c, s);
+  else if (G == 4) launch_bring<4>(a, c, s);
+  else launch_bring<2>(a, c, s);
+}
+
+void launch_batch_iteration(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, const RingClass *cls, int ncls,
+                            const int *groups, int *bstate, cudaStream_t s) {
+  for (int c = 0; c < ncls; ++c) launch_batch_ring_class(a, cls[c], groups ? groups[c] : 0, s);
   bfilter_kernel<<<a.B, 256, 0, s>>>(a);
   launch_batch_gemms_tc(a, t, maps, s, 0);   // FT -> XT, analysis GEMM, Eq. 4
   launch_batch_gemms_tc(a, t, maps, s, 1);   // synthesis GEMM

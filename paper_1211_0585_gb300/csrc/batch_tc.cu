@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
     const int t = threadIdx.x - 64;
     for (int kc = 0; kc < nkc; ++kc) {
       const int s = kc % kStages;
-      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&full[s], (kc / kStages) & 1, kWaitLimit)) {
+      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&full[s], (kc / kStages) & 1, kWaitLimit)) {
         atomicExch(&abort_flag, 1);
         break;
       }
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
   for (int e = 0; e < 64; ++e) lo[e] = 0.f;
   if (warp >= 6) {
     for (int kc = 0; kc < nkc; ++kc) {
-      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&segf[kc & 1], (kc >> 1) & 1, kWaitLimit)) {
+      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&segf[kc & 1], (kc >> 1) & 1, kWaitLimit)) {
         atomicExch(&abort_flag, 1);
         break;
       }
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
     const int np = n_par(m, p, lmax);
     const bool row_ok = i < np;
     const int l = m + p + 2 * i;
-    const size_t idx = row_ok ? aidx(lmax, l, m) : 0;
+    const size_t idx = (size_t)rowA + (row_ok ? i : 0);   // state row (the analysis table's row order)
     const float wgt = (m == 0) ? 1.f : 2.f;
 #pragma unroll
     for (int bb = 0; bb < 4; ++bb) {
@@ -401,12 +401,12 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
         if (row_ok && b < B && A.active[b] && !A.ctl[b].done) {
           float4 *sb = A.sdf + (size_t)b * A.nalm;
           const float4 so = sb[idx];
-          const float2 f2 = A.fdf[(size_t)b * (lmax + 1) + l];
+          const float2 f2 = A.fdf[(size_t)l * B + b];
           const dfl f = dfl{f2.x, f2.y};
           const dfl re = df_mul(f, df_add(dfl{so.x, so.y}, dfl{th[2 * jj], tl[2 * jj]}));
           const dfl im = df_mul(f, df_add(dfl{so.z, so.w}, dfl{th[2 * jj + 1], tl[2 * jj + 1]}));
           const float4 sn = make_float4(re.h, re.l, im.h, im.l);
-          c2 = wgt * (so.x * so.x + so.z * so.z) * A.icl[(size_t)b * (lmax + 1) + l];
+          c2 = wgt * (so.x * so.x + so.z * so.z) * A.icl[(size_t)l * B + b];
           const float dx = (sn.x - so.x) + (sn.y - so.y), dy = (sn.z - so.z) + (sn.w - so.w);
           inc = wgt * (dx * dx + dy * dy);
           nrm = wgt * (sn.x * sn.x + sn.z * sn.z);
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int t = threadIdx.x - 64;
     for (int qi = 0; qi < nq; ++qi) {
       const int s = qi % kStages;
-      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&full[s], (qi / kStages) & 1, kWaitLimit)) {
+      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&full[s], (qi / kStages) & 1, kWaitLimit)) {
         atomicExch(&abort_flag, 1);
         break;
       }
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
   }
   // ---- epilogue (warps 2-5): row k0 + r of E (columns 0 .. Nc) and O (Nc .. 2 Nc)
-  if (warp >= 2 && nq > 0 && !*(volatile int *)&abort_flag && !tc::mbar_wait(&accf, 0, kWaitLimit))
+  if (warp >= 2 && nq > 0 && !tc::warp_flag(&abort_flag) && !tc::mbar_wait_warp(&accf, 0, kWaitLimit))
     atomicExch(&abort_flag, 1);
   __syncthreads();   // abort_flag is final from here on
   tc::tc_fence_after();

@@ -64,6 +64,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
   return false;
 }
 
+// A flag in shared memory as lane 0 of the warp reads it (uniform over the warp).
+__device__ __forceinline__ bool warp_flag(const int *flag) {
+  int v = 0;
+  if ((threadIdx.x & 31) == 0) v = *(const volatile int *)flag;
+  return __shfl_sync(0xffffffffu, v, 0) != 0;
+}
+
+// The same bounded wait for a whole warp: lane 0 polls, the result is shared
+// (32 lanes polling one barrier would serialise in the shared-memory pipe).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, uint32_t limit = 1u << 24) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, limit);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
 // ------------------------------------------------------------------ TMA
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
   asm volatile(

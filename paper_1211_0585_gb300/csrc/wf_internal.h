@@ -154,9 +154,11 @@ struct BatchArgs {
   const double *d, *w, *cl;  // [B][npix], [B][npix], [B][lmax+1]
   float2 *dw32;              // [B][npix] (d, w) in FP32, read by the mixed-precision ring stage
   double2 *s;                // [B][nalm] exported a_lm of finished slots
-  float4 *sdf;               // [B][nalm] state, double-float (re hi, re lo, im hi, im lo)
-  float2 *fdf;               // [B][lmax+1] Eq. 4 filter f_l(lambda_b) of this iteration, double-float
-  float *icl;                // [B][lmax+1] 1 / C_l (0 where C_l = 0)
+  float4 *sdf;               // [B][nalm] state, double-float (re hi, re lo, im hi, im lo), in the
+                             // order of the analysis table rows: (m, parity of l - m, (l - m) / 2)
+  const int *alm_of_row;     // [nalm] a_lm index m (2 lmax + 1 - m) / 2 + l of each state row
+  float2 *fdf;               // [lmax+1][B] Eq. 4 filter f_l(lambda_b) of this iteration, double-float
+  float *icl;                // [lmax+1][B] 1 / C_l (0 where C_l = 0)
   float4 *FS, *FT;           // [(m RP + k) B + b] (north re, north im, south re, south im)
   Ctl *ctl;                  // [B]
   const int *active;         // [B]
@@ -184,8 +186,11 @@ struct TcArgs {
 void launch_lam_tc_tables(const double *x, const LegDfArgs &D, int lmax, int RP, int RPp, const int *offTc,
                           float *lamA, float *lamT, cudaStream_t s);
 struct TcMaps;
+// groups: slots per ring-stage CTA for each class (0 or nullptr: the default rule)
 void launch_batch_iteration(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, const RingClass *cls, int ncls,
-                            int *bstate, cudaStream_t s);
+                            const int *groups, int *bstate, cudaStream_t s);
+void launch_batch_ring_class(const BatchArgs &a, const RingClass &c, int G, cudaStream_t s);
+bool batch_ring_group_ok(int logM, int G);
 void launch_batch_state(const BatchArgs &a, int *bstate, cudaStream_t s);
 void launch_batch_zero_slot(const BatchArgs &a, const TcArgs &t, long long nchunks, int b, cudaStream_t s);
 void launch_batch_convert_slot(const BatchArgs &a, int b, cudaStream_t s);
