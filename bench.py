@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-mixed and serving measurements")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--profile-batch", type=int, nargs=2, metavar=("NRHS", "ITERS"), default=None,
+                    help="profiling target: ITERS full-band iterations of the batched engine on NRHS right-hand "
+                         "sides of the WMAP-shaped problem (cooling off), one text line, no JSON")
     return ap.parse_args()
 
 
@@ -427,8 +430,37 @@ def run_reference(args):
 DEFAULT_LEVELS = [[6.1793721184416155, 120, 5], [1.575, 140, 4], [1.0, 1024, 342]]
 
 
+def profile_batch(nrhs, iters, seed):
+    """A fixed amount of full-band batched work for ncu captures: every
+    iteration runs at lambda = 1 and lmax_SHT = lmax (cooling off)."""
+    import torch
+    from paper_1211_0585_gb300 import wf
+    prob = make_problem(seed)
+    P64 = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask, wf.options())
+    Pm = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask,
+                 wf.options(tol=0.0, max_iter=iters, cooling=0, precision=wf.WF_PREC_MIXED,
+                            batch_slots=min(64, nrhs)))
+    a = torch.from_numpy(prob.alm_true.view(np.float64).copy()).cuda()
+    base = torch.empty(prob.npix, dtype=torch.float64, device="cuda")
+    P64.alm2map(LMAX, a.data_ptr(), base.data_ptr())
+    torch.cuda.synchronize()
+    D = torch.stack([base + torch.from_numpy(np.random.default_rng(seed + i).standard_normal(prob.npix)
+                                             * np.sqrt(prob.noise_var)).cuda() for i in range(nrhs)])
+    out = torch.empty((nrhs, 2 * Pm.nalm), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, status = Pm.solve_batch(D.data_ptr(), on_device=True, alm_out=out.data_ptr(), nrhs=nrhs)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(f"full-band batched: {nrhs} right-hand sides x {iters} iterations in {dt:.3f} s "
+          f"({1e3 * dt / iters:.2f} ms / iteration, status {status})", flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_batch:
+        profile_batch(args.profile_batch[0], args.profile_batch[1], args.seed)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
