@@ -41,10 +41,17 @@ namespace wfk {
 
 namespace {
 
-constexpr int kStages = 2;
+// Products per k-step: 5 (FP32-level: the data split exactly into three tf32
+// parts) or 3 (data in two parts, ~2^-22 per product).
+constexpr int kProducts = 5;
+constexpr int kDerTiles = kProducts == 5 ? 3 : 2;   // table lo, data (mid,) lo
+constexpr int kDerSets = 2;                          // double-buffered split parts
 constexpr int kTileRows = 128;                       // M of every MMA
 constexpr int kTileBytes = kTileRows * 128;          // 128 rows x 32 fp32
-constexpr int kGemmThreads = 192;
+constexpr int kSmemTiles = 12;                       // 192 KB of operand tiles per CTA
+constexpr int kStages = (kSmemTiles - kDerSets * kDerTiles) / 2;   // raw TMA stages (table, data)
+constexpr int kSynThreads = 320;                     // synthesis: TMA, MMA, 8 splitting warps (2-5: epilogue)
+constexpr int kSynSplitWarps = 8;
 constexpr uint32_t kWaitLimit = 1u << 22;            // polls of one bounded mbarrier wait
 
 __device__ __forceinline__ size_t aidx(int lmax, int l, int m) { return (size_t)m * (2 * lmax + 1 - m) / 2 + l; }
@@ -52,80 +59,100 @@ __device__ __forceinline__ size_t aidx(int lmax, int l, int m) { return (size_t)
 // number of l in [m, L] with l - m = p (mod 2)
 __host__ __device__ __forceinline__ int n_par(int m, int p, int L) { return L >= m + p ? (L - m - p) / 2 + 1 : 0; }
 
-enum { kTA = 0, kTAlo = 1, kTB = 2, kTBmid = 3, kTBlo = 4, kTiles = 5 };
-
+// Shared memory: kStages raw stages of (table, data) tiles that TMA fills, the
+// tf32 split writing the leading parts in place, and kDerSets sets of the
+// remaining parts (table lo, data mid, data lo). Every tile 1024-byte aligned.
 struct Smem {
-  // per stage: table hi (landed raw), table lo, data hi (landed raw), data mid,
-  // data lo; every tile 1024-byte aligned
-  __device__ static uint8_t *tile(uint8_t *base, int s, int which) {
-    return base + ((size_t)s * kTiles + which) * kTileBytes;
+  __device__ static uint8_t *raw(uint8_t *base, int s, int which) {   // which: 0 table, 1 data
+    return base + ((size_t)s * 2 + which) * kTileBytes;
+  }
+  __device__ static uint8_t *der(uint8_t *base, int d, int which) {   // which: 0 table lo, 1 data lo, 2 data mid
+    return base + ((size_t)kStages * 2 + (size_t)d * kDerTiles + which) * kTileBytes;
   }
 };
 
-// table tile (22-bit values): th in place, tl = v - th (exact)
+// v rounded to 11 significant bits (a tf32 number; ties away from zero) by
+// integer arithmetic on its bits; v - hi is then exact. Rounding to nearest
+// keeps the remainders unbiased, so the correction sums partly cancel.
+__device__ __forceinline__ float tf32_rn(float v) {
+  return __int_as_float((__float_as_int(v) + 0x1000) & (int)0xffffe000);
+}
+
+// table tile (22-bit values): th = v rounded to 11 bits in place, tl = v - th
+// (exact, and a tf32 number)
 __device__ __forceinline__ void split_table(uint8_t *hi, uint8_t *lo, int nbytes, int t, int nt) {
   float4 *h4 = reinterpret_cast<float4 *>(hi);
   float4 *l4 = reinterpret_cast<float4 *>(lo);
   for (int e = t; e < nbytes / 16; e += nt) {
     const float4 v = h4[e];
     float4 h, l;
-    h.x = tc::to_tf32(v.x); l.x = tc::to_tf32(v.x - h.x);
-    h.y = tc::to_tf32(v.y); l.y = tc::to_tf32(v.y - h.y);
-    h.z = tc::to_tf32(v.z); l.z = tc::to_tf32(v.z - h.z);
-    h.w = tc::to_tf32(v.w); l.w = tc::to_tf32(v.w - h.w);
+    h.x = tf32_rn(v.x); l.x = v.x - h.x;
+    h.y = tf32_rn(v.y); l.y = v.y - h.y;
+    h.z = tf32_rn(v.z); l.z = v.z - h.z;
+    h.w = tf32_rn(v.w); l.w = v.w - h.w;
     h4[e] = h;
     l4[e] = l;
   }
 }
 
+// v = h + m + l exactly: 11 + 11 + at most 3 significant bits, every part a tf32 number
 __device__ __forceinline__ void split3(float v, float &h, float &m, float &l) {
-  h = tc::to_tf32(v);
+  h = tf32_rn(v);
   const float r = v - h;   // exact
-  m = tc::to_tf32(r);
-  l = tc::to_tf32(r - m);  // exact: at most 2 significant bits remain
+  m = tf32_rn(r);
+  l = r - m;               // exact: the last bits
 }
 
-// data tile (FP32): ah in place, am, al (ah + am + al = v exactly)
-__device__ __forceinline__ void split_data(uint8_t *hi, uint8_t *mid, uint8_t *lo, int nbytes, int t, int nt) {
+// data tile (FP32): ah in place, then am, al (ah + am + al = v exactly) or,
+// with three products, al = v - ah rounded to 11 bits
+__device__ __forceinline__ void split_data(uint8_t *hi, uint8_t *lo, uint8_t *mid, int nbytes, int t, int nt) {
   float4 *h4 = reinterpret_cast<float4 *>(hi);
   float4 *m4 = reinterpret_cast<float4 *>(mid);
   float4 *l4 = reinterpret_cast<float4 *>(lo);
   for (int e = t; e < nbytes / 16; e += nt) {
     const float4 v = h4[e];
     float4 h, m, l;
-    split3(v.x, h.x, m.x, l.x);
-    split3(v.y, h.y, m.y, l.y);
-    split3(v.z, h.z, m.z, l.z);
-    split3(v.w, h.w, m.w, l.w);
+    if (kProducts == 5) {
+      split3(v.x, h.x, m.x, l.x);
+      split3(v.y, h.y, m.y, l.y);
+      split3(v.z, h.z, m.z, l.z);
+      split3(v.w, h.w, m.w, l.w);
+      m4[e] = m;
+    } else {
+      h.x = tf32_rn(v.x); l.x = tf32_rn(v.x - h.x);
+      h.y = tf32_rn(v.y); l.y = tf32_rn(v.y - h.y);
+      h.z = tf32_rn(v.z); l.z = tf32_rn(v.z - h.z);
+      h.w = tf32_rn(v.w); l.w = tf32_rn(v.w - h.w);
+    }
     h4[e] = h;
-    m4[e] = m;
     l4[e] = l;
   }
 }
 
-// 4 k-steps of 8 over one 32-wide chunk of stage tiles, five products per
-// step. The leading product th ah accumulates alone in `dmain`; the four
-// correction products (2^-11 and less of it) accumulate in `dcorr`, so the
-// rounding of the tensor-core accumulation stays relative to each sum's own
-// size (the leading sum is not perturbed by the many small additions).
-// REV runs the k-steps from the end of the chunk to its start.
+// 4 k-steps of 8 over one 32-wide chunk. The leading product th ah
+// accumulates alone in `dmain`; the correction products (2^-11 and less of
+// it) accumulate in `dcorr`, so the rounding of the tensor-core accumulation
+// stays relative to each sum's own size. REV runs the k-steps from the end of
+// the chunk to its start.
 template <bool REV = false>
-__device__ __forceinline__ void mma_chunk(uint32_t dmain, uint32_t dcorr, uint8_t *stage, uint32_t idesc,
+__device__ __forceinline__ void mma_chunk(uint32_t dmain, uint32_t dcorr, uint8_t *raw, uint8_t *der, uint32_t idesc,
                                           bool acc_main, bool acc_corr) {
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     const int ks = REV ? 3 - kk : kk;
     const uint64_t off = (uint64_t)((ks * 32) >> 4);   // 32 bytes along K inside the swizzle atom
-    const uint64_t th = tc::sw128_desc(stage + kTA * kTileBytes) + off;
-    const uint64_t tl = tc::sw128_desc(stage + kTAlo * kTileBytes) + off;
-    const uint64_t ah = tc::sw128_desc(stage + kTB * kTileBytes) + off;
-    const uint64_t am = tc::sw128_desc(stage + kTBmid * kTileBytes) + off;
-    const uint64_t al = tc::sw128_desc(stage + kTBlo * kTileBytes) + off;
+    const uint64_t th = tc::sw128_desc(raw) + off;
+    const uint64_t ah = tc::sw128_desc(raw + kTileBytes) + off;
+    const uint64_t tl = tc::sw128_desc(der) + off;
+    const uint64_t al = tc::sw128_desc(der + kTileBytes) + off;
     tc::mma_tf32(dmain, th, ah, idesc, acc_main || kk > 0);
-    tc::mma_tf32(dcorr, th, am, idesc, acc_corr || kk > 0);
+    tc::mma_tf32(dcorr, th, al, idesc, acc_corr || kk > 0);
     tc::mma_tf32(dcorr, tl, ah, idesc, true);
-    tc::mma_tf32(dcorr, tl, am, idesc, true);
-    tc::mma_tf32(dcorr, th, al, idesc, true);
+    if (kProducts == 5) {
+      const uint64_t am = tc::sw128_desc(der + 2 * kTileBytes) + off;
+      tc::mma_tf32(dcorr, th, am, idesc, true);
+      tc::mma_tf32(dcorr, tl, am, idesc, true);
+    }
   }
 }
 
@@ -241,9 +268,10 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
                    const BatchArgs A, const TcArgs T) {
   extern __shared__ __align__(1024) uint8_t tsm_raw[];
   uint8_t *tsm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], segf[2], segfree[2];
+  __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], dfree[kDerSets], segf[2], segfree[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ unsigned long long live_slots;   // bit b: slot b iterates
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int4 tile = T.atiles[blockIdx.x];
   const int m = tile.x, p = tile.y, i0 = tile.z, rowA = tile.w;
@@ -259,15 +287,20 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&conv[s], 128);
+      tc::mbar_init(&conv[s], 4);   // one arrival per splitting warp
       tc::mbar_init(&empty[s], 1);
     }
+    for (int d = 0; d < kDerSets; ++d) tc::mbar_init(&dfree[d], 1);
     for (int j = 0; j < 2; ++j) {
       tc::mbar_init(&segf[j], 1);
-      tc::mbar_init(&segfree[j], kFoldThreads);
+      tc::mbar_init(&segfree[j], kFoldThreads / 32);   // one arrival per folding warp
     }
     tc::fence_mbar_init();
     abort_flag = 0;
+    unsigned long long mask = 0;
+    for (int b = 0; b < B; ++b)
+      if (A.active[b] && !A.ctl[b].done) mask |= 1ull << b;
+    live_slots = mask;
   }
   if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
   tc::tc_fence_before();
@@ -289,8 +322,8 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
       }
       if (*(volatile int *)&abort_flag) break;
       tc::mbar_arrive_expect_tx(&full[s], kTileBytes + bbytes);
-      tc::tma_load_2d(Smem::tile(tsm, s, kTA), &mapA, 32 * kc, rowA + i0, &full[s]);
-      tc::tma_load_2d(Smem::tile(tsm, s, kTB), &mapX, 0, (int)((((size_t)m * 2 + p) * T.nkc + kc) * Nc), &full[s]);
+      tc::tma_load_2d(Smem::raw(tsm, s, 0), &mapA, 32 * kc, rowA + i0, &full[s]);
+      tc::tma_load_2d(Smem::raw(tsm, s, 1), &mapX, 0, (int)((((size_t)m * 2 + p) * T.nkc + kc) * Nc), &full[s]);
       issued = kc + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -308,22 +341,24 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
         break;
       }
       tc::tc_fence_after();
-      mma_chunk(seg, tmem + kColCorr, Smem::tile(tsm, s, 0), idesc, false, kc > 0);
+      mma_chunk(seg, tmem + kColCorr, Smem::raw(tsm, s, 0), Smem::der(tsm, kc % kDerSets, 0), idesc, false, kc > 0);
       tc::mma_commit(&empty[s]);
+      tc::mma_commit(&dfree[kc % kDerSets]);
       tc::mma_commit(&segf[kc & 1]);
     }
   } else if (warp >= 2 && warp < 6) {
     const int t = threadIdx.x - 64;
     for (int kc = 0; kc < nkc; ++kc) {
-      const int s = kc % kStages;
-      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&full[s], (kc / kStages) & 1, kWaitLimit)) {
+      const int s = kc % kStages, dset = kc % kDerSets;
+      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&full[s], (kc / kStages) & 1, kWaitLimit) ||
+          (kc >= kDerSets && !tc::mbar_wait_warp(&dfree[dset], ((kc / kDerSets) - 1) & 1, kWaitLimit))) {
         atomicExch(&abort_flag, 1);
         break;
       }
-      split_table(Smem::tile(tsm, s, kTA), Smem::tile(tsm, s, kTAlo), kTileBytes, t, 128);
-      split_data(Smem::tile(tsm, s, kTB), Smem::tile(tsm, s, kTBmid), Smem::tile(tsm, s, kTBlo), (int)bbytes, t, 128);
+      split_table(Smem::raw(tsm, s, 0), Smem::der(tsm, dset, 0), kTileBytes, t, 128);
+      split_data(Smem::raw(tsm, s, 1), Smem::der(tsm, dset, 1), Smem::der(tsm, dset, 2), (int)bbytes, t, 128);
       tc::fence_proxy_async_smem();
-      tc::mbar_arrive(&conv[s]);
+      tc::mbar_arrive_warp(&conv[s]);
     }
   }
   // folding warps: chunk sums into (hi in TMEM, lo in registers)
@@ -344,13 +379,20 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
       for (int bb = 0; bb < 4; ++bb) {
         const int cb = 4 * fh + bb;
         if (16 * cb >= Nc) break;
+        uint32_t vr[16], hr[16];
+        tc::tmem_ld16_issue(seg + 16 * cb, vr);
+        if (kc > 0) tc::tmem_ld16_issue(tmem + flanes + kColHi + 16 * cb, hr);
+        tc::tmem_ld_wait(vr);
+        if (kc > 0) tc::tmem_ld_wait(hr);
         float v[16], h[16];
-        tc::tmem_ld16(seg + 16 * cb, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(vr[e]);
         if (kc == 0) {
 #pragma unroll
           for (int e = 0; e < 16; ++e) h[e] = v[e];
         } else {
-          tc::tmem_ld16(tmem + flanes + kColHi + 16 * cb, h);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) h[e] = __uint_as_float(hr[e]);
 #pragma unroll
           for (int e = 0; e < 16; ++e) {   // two_sum(h, v): the rounding error goes to lo
             const float sum = h[e] + v[e];
@@ -363,8 +405,20 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
       }
       tc::tmem_wait_st();
       tc::tc_fence_before();
-      tc::mbar_arrive(&segfree[kc & 1]);
+      tc::mbar_arrive_warp(&segfree[kc & 1]);
     }
+    // the chunk blocks are free now: park lo there for the epilogue (frees the registers)
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) {
+      const int cb = 4 * fh + bb;
+      if (16 * cb >= Nc) break;
+      float v[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] = lo[16 * bb + e];
+      tc::tmem_st16(tmem + flanes + kColSeg0 + 16 * cb, v);
+    }
+    tc::tmem_wait_st();
+    tc::tc_fence_before();
   }
 
   // ---- epilogue (warps 6-13)
@@ -386,34 +440,57 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
       if (16 * cb >= Nc) break;
       float th[16], tl[16];
       if (ok_acc) {   // t = hi + (lo + corrections)
-        tc::tmem_ld16(tmem + flanes + kColHi + 16 * cb, th);
-        tc::tmem_ld16(tmem + flanes + kColCorr + 16 * cb, tl);
+        uint32_t hr[16], cr[16], lr[16];
+        tc::tmem_ld16_issue(tmem + flanes + kColHi + 16 * cb, hr);
+        tc::tmem_ld16_issue(tmem + flanes + kColCorr + 16 * cb, cr);
+        tc::tmem_ld16_issue(tmem + flanes + kColSeg0 + 16 * cb, lr);
+        tc::tmem_ld_wait(hr);
+        tc::tmem_ld_wait(cr);
+        tc::tmem_ld_wait(lr);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) tl[e] += lo[16 * bb + e];
+        for (int e = 0; e < 16; ++e) {
+          th[e] = __uint_as_float(hr[e]);
+          tl[e] = __uint_as_float(cr[e]) + __uint_as_float(lr[e]);
+        }
       } else {
 #pragma unroll
         for (int e = 0; e < 16; ++e) { th[e] = 0.f; tl[e] = 0.f; }
       }
+      // every load of the eight slots first (independent), then the updates
+      const unsigned live8 = row_ok ? (unsigned)(live_slots >> (8 * cb)) & 0xffu : 0u;
+      float4 so[8], fv[4], iv[2];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        so[jj] = (live8 >> jj) & 1u ? A.sdf[(size_t)(8 * cb + jj) * A.nalm + idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (live8) {   // filter and 1 / C_l of the eight slots: [l][slot], 16-byte aligned runs
+        const float4 *f4 = reinterpret_cast<const float4 *>(A.fdf + (size_t)l * B + 8 * cb);
+        const float4 *c4 = reinterpret_cast<const float4 *>(A.icl + (size_t)l * B + 8 * cb);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) fv[e] = f4[e];
+        iv[0] = c4[0];
+        iv[1] = c4[1];
+      }
+      float *spt = T.SPT + (((size_t)T.offTc[2 * m + p] + (i >> 5)) * Nc + 16 * cb) * 32 + (i & 31);
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
         const int b = 8 * cb + jj;
         float c2 = 0.f, inc = 0.f, nrm = 0.f;
-        if (row_ok && b < B && A.active[b] && !A.ctl[b].done) {
-          float4 *sb = A.sdf + (size_t)b * A.nalm;
-          const float4 so = sb[idx];
-          const float2 f2 = A.fdf[(size_t)l * B + b];
-          const dfl f = dfl{f2.x, f2.y};
-          const dfl re = df_mul(f, df_add(dfl{so.x, so.y}, dfl{th[2 * jj], tl[2 * jj]}));
-          const dfl im = df_mul(f, df_add(dfl{so.z, so.w}, dfl{th[2 * jj + 1], tl[2 * jj + 1]}));
+        if ((live8 >> jj) & 1u) {
+          const float4 fq4 = fv[jj >> 1];
+          const dfl f = (jj & 1) ? dfl{fq4.z, fq4.w} : dfl{fq4.x, fq4.y};
+          const float icl = (jj < 4) ? ((jj & 2) ? ((jj & 1) ? iv[0].w : iv[0].z) : ((jj & 1) ? iv[0].y : iv[0].x))
+                                     : ((jj & 2) ? ((jj & 1) ? iv[1].w : iv[1].z) : ((jj & 1) ? iv[1].y : iv[1].x));
+          const float4 o = so[jj];
+          const dfl re = df_mul(f, df_add(dfl{o.x, o.y}, dfl{th[2 * jj], tl[2 * jj]}));
+          const dfl im = df_mul(f, df_add(dfl{o.z, o.w}, dfl{th[2 * jj + 1], tl[2 * jj + 1]}));
           const float4 sn = make_float4(re.h, re.l, im.h, im.l);
-          c2 = wgt * (so.x * so.x + so.z * so.z) * A.icl[(size_t)l * B + b];
-          const float dx = (sn.x - so.x) + (sn.y - so.y), dy = (sn.z - so.z) + (sn.w - so.w);
+          c2 = wgt * (o.x * o.x + o.z * o.z) * icl;
+          const float dx = (sn.x - o.x) + (sn.y - o.y), dy = (sn.z - o.z) + (sn.w - o.w);
           inc = wgt * (dx * dx + dy * dy);
           nrm = wgt * (sn.x * sn.x + sn.z * sn.z);
-          sb[idx] = sn;
-          float *spt = T.SPT + (((size_t)T.offTc[2 * m + p] + (i >> 5)) * Nc + 2 * b) * 32 + (i & 31);
-          spt[0] = sn.x;
-          spt[32] = sn.z;
+          A.sdf[(size_t)b * A.nalm + idx] = sn;
+          spt[(2 * jj) * 32] = sn.x;
+          spt[(2 * jj + 1) * 32] = sn.z;
         }
         red[(0 * B + b) * 129 + r] = c2;
         red[(1 * B + b) * 129 + r] = inc;
@@ -447,12 +524,12 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
 // One CTA per (m, 128 ring pairs): E and O accumulate in two tensor-memory
 // blocks over the chunks of 32 values of i of each parity up to the live band
 // limit; the epilogue writes FS = (E + O, E - O) for every slot.
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(kSynThreads, 1)
     bsyn_tc_kernel(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapS,
                    const BatchArgs A, const TcArgs T) {
   extern __shared__ __align__(1024) uint8_t tsm_raw[];
   uint8_t *tsm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], accf;
+  __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], dfree[kDerSets], accf;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -466,9 +543,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&conv[s], 128);
+      tc::mbar_init(&conv[s], kSynSplitWarps);   // one arrival per splitting warp
       tc::mbar_init(&empty[s], 1);
     }
+    for (int d = 0; d < kDerSets; ++d) tc::mbar_init(&dfree[d], 1);
     tc::mbar_init(&accf, 1);
     tc::fence_mbar_init();
     abort_flag = 0;
@@ -499,8 +577,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const int p = qi < nc0 ? 0 : 1, ic = p ? nc0 + nc1 - 1 - qi : nc0 - 1 - qi;
       const long long q = (long long)T.offTc[2 * m + p] + ic;
       tc::mbar_arrive_expect_tx(&full[s], kTileBytes + bbytes);
-      tc::tma_load_2d(Smem::tile(tsm, s, kTA), &mapT, 0, (int)(q * T.RPp + k0), &full[s]);
-      tc::tma_load_2d(Smem::tile(tsm, s, kTB), &mapS, 0, (int)(q * Nc), &full[s]);
+      tc::tma_load_2d(Smem::raw(tsm, s, 0), &mapT, 0, (int)(q * T.RPp + k0), &full[s]);
+      tc::tma_load_2d(Smem::raw(tsm, s, 1), &mapS, 0, (int)(q * Nc), &full[s]);
       issued = qi + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -513,51 +591,62 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       tc::tc_fence_after();
       const int p = qi < nc0 ? 0 : 1, first = p ? qi == nc0 : qi == 0;
       // leading products of parity p in columns 128 p, corrections in 256 + 128 p
-      mma_chunk<true>(tmem + (uint32_t)(128 * p), tmem + (uint32_t)(256 + 128 * p), Smem::tile(tsm, s, 0), idesc,
-                      !first, !first);
+      mma_chunk<true>(tmem + (uint32_t)(128 * p), tmem + (uint32_t)(256 + 128 * p), Smem::raw(tsm, s, 0),
+                      Smem::der(tsm, qi % kDerSets, 0), idesc, !first, !first);
       tc::mma_commit(&empty[s]);
+      tc::mma_commit(&dfree[qi % kDerSets]);
     }
     if (nq > 0) tc::mma_commit(&accf);
   } else if (warp >= 2) {
-    const int t = threadIdx.x - 64;
+    const int t = threadIdx.x - 64, nt = 32 * kSynSplitWarps;
     for (int qi = 0; qi < nq; ++qi) {
-      const int s = qi % kStages;
-      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&full[s], (qi / kStages) & 1, kWaitLimit)) {
+      const int s = qi % kStages, dset = qi % kDerSets;
+      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&full[s], (qi / kStages) & 1, kWaitLimit) ||
+          (qi >= kDerSets && !tc::mbar_wait_warp(&dfree[dset], ((qi / kDerSets) - 1) & 1, kWaitLimit))) {
         atomicExch(&abort_flag, 1);
         break;
       }
-      split_table(Smem::tile(tsm, s, kTA), Smem::tile(tsm, s, kTAlo), kTileBytes, t, 128);
-      split_data(Smem::tile(tsm, s, kTB), Smem::tile(tsm, s, kTBmid), Smem::tile(tsm, s, kTBlo), (int)bbytes, t, 128);
+      split_table(Smem::raw(tsm, s, 0), Smem::der(tsm, dset, 0), kTileBytes, t, nt);
+      split_data(Smem::raw(tsm, s, 1), Smem::der(tsm, dset, 1), Smem::der(tsm, dset, 2), (int)bbytes, t, nt);
       tc::fence_proxy_async_smem();
-      tc::mbar_arrive(&conv[s]);
+      tc::mbar_arrive_warp(&conv[s]);
     }
   }
   // ---- epilogue (warps 2-5): row k0 + r of E (columns 0 .. Nc) and O (Nc .. 2 Nc)
-  if (warp >= 2 && nq > 0 && !tc::warp_flag(&abort_flag) && !tc::mbar_wait_warp(&accf, 0, kWaitLimit))
+  if (warp >= 2 && warp < 6 && nq > 0 && !tc::warp_flag(&abort_flag) && !tc::mbar_wait_warp(&accf, 0, kWaitLimit))
     atomicExch(&abort_flag, 1);
   __syncthreads();   // abort_flag is final from here on
   tc::tc_fence_after();
   const bool have = nq > 0 && abort_flag == 0;   // uniform over the CTA
-  if (warp >= 2) {
+  if (warp >= 2 && warp < 6) {
     const int qd = warp & 3;
     const int k = k0 + 32 * qd + lane;
     const uint32_t lanes = (uint32_t)(32 * qd) << 16;
     for (int cb = 0; cb < Nc / 16; ++cb) {
-      float e[16], o[16], ce[16], co[16];
+      float e[16], o[16];
+      uint32_t er[16], cer[16], orr[16], cor[16];
       if (have && nc0 > 0) {
-        tc::tmem_ld16(tmem + lanes + 16 * cb, e);
-        tc::tmem_ld16(tmem + lanes + 256 + 16 * cb, ce);
+        tc::tmem_ld16_issue(tmem + lanes + 16 * cb, er);
+        tc::tmem_ld16_issue(tmem + lanes + 256 + 16 * cb, cer);
+      }
+      if (have && nc1 > 0) {
+        tc::tmem_ld16_issue(tmem + lanes + 128 + 16 * cb, orr);
+        tc::tmem_ld16_issue(tmem + lanes + 384 + 16 * cb, cor);
+      }
+      if (have && nc0 > 0) {
+        tc::tmem_ld_wait(er);
+        tc::tmem_ld_wait(cer);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) e[j] += ce[j];
+        for (int j = 0; j < 16; ++j) e[j] = __uint_as_float(er[j]) + __uint_as_float(cer[j]);
       } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) e[j] = 0.f;
       }
       if (have && nc1 > 0) {
-        tc::tmem_ld16(tmem + lanes + 128 + 16 * cb, o);
-        tc::tmem_ld16(tmem + lanes + 384 + 16 * cb, co);
+        tc::tmem_ld_wait(orr);
+        tc::tmem_ld_wait(cor);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) o[j] += co[j];
+        for (int j = 0; j < 16; ++j) o[j] = __uint_as_float(orr[j]) + __uint_as_float(cor[j]);
       } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) o[j] = 0.f;
@@ -587,7 +676,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 }
 
 // ---------------------------------------------------------------- host side
-static size_t gemm_smem() { return (size_t)kStages * kTiles * kTileBytes + 1024; }
+static size_t gemm_smem() { return (size_t)kSmemTiles * kTileBytes + 1024; }
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -630,7 +719,7 @@ void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &ma
     xt_kernel<<<dim3(t.nkc, a.lmax + 1), 256, 0, s>>>(a, t);
     bana_tc_kernel<<<t.natiles, kAnaThreads, gemm_smem(), s>>>(maps.A, maps.X, a, t);
   } else {
-    bsyn_tc_kernel<<<t.nstiles, kGemmThreads, gemm_smem(), s>>>(maps.T, maps.S, a, t);
+    bsyn_tc_kernel<<<t.nstiles, kSynThreads, gemm_smem(), s>>>(maps.T, maps.S, a, t);
   }
 }
 
