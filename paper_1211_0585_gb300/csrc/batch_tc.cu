@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(256) xt_kernel(const BatchArgs A, const TcArgs
 // partials.
 constexpr int kAnaThreads = 448;
 constexpr int kFoldThreads = 256;
+constexpr int kFoldChunks = 1;   // chunks of 32 ring pairs per folded segment
 constexpr uint32_t kColSeg0 = 0, kColSeg1 = 128, kColCorr = 256, kColHi = 384;
 
 __global__ void __launch_bounds__(kAnaThreads, 1)
@@ -328,11 +329,11 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
     }
   } else if (warp == 1 && lane == 0) {
     for (int kc = 0; kc < nkc; ++kc) {
-      const int s = kc % kStages;
-      const uint32_t seg = tmem + ((kc & 1) ? kColSeg1 : kColSeg0);
-      // a chunk block is reused once the folding warps have read it
-      if (kc >= 2 &&
-          (*(volatile int *)&abort_flag || !tc::mbar_wait(&segfree[kc & 1], ((kc - 2) >> 1) & 1, kWaitLimit))) {
+      const int s = kc % kStages, j = kc / kFoldChunks;
+      const uint32_t seg = tmem + ((j & 1) ? kColSeg1 : kColSeg0);
+      // a segment block is reused once the folding warps have read it
+      if (kc % kFoldChunks == 0 && j >= 2 &&
+          (*(volatile int *)&abort_flag || !tc::mbar_wait(&segfree[j & 1], ((j - 2) >> 1) & 1, kWaitLimit))) {
         atomicExch(&abort_flag, 1);
         break;
       }
@@ -341,10 +342,11 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
         break;
       }
       tc::tc_fence_after();
-      mma_chunk(seg, tmem + kColCorr, Smem::raw(tsm, s, 0), Smem::der(tsm, kc % kDerSets, 0), idesc, false, kc > 0);
+      mma_chunk(seg, tmem + kColCorr, Smem::raw(tsm, s, 0), Smem::der(tsm, kc % kDerSets, 0), idesc,
+                kc % kFoldChunks != 0, kc > 0);
       tc::mma_commit(&empty[s]);
       tc::mma_commit(&dfree[kc % kDerSets]);
-      tc::mma_commit(&segf[kc & 1]);
+      if (kc % kFoldChunks == kFoldChunks - 1 || kc == nkc - 1) tc::mma_commit(&segf[j & 1]);
     }
   } else if (warp >= 2 && warp < 6) {
     const int t = threadIdx.x - 64;
@@ -368,7 +370,8 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
 #pragma unroll
   for (int e = 0; e < 64; ++e) lo[e] = 0.f;
   if (warp >= 6) {
-    for (int kc = 0; kc < nkc; ++kc) {
+    const int nseg = (nkc + kFoldChunks - 1) / kFoldChunks;
+    for (int kc = 0; kc < nseg; ++kc) {   // segment index
       if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&segf[kc & 1], (kc >> 1) & 1, kWaitLimit)) {
         atomicExch(&abort_flag, 1);
         break;
