@@ -166,36 +166,49 @@ __global__ void __launch_bounds__(kBringThreads, 6) bring_kernel(const BatchArgs
   float c2n[G], c2l[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) { c2n[g] = 0.f; c2l[g] = 0.f; }
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const float2 cp = rg.blue ? hi2(ch[p]) : make_float2(0.f, 0.f);
-    const int br = px<OpsF32>(rg.blue ? p : digitrev(p, rg.logM));
+  // kPix pixels per thread at a time: their (d, w) loads are issued together
+  constexpr int kPix = G <= 2 ? 8 : 16 / G;
+  for (int p0 = threadIdx.x; p0 < n; p0 += kPix * blockDim.x) {
+    float2 dw[kPix][G];
 #pragma unroll
-    for (int pp = 0; pp < P; ++pp) {
-      const float2 z = buf[pp * M + br];
-      float sv[2];
-      if (rg.blue) {   // the inverse DFT came out conjugated (conj of the DFT of conj Z)
-        const float2 R = f2mul(cp, z);
-        sv[0] = R.x; sv[1] = -R.y;
-      } else {
-        sv[0] = z.x; sv[1] = z.y;
-      }
-      float u[2];
+    for (int k = 0; k < kPix; ++k) {
+      const int p = p0 + k * blockDim.x;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int g = 2 * pp + e;
-        u[e] = 0.f;
-        if (!on[g]) continue;
-        const size_t pix = (size_t)(b0 + g) * A.npix + rg.off + p;
-        const float2 dw = __ldg(A.dw32 + pix);
-        const float wp = dw.y;
-        const float res = dw.x - sv[e];
-        const float gg = __fdividef(wp, fmaf(l1t[g], wp, 1.f));
-        c2n[g] = fmaf(wp * res, res, c2n[g]);
-        c2l[g] = fmaf(gg * res, res, c2l[g]);
-        u[e] = lt[g] * gg * res;
+      for (int g = 0; g < G; ++g)
+        dw[k][g] = (p < n && on[g]) ? __ldg(A.dw32 + (size_t)(b0 + g) * A.npix + rg.off + p) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+      const int p = p0 + k * blockDim.x;
+      if (p >= n) break;
+      const float2 cp = rg.blue ? hi2(ch[p]) : make_float2(0.f, 0.f);
+      const int br = px<OpsF32>(rg.blue ? p : digitrev(p, rg.logM));
+#pragma unroll
+      for (int pp = 0; pp < P; ++pp) {
+        const float2 z = buf[pp * M + br];
+        float sv[2];
+        if (rg.blue) {   // the inverse DFT came out conjugated (conj of the DFT of conj Z)
+          const float2 R = f2mul(cp, z);
+          sv[0] = R.x; sv[1] = -R.y;
+        } else {
+          sv[0] = z.x; sv[1] = z.y;
+        }
+        float u[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int g = 2 * pp + e;
+          u[e] = 0.f;
+          if (!on[g]) continue;
+          const float wp = dw[k][g].y;
+          const float res = dw[k][g].x - sv[e];
+          const float gg = __fdividef(wp, fmaf(l1t[g], wp, 1.f));
+          c2n[g] = fmaf(wp * res, res, c2n[g]);
+          c2l[g] = fmaf(gg * res, res, c2l[g]);
+          u[e] = lt[g] * gg * res;
+        }
+        const float2 uz = make_float2(u[0], u[1]);
+        buf[pp * M + br] = rg.blue ? f2mul(uz, cp) : uz;
       }
-      const float2 uz = make_float2(u[0], u[1]);
-      buf[pp * M + br] = rg.blue ? f2mul(uz, cp) : uz;
     }
   }
   if (rg.blue)
