@@ -42,11 +42,11 @@ __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.x, v.z); 
 // The G / 2 packed arrays share every twiddle load, the pixel pass updates
 // them in place (the inverse transform's output order is the forward
 // transform's input order), and the G slots read their Fourier coefficients
-// as one contiguous run of G float4. Four CTAs of 128 threads per SM, so that
+// as one contiguous run of G float4. Three CTAs of 256 threads per SM, so that
 // the FFT passes of one CTA overlap the global loads and stores of another.
-constexpr int kBringThreads = 128;
+constexpr int kBringThreads = 256;
 template <int G>
-__global__ void __launch_bounds__(kBringThreads, 6) bring_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kBringThreads, 3) bring_kernel(const BatchArgs A) {
   static_assert(G % 2 == 0, "slots are packed in pairs");
   constexpr int P = G / 2;
   extern __shared__ float2 bsm[];
@@ -65,8 +65,10 @@ __global__ void __launch_bounds__(kBringThreads, 6) bring_kernel(const BatchArgs
   const RingDev rg = A.rings[r];
   const int n = rg.n, M = 1 << rg.logM;
   float2 *buf = bsm;                                          // [P][M] (swizzled, px)
+  // alias partial sums of rings shorter than the block: [kBringThreads][G] after
+  // the FFT buffers (present in the classes whose rings can be that short)
+  float2(*fpart)[G] = reinterpret_cast<float2(*)[G]>(bsm + P * M);
   __shared__ double red[kBringThreads / 32][2 * G];
-  __shared__ float2 fpart[kBringThreads][G];   // alias partial sums of short rings
   const float4 *hs = A.hsf + rg.hs_off;
   const float4 *ch = A.chf + rg.ch_off;
   const float2 *Bf = A.Bf2 + rg.B_off;
@@ -384,17 +386,25 @@ void launch_batch_convert_slot(const BatchArgs &a, int b, cudaStream_t s) {
 // shared memory of one packed pair of slots of a class
 static size_t bring_smem_per_pair(int logM) { return ((size_t)1 << logM) * sizeof(float2); }
 
-// slots per ring-stage CTA of a class: 8, 4 or 2 (pairs share one FFT),
-// within a quarter of an SM's shared memory so that four CTAs share each SM
+// shared memory of a CTA of G slots: the packed FFT buffers, plus the alias
+// partial sums when the class can hold rings shorter than the block
+static size_t bring_smem(int logM, int G) {
+  const size_t part = ((size_t)1 << logM) <= 2 * kBringThreads ? (size_t)kBringThreads * G * sizeof(float2) : 0;
+  return (size_t)(G / 2) * bring_smem_per_pair(logM) + part;
+}
+
+// default slots per ring-stage CTA of a class (before autotuning): 8, 4 or 2
+// (pairs share one FFT), within a third of an SM's shared memory so that three
+// CTAs share each SM
 static int batch_ring_group(int logM, int B) {
   int G = 8;
-  while (G > 2 && ((G / 2) * bring_smem_per_pair(logM) > 56 * 1024 || G >= 2 * B)) G >>= 1;
+  while (G > 2 && (bring_smem(logM, G) > 72 * 1024 || G >= 2 * B)) G >>= 1;
   return G;
 }
 
 template <int G>
 static void launch_bring(const BatchArgs &a, const RingClass &c, cudaStream_t s) {
-  const size_t sm = (size_t)(G / 2) * bring_smem_per_pair(c.logM);
+  const size_t sm = bring_smem(c.logM, G);
   BatchArgs ac = a;
   ac.first = c.first;
   bring_kernel<G><<<dim3(c.count, (a.B + G - 1) / G), kBringThreads, sm, s>>>(ac);
@@ -403,7 +413,7 @@ static void launch_bring(const BatchArgs &a, const RingClass &c, cudaStream_t s)
 // slots per CTA that a ring class may use: even, at most 8, the packed FFT
 // buffers within the shared memory of one CTA
 bool batch_ring_group_ok(int logM, int G) {
-  return (G == 2 || G == 4 || G == 8) && (size_t)(G / 2) * bring_smem_per_pair(logM) <= 200 * 1024;
+  return (G == 2 || G == 4 || G == 8) && bring_smem(logM, G) <= 200 * 1024;
 }
 
 void launch_batch_ring_class(const BatchArgs &a, const RingClass &c, int G, cudaStream_t s) {
