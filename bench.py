@@ -199,17 +199,36 @@ def run_ours(args):
     # recurrence step (19 FP32 instructions) and two compensated multiply-adds
     # (13 each) in each of the analysis and synthesis passes = 90 FP32
     # instructions; each counted as 2 flops against the FP32 FMA peak
-    flops = 2.0 * LEGENDRE_DF_INSTR * evaluated
-    achieved = flops / (prof["legendre"] * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "legendre_df_kernel<LEG_ITER> (double-float on the FP32 pipe)",
-                "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": None,
-                "per_launch_ms": round(prof["legendre"], 4), "algorithmic_flops_per_launch": flops,
-                "evaluated_terms": evaluated, "full_triangle_terms": full,
-                "peak_source": "FP32 FMA rate measured by paper_1211_0585_gb300/probe/alu_peak.cu in this run"
-                if alu.get("fp32_tflops") else "recorded FP32 FMA probe value (probe unavailable)",
-                "fp64_pipe_tflops": alu.get("fp64_tflops"),
-                "kernel_ms": {k: round(v, 4) for k, v in prof.items()}}
+    held, per_pass = P.legendre_table(LMAX)
+    t_leg = prof["legendre"] * 1e-3
+    if held:
+        # the table form reads lambda from HBM in both passes: algorithmic bytes
+        # per launch = the table rows each pass needs, the ring-pair Fourier
+        # coefficients in (analysis) and out (synthesis, every m), the start
+        # rows read in both passes, and the a_lm state read and written
+        rp = 2 * NSIDE
+        nbytes = (2 * per_pass + (LMAX + 1) * rp * 32 * 2 + (LMAX + 1) * rp * 4 * 2 + P.nalm * 16 * 2)
+        hbm_peak, src = hbm_peak_gbs()
+        achieved = nbytes / t_leg / 1e9
+        roofline = {"bound": "hbm", "kernel": "legendre_df_kernel<LEG_ITER, table> (double-float lambda table)",
+                    "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                    "per_launch_ms": round(prof["legendre"], 4), "algorithmic_bytes_per_launch": nbytes,
+                    "table_bytes_held": held, "table_bytes_per_pass": per_pass,
+                    "evaluated_terms": evaluated, "full_triangle_terms": full, "peak_source": src,
+                    "kernel_ms": {k: round(v, 4) for k, v in prof.items()}}
+    else:
+        flops = 2.0 * LEGENDRE_DF_INSTR * evaluated
+        achieved = flops / t_leg / 1e12
+        roofline = {"bound": "alu", "kernel": "legendre_df_kernel<LEG_ITER> (double-float on the FP32 pipe)",
+                    "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                    "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                    "per_launch_ms": round(prof["legendre"], 4), "algorithmic_flops_per_launch": flops,
+                    "evaluated_terms": evaluated, "full_triangle_terms": full,
+                    "peak_source": "FP32 FMA rate measured by paper_1211_0585_gb300/probe/alu_peak.cu in this run"
+                    if alu.get("fp32_tflops") else "recorded FP32 FMA probe value (probe unavailable)",
+                    "fp64_pipe_tflops": alu.get("fp64_tflops"),
+                    "kernel_ms": {k: round(v, 4) for k, v in prof.items()}}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     d_host = torch.empty(prob.npix, dtype=torch.float64).pin_memory()
@@ -232,7 +251,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "npix": prob.npix, "tol": TOL,
-                   "precision": "fp64 (double-float Legendre and ring FFTs, double updates and reductions)",
+                   "precision": "fp64 (double-float Legendre and ring FFTs, double updates and reductions)"
+                   + ("; Legendre stage reads a precomputed double-float lambda table" if held else ""),
                    "iterations_per_solve": iters, "parallelism": f"replicas{world}",
                    "l2": "flushed (512 MiB write) between timed solves", "seed": args.seed},
         "sht_pair_ms": round(sht_pair_ms, 4),
@@ -337,6 +357,17 @@ def serving_run(seconds=8.0, rate=4.0, seed=3):
             "p50_ms": round(st["p50_ms"], 1), "p99_ms": round(st["p99_ms"], 1), "max_batch": 16,
             "shapes": "Nside 128/256/512, lmax 2 Nside", "tol_mix": "1e-5 mixed / 1e-8 FP64, half each",
             "note": "inputs generated before the stream starts (%.1f s)" % t_gen}
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this GPU type (MEASURED_PEAKS.json at the
+    repository root), else the recorded fallback."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured STREAM-style copy (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (no measured peak file)"
 
 
 def measure_alu_peaks():

@@ -88,6 +88,12 @@ typedef struct {
   int max_level_iters;   /* a level ends after this many iterations regardless (1000) */
   int graph_iters;       /* iterations captured per CUDA graph launch (16) */
   int batch_slots;       /* slots of the batched mixed-precision engine, 1 .. 64 (64) */
+  size_t legendre_table_bytes; /* WF_PREC_FP64 plans: hold lambda_lm(x_k) precomputed (double-float,
+                            8 bytes per (l, m, ring pair), ring pairs padded to a multiple of 32) when
+                            the table takes at most this many device
+                            bytes; the Legendre stage then reads it instead of running the recurrence.
+                            Decided at wf_plan_create; 0 = always the recurrence (8 GiB: Nside <= 512
+                            at lmax = 2 Nside) */
   void *stream;          /* cudaStream_t to run on; NULL = the plan's own stream */
 } wf_options;
 
@@ -143,6 +149,14 @@ wf_status wf_plan_info(wf_plan_t plan, int64_t *npix, int64_t *nalm, double *tau
  * with |lambda_lm| below 2^-60 are skipped), and the full count
  * (lsht+1)(lsht+2)/2 * 2 nside for comparison. Either out pointer may be NULL. */
 wf_status wf_plan_legendre_terms(wf_plan_t plan, int lsht, int64_t *evaluated, int64_t *full);
+
+/* The precomputed lambda table of a WF_PREC_FP64 plan (Sect. 2 Legendre stage):
+ * *held = its device bytes (0 when the plan runs the recurrence), *per_pass =
+ * the bytes of it that one Legendre pass (analysis or synthesis) at band limit
+ * lsht needs: for every m <= lsht and ring pair, the 16-byte rows of two l
+ * from the row holding the first term at or above the 2^-60 cut through the
+ * row holding lsht. Either out pointer may be NULL. */
+wf_status wf_plan_legendre_table(wf_plan_t plan, int lsht, int64_t *held, int64_t *per_pass);
 
 /* Kernel launches in one messenger iteration of the plan's single-solve path
  * (WF_PREC_FP64 or WF_PREC_FP64_NATIVE): the ring stage (one launch, or at

@@ -240,6 +240,10 @@ static wf_status build_geometry(Plan *P) {
   return WF_OK;
 }
 
+// dynamic shared memory the table form of the Legendre kernel may use (with its
+// static arrays within the 227 KB a CTA can have)
+constexpr size_t kTabSmemLimit = 220 * 1024;
+
 static wf_status build_legendre(Plan *P) {
   const int lmax = P->lmax;
   std::vector<double2> rec(alm_count(lmax));
@@ -269,6 +273,21 @@ static wf_status build_legendre(Plan *P) {
   WF_CUDA(cudaMemcpyAsync(P->d_rec, rec.data(), sizeof(double2) * rec.size(), cudaMemcpyHostToDevice, P->stream));
   launch_start_values(P->d_x, P->d_rec, lmax, P->RP, P->d_ls, P->d_sv, P->stream);
   launch_df_tables(P->d_x, P->d_rec, lmax, P->RP, P->d_dfg, P->d_dfA, P->d_dfls, P->d_dfsv, P->stream);
+  const size_t rows = lam_table_rows(lmax);
+  const size_t tab_bytes = rows * (size_t)((P->RP + 31) / 32 * 32) * sizeof(float4);  // tiles of 32 ring pairs
+  if (P->opt.precision == WF_PREC_FP64 && tab_bytes <= P->opt.legendre_table_bytes &&
+      leg_tab_smem(lmax, P->RP) <= kTabSmemLimit) {
+    std::vector<long long> poff(lmax + 1);
+    long long r = 0;
+    for (int m = 0; m <= lmax; ++m) { poff[m] = r; r += (lmax - m + 2) / 2; }
+    if ((st = P->dalloc((void **)&P->d_poff, sizeof(long long) * poff.size()))) return st;
+    if ((st = P->dalloc((void **)&P->d_tab, tab_bytes))) return st;
+    WF_CUDA(cudaMemcpyAsync(P->d_poff, poff.data(), sizeof(long long) * poff.size(), cudaMemcpyHostToDevice,
+                            P->stream));
+    if (P->RP % 32) WF_CUDA(cudaMemsetAsync(P->d_tab, 0, tab_bytes, P->stream));  // columns past RP
+    launch_lam_table(P->d_x, P->d_rec, P->d_ls, P->d_sv, P->d_dfls, P->d_poff, lmax, P->RP, P->d_tab, P->stream);
+    P->tab_bytes = tab_bytes;
+  }
   WF_CUDA(cudaStreamSynchronize(P->stream));
   WF_CUDA(cudaGetLastError());
   return WF_OK;
@@ -393,6 +412,7 @@ wf_status wf_options_default(wf_options *o) {
   o->max_level_iters = 1000;
   o->graph_iters = 16;
   o->batch_slots = kBatchMax;
+  o->legendre_table_bytes = (size_t)8 << 30;
   o->stream = nullptr;
   return WF_OK;
 }
@@ -516,6 +536,26 @@ wf_status wf_plan_legendre_terms(wf_plan_t plan, int lsht, int64_t *evaluated, i
     }
   if (evaluated) *evaluated = ev;
   if (full) *full = (int64_t)(lsht + 1) * (lsht + 2) / 2 * P->RP;
+  return WF_OK;
+}
+
+wf_status wf_plan_legendre_table(wf_plan_t plan, int lsht, int64_t *held, int64_t *per_pass) {
+  if (!plan) { set_error("wf_plan_legendre_table: NULL plan"); return WF_EINVAL; }
+  Plan *P = static_cast<Plan *>(plan);
+  if (lsht < 0 || lsht > P->lmax) { set_error("wf_plan_legendre_table: lsht out of range"); return WF_EINVAL; }
+  if (held) *held = (int64_t)P->tab_bytes;
+  if (per_pass) {
+    const size_t nmk = (size_t)(P->lmax + 1) * P->RP;
+    std::vector<int> ls(nmk);
+    WF_CUDA(cudaMemcpy(ls.data(), P->d_dfls, sizeof(int) * nmk, cudaMemcpyDeviceToHost));
+    int64_t rows = 0;
+    for (int m = 0; m <= lsht; ++m)
+      for (int k = 0; k < P->RP; ++k) {
+        const int l0 = ls[(size_t)m * P->RP + k];
+        if (l0 <= lsht) rows += (lsht - m) / 2 - (l0 - m) / 2 + 1;
+      }
+    *per_pass = rows * (int64_t)sizeof(float4);
+  }
   return WF_OK;
 }
 

@@ -23,6 +23,21 @@
 //
 // Terms with |lambda_lm(x)| < 2^-60 (the evanescent region near the poles) are
 // not evaluated; they lie below the 48-bit precision of any sum they enter.
+//
+// Table form (TAB): where the plan holds lambda_lm(x_k) precomputed (FP64
+// recurrence, stored as double-float), both passes read it instead of running
+// the recurrence, which turns the stage from FP32-issue-bound into HBM-bound:
+// 8 bytes per (l, m, ring pair) term and pass against 19 FP32 instructions of
+// the recurrence step. Layout: per m, rows of two consecutive l (l - m = 2r and
+// 2r + 1, the even and odd parity parts), each row RP float4 (lambda_{m+2r}
+// hi, lo, lambda_{m+2r+1} hi, lo) over the ring pairs, stored in tiles of 32
+// ring pairs: [m][tile of 32 ring pairs][row][32]. Entries below the 2^-60 cut
+// (and the columns past RP of a partial tile) are zero. The analysis gives each
+// warp groups of 4 rows, streamed over all tiles, so that a lane sums over ring
+// pairs with 4 compensated accumulators and the lanes of a row combine once per
+// row group (no block-wide reduction per block of l); the synthesis gives each
+// warp tiles (lane = ring pair) walked along the rows. Both keep the next loads
+// in flight in registers while they compute on the current ones.
 #include <cuda_runtime.h>
 
 #include "df.cuh"
@@ -32,6 +47,8 @@ namespace wfk {
 
 constexpr int kNoStartD = 1 << 30;
 constexpr int kAnaChunk = 1024;   // ring pairs whose analysis state is held in shared memory at once
+constexpr int kTabTiles = kAnaChunk / 32;  // table form: tiles of 32 ring pairs per analysis chunk
+constexpr int kWarps = kThreads / 32;
 
 __device__ __forceinline__ size_t alm_idx_d(int lmax, int l, int m) {
   return (size_t)m * (2 * lmax + 1 - m) / 2 + l;
@@ -154,11 +171,56 @@ __global__ void rescale_coeffs_kernel(const double2 *rec, int lmax, double *g, f
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs A, const LegDfArgs D) {
+// The table: one thread per (m, k) runs the FP64 recurrence from the start
+// values of the FP64 kernel and stores lambda as (hi, lo) from the first l of
+// the 2^-60 cut on, zeros below it.
+__global__ void lam_table_kernel(const double *xk, const double2 *rec, const int *ls64, const double2 *sv64,
+                                 const int *ls_df, const long long *poff, int lmax, int RP, float4 *tab) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)(lmax + 1) * RP) return;
+  const int m = (int)(id / RP), k = (int)(id % RP);
+  const int npr = (lmax - m + 2) / 2;
+  float4 *col = tab + ((size_t)poff[m] * ((RP + 31) >> 5) + (size_t)(k >> 5) * npr) * 32 + (k & 31);
+  const int l64 = ls64[id], ldf = ls_df[id];
+  const double x = xk[k];
+  const size_t base = alm_idx_d(lmax, m, m);
+  double p2 = 0.0, p1 = 0.0;  // lambda_{l-2}, lambda_{l-1}
+  dfl ev{0.f, 0.f};           // the row's even part
+  for (int l = m; l < m + 2 * npr; ++l) {
+    double lam = 0.0;
+    if (l <= lmax && l >= l64) {
+      if (l == l64) lam = sv64[id].x;
+      else if (l == l64 + 1) lam = sv64[id].y;
+      else {
+        const double2 ab = rec[base + (l - m)];
+        lam = ab.x * x * p1 - ab.y * p2;
+      }
+      p2 = p1;
+      p1 = lam;
+    }
+    const dfl d = (l >= ldf && l <= lmax) ? df_from(lam) : dfl{0.f, 0.f};
+    if (((l - m) & 1) == 0) ev = d;
+    else col[(size_t)((l - m) >> 1) * 32] = make_float4(ev.h, ev.l, d.h, d.l);
+  }
+}
+
+// (S, C) += the (S, C) of the lane `off` away (xor), error-free in S: the
+// compensated sum of two lanes' partial sums
+__device__ __forceinline__ void df_xor_sum(float &S, float &C, int off) {
+  const float rS = __shfl_xor_sync(0xffffffffu, S, off), rC = __shfl_xor_sync(0xffffffffu, C, off);
+  const float s = S + rS;
+  const float bb = s - S;
+  const float e = (S - (s - bb)) + (rS - bb);
+  S = s;
+  C = C + rC + e;
+}
+
+template <int MODE, bool TAB>
+__global__ void __launch_bounds__(kThreads, TAB ? 3 : 2) legendre_df_kernel(const LegArgs A, const LegDfArgs D) {
   extern __shared__ double2 dsm[];
   __shared__ double red[kThreads / 32][32];
   __shared__ double mred[kThreads / 32][3];
+  __shared__ int tab_tmin[kTabTiles];  // table form: first evaluated l of each tile of the chunk
   const int m = blockIdx.x;
   const int lmax = A.lmax, RP = A.RP;
   int L = A.lsht;
@@ -206,22 +268,97 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
   }
   const int Lm = L - m + 1;
   const int Lp = Lm + kLB;
-  // shared: tl [Lp] double2 | sA [Lp] float2 | ss [Lp] float4 (synthesis coefficients g_l s_lm)
+  // shared: tl [Lp] double2 | sA [Lp] float2 | ss [Lp] float4 (synthesis coefficients g_l s_lm);
+  // table form: tl | ss (no sA)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double2 *tl = dsm;
   float2 *sA = reinterpret_cast<float2 *>(dsm + Lp);
-  float4 *ss = reinterpret_cast<float4 *>(sA + Lp + (Lp & 1));
+  float4 *ss = TAB ? reinterpret_cast<float4 *>(dsm + Lp) : reinterpret_cast<float4 *>(sA + Lp + (Lp & 1));
   for (int i = threadIdx.x; i < Lp; i += blockDim.x) {
-    sA[i] = (i < Lm) ? D.A[base + i] : make_float2(0.f, 0.f);
+    if (!TAB) sA[i] = (i < Lm) ? D.A[base + i] : make_float2(0.f, 0.f);
     tl[i] = make_double2(0.0, 0.0);
   }
+  const int npr = (lmax - m + 2) >> 1;  // table form: rows of m
+  const int rlast = (L - m) >> 1;       // table form: last row needed
+  const float4 *tm = TAB ? D.tab + (size_t)D.poff[m] * ((RP + 31) >> 5) * 32 : nullptr;
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (MODE == LEG_ANALYSIS || MODE == LEG_ITER) {
     // per ring pair state in shared memory: the thread's sums then cover all of
     // its ring pairs of a chunk before one reduction per block of kLB values of
     // l; chunks of kAnaChunk ring pairs run one after another (one chunk up to
     // Nside 512), each adding its share to t_l
+    if (TAB) {
+      // lane (rho, sigma) = (lane / 8, lane % 8) sums row 4 rg + rho of the warp's row group
+      // over the columns sigma + 8 j of every tile
+      const int rho = lane >> 3, sig = lane & 7;
+      for (int k0 = 0; k0 < RP; k0 += kAnaChunk) {
+        const int nk = min(kAnaChunk, RP - k0);
+        const int ntile = (nk + 31) >> 5;
+        float4 *stE = ss, *stO = ss + nk;
+        for (int kk = threadIdx.x; kk < nk; kk += blockDim.x) {
+          const double4_32a t = A.FT[(size_t)m * RP + k0 + kk];
+          const dfl er = df_from(t.x + t.z), ei = df_from(t.y + t.w);
+          const dfl orr = df_from(t.x - t.z), oi = df_from(t.y - t.w);
+          stE[kk] = make_float4(er.h, er.l, ei.h, ei.l);
+          stO[kk] = make_float4(orr.h, orr.l, oi.h, oi.l);
+        }
+        for (int t = warp; t < ntile; t += kWarps) {
+          const int kk = 32 * t + lane;
+          const int mn = __reduce_min_sync(0xffffffffu, kk < nk ? D.ls[(size_t)m * RP + k0 + kk] : kNoStartD);
+          if (lane == 0) tab_tmin[t] = mn;
+        }
+        __syncthreads();
+        const float4 *tc0 = tm + (size_t)(k0 >> 5) * npr * 32;  // the chunk's first tile
+        for (int rg = warp; 4 * rg <= rlast; rg += kWarps) {
+          const int r = 4 * rg + rho;
+          const int lhi = m + 8 * rg + 7;  // last l of the row group
+          auto next_tile = [&](int t) {    // the next tile holding a term of the row group
+            while (t < ntile && tab_tmin[t] > lhi) ++t;
+            return t;
+          };
+          auto load = [&](int t, float4 (&v)[4]) {
+            const float4 *src = tc0 + ((size_t)t * npr + r) * 32 + sig;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = (r <= rlast) ? __ldcs(src + 8 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+          };
+          float aS[4] = {0.f, 0.f, 0.f, 0.f}, aC[4] = {0.f, 0.f, 0.f, 0.f};
+          float4 cur[4], nxt[4];
+          int t = next_tile(0);
+          if (t < ntile) load(t, cur);
+          while (t < ntile) {
+            const int tn = next_tile(t + 1);
+            if (tn < ntile) load(tn, nxt);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int kk = 32 * t + sig + 8 * j;
+              if (kk < nk) {
+                const float4 e4 = stE[kk], o4 = stO[kk];
+                const dfl le{cur[j].x, cur[j].y}, lo{cur[j].z, cur[j].w};
+                dot2_acc(aS[0], aC[0], le, dfl{e4.x, e4.y});
+                dot2_acc(aS[1], aC[1], le, dfl{e4.z, e4.w});
+                dot2_acc(aS[2], aC[2], lo, dfl{o4.x, o4.y});
+                dot2_acc(aS[3], aC[3], lo, dfl{o4.z, o4.w});
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
+            t = tn;
+          }
+#pragma unroll
+          for (int off = 1; off < 8; off <<= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) df_xor_sum(aS[q], aC[q], off);
+          if (sig == 0 && r <= rlast) {  // l = m + 2 r (even part) and m + 2 r + 1 (odd part)
+            tl[2 * r].x += (double)aS[0] + (double)aC[0];
+            tl[2 * r].y += (double)aS[1] + (double)aC[1];
+            tl[2 * r + 1].x += (double)aS[2] + (double)aC[2];
+            tl[2 * r + 1].y += (double)aS[3] + (double)aC[3];
+          }
+        }
+        __syncthreads();
+      }
+    } else
     for (int k0 = 0; k0 < RP; k0 += kAnaChunk) {
       const int nk = min(kAnaChunk, RP - k0);
       float4 *stE = ss;                            // (Er, Ei) as hi/lo
@@ -275,8 +412,8 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
         __syncthreads();
       }
     }
-    // undo the rescaling: lambda = g mu
-    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+    // undo the rescaling: lambda = g mu (the table holds lambda itself)
+    for (int l = m + threadIdx.x; l <= L && !TAB; l += blockDim.x) {
       const double gl = D.g[base + (l - m)];
       tl[l - m].x *= gl;
       tl[l - m].y *= gl;
@@ -309,11 +446,12 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
       nrm += wgt * (sn.x * sn.x + sn.y * sn.y);
       A.alm[base + (l - m)] = sn;
       if (l <= L) {
-        const double gl = D.g[base + (l - m)];
+        const double gl = TAB ? 1.0 : D.g[base + (l - m)];
         const dfl re = df_from(gl * sn.x), im = df_from(gl * sn.y);
         ss[l - m] = make_float4(re.h, re.l, im.h, im.l);
       }
     }
+    if (TAB && threadIdx.x < 2) ss[Lm + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int o = 16; o > 0; o >>= 1) {
       c2 += __shfl_xor_sync(0xffffffffu, c2, o);
       inc += __shfl_xor_sync(0xffffffffu, inc, o);
@@ -329,8 +467,9 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
       A.m_part[3 * m + 2] = c;
     }
   } else {  // LEG_SYNTH
+    if (TAB && threadIdx.x < 2) ss[Lm + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
-      const double gl = D.g[base + (l - m)];
+      const double gl = TAB ? 1.0 : D.g[base + (l - m)];
       const double2 s = A.alm_in[base + (l - m)];
       const dfl re = df_from(gl * s.x), im = df_from(gl * s.y);
       ss[l - m] = make_float4(re.h, re.l, im.h, im.l);
@@ -339,58 +478,101 @@ __global__ void __launch_bounds__(kThreads, 2) legendre_df_kernel(const LegArgs 
   }
 
   // ---- synthesis onto every ring pair (one ring pair per thread at a time)
-  for (int k = threadIdx.x; k < RP; k += blockDim.x) {
-    const size_t mk = (size_t)m * RP + k;
-    const int ls = D.ls[mk];
-    float ERs = 0.f, ERc = 0.f, EIs = 0.f, EIc = 0.f, ORs = 0.f, ORc = 0.f, OIs = 0.f, OIc = 0.f;
-    if (ls <= L) {
-      const dfl x = df_from(A.x[k]);
-      const float4 s4 = D.sv[mk];
-      dfl p2 = dfl{s4.x, s4.y};
-      dfl p1 = dfl{s4.z, s4.w};
-      int l = ls;
-      {
-        const float4 c = ss[l - m];
-        if (((l - m) & 1) == 0) { dot2_acc(ERs, ERc, p2, dfl{c.x, c.y}); dot2_acc(EIs, EIc, p2, dfl{c.z, c.w}); }
-        else { dot2_acc(ORs, ORc, p2, dfl{c.x, c.y}); dot2_acc(OIs, OIc, p2, dfl{c.z, c.w}); }
+  if constexpr (TAB) {
+    // each warp takes tiles of 32 ring pairs (lane = ring pair) and walks the rows
+    // from the first any of them needs; rows below a ring pair's cut hold zeros
+    for (int cg = warp; 32 * cg < RP; cg += kWarps) {
+      const int k = 32 * cg + lane;
+      const int lw = __reduce_min_sync(0xffffffffu, k < RP ? D.ls[(size_t)m * RP + k] : kNoStartD);
+      float ERs = 0.f, ERc = 0.f, EIs = 0.f, EIc = 0.f, ORs = 0.f, ORc = 0.f, OIs = 0.f, OIc = 0.f;
+      if (lw <= L) {
+        const float4 *src = tm + (size_t)cg * npr * 32 + lane;
+        auto load = [&](int r, float4 (&v)[4]) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            v[i] = (r + i <= rlast) ? __ldcs(src + (size_t)(r + i) * 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        float4 cur[4], nxt[4];
+        int r = (lw - m) >> 1;
+        load(r, cur);
+        for (; r <= rlast; r += 4) {
+          if (r + 4 <= rlast) load(r + 4, nxt);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (r + i <= rlast) {
+              const float4 ce = ss[2 * (r + i)], co = ss[2 * (r + i) + 1];
+              const dfl le{cur[i].x, cur[i].y}, lo{cur[i].z, cur[i].w};
+              dot2_acc(ERs, ERc, le, dfl{ce.x, ce.y});
+              dot2_acc(EIs, EIc, le, dfl{ce.z, ce.w});
+              dot2_acc(ORs, ORc, lo, dfl{co.x, co.y});
+              dot2_acc(OIs, OIc, lo, dfl{co.z, co.w});
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
+        }
       }
-      if (l + 1 <= L) {
-        const float4 c = ss[l + 1 - m];
-        if (((l + 1 - m) & 1) == 0) { dot2_acc(ERs, ERc, p1, dfl{c.x, c.y}); dot2_acc(EIs, EIc, p1, dfl{c.z, c.w}); }
-        else { dot2_acc(ORs, ORc, p1, dfl{c.x, c.y}); dot2_acc(OIs, OIc, p1, dfl{c.z, c.w}); }
-      }
-      l += 2;
-      if (((l - m) & 1) == 1 && l <= L) {
-        const float2 a2 = sA[l - m];
-        const dfl mu = df_step(dfl{a2.x, a2.y}, x, p1, p2);
-        p2 = p1; p1 = mu;
-        const float4 c = ss[l - m];
-        dot2_acc(ORs, ORc, mu, dfl{c.x, c.y});
-        dot2_acc(OIs, OIc, mu, dfl{c.z, c.w});
-        ++l;
-      }
-      for (; l + 1 <= L; l += 2) {
-        const float2 a0 = sA[l - m], a1 = sA[l + 1 - m];
-        const dfl me = df_step(dfl{a0.x, a0.y}, x, p1, p2);
-        const dfl mo = df_step(dfl{a1.x, a1.y}, x, me, p1);
-        p2 = me; p1 = mo;
-        const float4 ce = ss[l - m], co = ss[l + 1 - m];
-        dot2_acc(ERs, ERc, me, dfl{ce.x, ce.y});
-        dot2_acc(EIs, EIc, me, dfl{ce.z, ce.w});
-        dot2_acc(ORs, ORc, mo, dfl{co.x, co.y});
-        dot2_acc(OIs, OIc, mo, dfl{co.z, co.w});
-      }
-      if (l <= L) {
-        const float2 a0 = sA[l - m];
-        const dfl me = df_step(dfl{a0.x, a0.y}, x, p1, p2);
-        const float4 ce = ss[l - m];
-        dot2_acc(ERs, ERc, me, dfl{ce.x, ce.y});
-        dot2_acc(EIs, EIc, me, dfl{ce.z, ce.w});
+      if (k < RP) {
+        const double er = (double)ERs + (double)ERc, ei = (double)EIs + (double)EIc;
+        const double orr = (double)ORs + (double)ORc, oi = (double)OIs + (double)OIc;
+        A.FS[(size_t)m * RP + k] = make_double4_32a(er + orr, ei + oi, er - orr, ei - oi);
       }
     }
-    const double er = (double)ERs + (double)ERc, ei = (double)EIs + (double)EIc;
-    const double orr = (double)ORs + (double)ORc, oi = (double)OIs + (double)OIc;
-    A.FS[mk] = make_double4_32a(er + orr, ei + oi, er - orr, ei - oi);
+    return;
+  } else {
+    for (int k = threadIdx.x; k < RP; k += blockDim.x) {
+      const size_t mk = (size_t)m * RP + k;
+      const int ls = D.ls[mk];
+      float ERs = 0.f, ERc = 0.f, EIs = 0.f, EIc = 0.f, ORs = 0.f, ORc = 0.f, OIs = 0.f, OIc = 0.f;
+      if (ls <= L) {
+        const dfl x = df_from(A.x[k]);
+        const float4 s4 = D.sv[mk];
+        dfl p2 = dfl{s4.x, s4.y};
+        dfl p1 = dfl{s4.z, s4.w};
+        int l = ls;
+        {
+          const float4 c = ss[l - m];
+          if (((l - m) & 1) == 0) { dot2_acc(ERs, ERc, p2, dfl{c.x, c.y}); dot2_acc(EIs, EIc, p2, dfl{c.z, c.w}); }
+          else { dot2_acc(ORs, ORc, p2, dfl{c.x, c.y}); dot2_acc(OIs, OIc, p2, dfl{c.z, c.w}); }
+        }
+        if (l + 1 <= L) {
+          const float4 c = ss[l + 1 - m];
+          if (((l + 1 - m) & 1) == 0) { dot2_acc(ERs, ERc, p1, dfl{c.x, c.y}); dot2_acc(EIs, EIc, p1, dfl{c.z, c.w}); }
+          else { dot2_acc(ORs, ORc, p1, dfl{c.x, c.y}); dot2_acc(OIs, OIc, p1, dfl{c.z, c.w}); }
+        }
+        l += 2;
+        if (((l - m) & 1) == 1 && l <= L) {
+          const float2 a2 = sA[l - m];
+          const dfl mu = df_step(dfl{a2.x, a2.y}, x, p1, p2);
+          p2 = p1; p1 = mu;
+          const float4 c = ss[l - m];
+          dot2_acc(ORs, ORc, mu, dfl{c.x, c.y});
+          dot2_acc(OIs, OIc, mu, dfl{c.z, c.w});
+          ++l;
+        }
+        for (; l + 1 <= L; l += 2) {
+          const float2 a0 = sA[l - m], a1 = sA[l + 1 - m];
+          const dfl me = df_step(dfl{a0.x, a0.y}, x, p1, p2);
+          const dfl mo = df_step(dfl{a1.x, a1.y}, x, me, p1);
+          p2 = me; p1 = mo;
+          const float4 ce = ss[l - m], co = ss[l + 1 - m];
+          dot2_acc(ERs, ERc, me, dfl{ce.x, ce.y});
+          dot2_acc(EIs, EIc, me, dfl{ce.z, ce.w});
+          dot2_acc(ORs, ORc, mo, dfl{co.x, co.y});
+          dot2_acc(OIs, OIc, mo, dfl{co.z, co.w});
+        }
+        if (l <= L) {
+          const float2 a0 = sA[l - m];
+          const dfl me = df_step(dfl{a0.x, a0.y}, x, p1, p2);
+          const float4 ce = ss[l - m];
+          dot2_acc(ERs, ERc, me, dfl{ce.x, ce.y});
+          dot2_acc(EIs, EIc, me, dfl{ce.z, ce.w});
+        }
+      }
+      const double er = (double)ERs + (double)ERc, ei = (double)EIs + (double)EIc;
+      const double orr = (double)ORs + (double)ORc, oi = (double)OIs + (double)OIc;
+      A.FS[mk] = make_double4_32a(er + orr, ei + oi, er - orr, ei - oi);
+    }
   }
 }
 
@@ -404,23 +586,48 @@ static size_t leg_df_smem(int lmax, int RP) {
   return Lp * sizeof(double2) + (Lp + 1) * sizeof(float2) + q * sizeof(float4) + 16;
 }
 
-void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode) {
-  const size_t sm = leg_df_smem(a.lmax, a.RP);
-  const int grid = a.lmax + 1;
+// table form: tl [Lp] double2 | max(Lp, 2 chunk) float4
+size_t leg_tab_smem(int lmax, int RP) {
+  const size_t Lp = (size_t)lmax + 1 + kLB;
+  const size_t nk = RP < kAnaChunk ? (size_t)RP : (size_t)kAnaChunk;
+  const size_t q = Lp > 2 * nk ? Lp : 2 * nk;
+  return Lp * sizeof(double2) + q * sizeof(float4);
+}
+
+template <bool TAB>
+static void launch_leg_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode, size_t sm, int grid) {
   switch (mode) {
     case LEG_SYNTH:
-      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_SYNTH>));
-      legendre_df_kernel<LEG_SYNTH><<<grid, kThreads, sm, s>>>(a, d);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_SYNTH, TAB>));
+      legendre_df_kernel<LEG_SYNTH, TAB><<<grid, kThreads, sm, s>>>(a, d);
       break;
     case LEG_ANALYSIS:
-      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_ANALYSIS>));
-      legendre_df_kernel<LEG_ANALYSIS><<<grid, kThreads, sm, s>>>(a, d);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_ANALYSIS, TAB>));
+      legendre_df_kernel<LEG_ANALYSIS, TAB><<<grid, kThreads, sm, s>>>(a, d);
       break;
     default:
-      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_ITER>));
-      legendre_df_kernel<LEG_ITER><<<grid, kThreads, sm, s>>>(a, d);
+      raise_smem_cap(reinterpret_cast<const void *>(legendre_df_kernel<LEG_ITER, TAB>));
+      legendre_df_kernel<LEG_ITER, TAB><<<grid, kThreads, sm, s>>>(a, d);
       break;
   }
+}
+
+void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode) {
+  const int grid = a.lmax + 1;
+  if (d.tab) launch_leg_df<true>(a, d, s, mode, leg_tab_smem(a.lmax, a.RP), grid);
+  else launch_leg_df<false>(a, d, s, mode, leg_df_smem(a.lmax, a.RP), grid);
+}
+
+size_t lam_table_rows(int lmax) {
+  size_t rows = 0;
+  for (int m = 0; m <= lmax; ++m) rows += (size_t)(lmax - m + 2) / 2;
+  return rows;
+}
+
+void launch_lam_table(const double *x, const double2 *rec, const int *ls64, const double2 *sv64, const int *ls_df,
+                      const long long *poff, int lmax, int RP, float4 *tab, cudaStream_t s) {
+  const long long n = (long long)(lmax + 1) * RP;
+  lam_table_kernel<<<(int)((n + 127) / 128), 128, 0, s>>>(x, rec, ls64, sv64, ls_df, poff, lmax, RP, tab);
 }
 
 void launch_df_tables(const double *x, const double2 *rec, int lmax, int RP, double *g, float2 *A, int *ls,

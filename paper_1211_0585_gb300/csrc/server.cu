@@ -137,6 +137,15 @@ Ctl request_ctl(const Plan *shape, const Request &r) {
   return c;
 }
 
+// an FP64 plan: the shape's tables and state, plus the precomputed lambda table
+// when it is within the default limit
+size_t fp64_bytes(int nside, int lmax) {
+  wf_options o;
+  wf_options_default(&o);
+  const size_t tab = lam_table_rows(lmax) * (size_t)((2 * nside + 31) / 32 * 32) * 16;
+  return engine_bytes(nside, lmax, 1) + (tab <= o.legendre_table_bytes ? tab : 0);
+}
+
 size_t bytes_in_use(wf_server_s *S) {
   size_t b = S->fp64_bytes_in_use;
   for (auto &kv : S->runners) b += kv.second->bytes;
@@ -266,7 +275,7 @@ void fp64_loop(wf_server_s *S) {
       if (S->stop) return;
       if (S->fp64_queue.empty()) continue;
       r = S->fp64_queue.front();
-      const size_t need = engine_bytes(r->nside, r->lmax, 1);
+      const size_t need = fp64_bytes(r->nside, r->lmax);
       if (S->fp64_bytes_in_use + need > S->budget) continue;  // wait for room
       S->fp64_queue.pop_front();
       S->fp64_bytes_in_use += need;

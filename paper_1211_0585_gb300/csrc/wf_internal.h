@@ -130,6 +130,8 @@ struct LegDfArgs {
   const double *g;        // [nalm] rescaling factor g_l (lambda = g mu)
   const int *ls;          // [(lmax+1) RP] first evaluated l (|lambda| >= 2^-60)
   const float4 *sv;       // [(lmax+1) RP] mu_{ls} (hi, lo), mu_{ls+1} (hi, lo)
+  const float4 *tab;      // precomputed lambda (hi, lo) in rows of two l, or nullptr (recurrence)
+  const long long *poff;  // [lmax+1] first table row of each m
 };
 
 // Double-float copies of the ring-stage tables (ring_df.cu): float4 =
@@ -205,6 +207,13 @@ void ring_classes(const RingDev *rings, int R, std::vector<int> &order, std::vec
 void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s);
 void launch_legendre(const LegArgs &a, cudaStream_t s, int mode);
 void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode);
+// rows of the precomputed double-float lambda table (sum over m of ceil((lmax - m + 1) / 2)),
+// each RP float4
+size_t lam_table_rows(int lmax);
+// dynamic shared memory of the table form of the Legendre kernel
+size_t leg_tab_smem(int lmax, int RP);
+void launch_lam_table(const double *x, const double2 *rec, const int *ls64, const double2 *sv64, const int *ls_df,
+                      const long long *poff, int lmax, int RP, float4 *tab, cudaStream_t s);
 void launch_df_tables(const double *x, const double2 *rec, int lmax, int RP, double *g, float2 *A, int *ls,
                       float4 *sv, cudaStream_t s);
 void launch_start_values(const double *x, const double2 *rec, int lmax, int RP, int *ls,

@@ -48,6 +48,9 @@ struct Plan : wf_plan_s {
   double *d_dfg = nullptr;
   int *d_dfls = nullptr;
   float4 *d_dfsv = nullptr;
+  float4 *d_tab = nullptr;              // precomputed lambda (FP64 path, when it fits opt.legendre_table_bytes)
+  long long *d_poff = nullptr;
+  size_t tab_bytes = 0;
   // working state
   double4_32a *d_FS = nullptr, *d_FT = nullptr;
   double *d_ring_part = nullptr, *d_m_part = nullptr;
@@ -70,7 +73,7 @@ struct Plan : wf_plan_s {
   cudaStream_t run_stream() const;
   RingArgs ring_args() const;
   LegArgs leg_args() const;
-  LegDfArgs legdf_args() const { return LegDfArgs{d_dfA, d_dfg, d_dfls, d_dfsv}; }
+  LegDfArgs legdf_args() const { return LegDfArgs{d_dfA, d_dfg, d_dfls, d_dfsv, d_tab, d_poff}; }
   RingDfArgs ringdf_args() const { return RingDfArgs{d_twf, d_hsf, d_chf, d_Bf}; }
   // the ring stage of the plan's precision
   void launch_rng(const RingArgs &a, cudaStream_t s, int mode) const {

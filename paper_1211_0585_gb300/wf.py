@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "W
                 5: "WF_ENUMERIC", 6: "WF_ETIMEOUT", 7: "WF_EBUSY", 8: "WF_ECANCELLED", 9: "WF_ENOTFOUND"}
 
 EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_info", "wf_plan_legendre_terms",
-            "wf_plan_kernels_per_iteration", "wf_plan_set_options",
+            "wf_plan_legendre_table", "wf_plan_kernels_per_iteration", "wf_plan_set_options",
             "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
             "wf_solve_history", "wf_solve_batch",
             "wf_server_create", "wf_submit", "wf_poll", "wf_server_drain", "wf_server_stats",
@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("band_limit", ctypes.c_int), ("plateau_eps", ctypes.c_double),
                 ("final_dchi2", ctypes.c_double), ("min_level_iters", ctypes.c_int),
                 ("max_level_iters", ctypes.c_int), ("graph_iters", ctypes.c_int),
-                ("batch_slots", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("batch_slots", ctypes.c_int), ("legendre_table_bytes", ctypes.c_size_t),
+                ("stream", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t)],
         "wf_plan_set_options": [_vp, ctypes.POINTER(Options)],
         "wf_plan_legendre_terms": [_vp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+        "wf_plan_legendre_table": [_vp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
         "wf_plan_kernels_per_iteration": [_vp, ctypes.POINTER(_i)],
         "wf_alm2map": [_vp, _i, _vp, _vp],
         "wf_map2alm": [_vp, _i, _vp, _vp],
@@ -194,6 +196,12 @@ class Plan:
         ev, full = ctypes.c_int64(), ctypes.c_int64()
         _check(load().wf_plan_legendre_terms(self.handle, lsht, ctypes.byref(ev), ctypes.byref(full)))
         return ev.value, full.value
+
+    def legendre_table(self, lsht):
+        """(held, per_pass) bytes of the precomputed lambda table (0 held: recurrence)."""
+        held, per_pass = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().wf_plan_legendre_table(self.handle, lsht, ctypes.byref(held), ctypes.byref(per_pass)))
+        return held.value, per_pass.value
 
     def kernels_per_iteration(self):
         n = _i()

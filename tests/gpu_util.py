@@ -6,6 +6,16 @@ from oracle import oracle as O
 from paper_1211_0585_gb300 import inputs as I
 
 
+# The FP64-accurate paths: the double-float Legendre stage reading the
+# precomputed lambda table (the default where it fits), the same stage running
+# the recurrence, and every step in native FP64.
+FP64_PATHS = {
+    "fp64-table": dict(precision=0),
+    "fp64-recurrence": dict(precision=0, legendre_table_bytes=0),
+    "fp64-native": dict(precision=2),
+}
+
+
 def dev(a):
     import torch
     a = np.ascontiguousarray(a)

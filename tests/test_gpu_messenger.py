@@ -11,7 +11,7 @@ import pytest
 from oracle import oracle as O
 from paper_1211_0585_gb300 import wf
 
-from gpu_util import dev, host_alm, problem
+from gpu_util import FP64_PATHS, dev, host_alm, problem
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,7 @@ def run_oracle_schedule(p, d, schedule):
     return res, states
 
 
-PRECS = [wf.WF_PREC_FP64, wf.WF_PREC_FP64_NATIVE]
+PRECS = list(FP64_PATHS)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -40,7 +40,7 @@ def test_iterates_match(kind, nside, lmax, lam, lsht, n, prec):
     import torch
     p, d = problem(kind, seed=2, nside=nside, lmax=lmax)
     res, states = run_oracle_schedule(p, d, [(lam, lsht, n)])
-    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(precision=prec))
+    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(**FP64_PATHS[prec]))
     dd = dev(d)
     s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
     for k in range(n):
@@ -59,7 +59,7 @@ def test_config1_two_hundred_iterations(prec):
     import torch
     p, d = problem("small", seed=1)
     res, _ = run_oracle_schedule(p, d, [(1.0, 32, 200)])
-    P = wf.Plan(16, 32, p.cl, p.noise_var, p.mask, wf.options(precision=prec))
+    P = wf.Plan(16, 32, p.cl, p.noise_var, p.mask, wf.options(**FP64_PATHS[prec]))
     s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
     recs = P.iterate(dev(d).data_ptr(), s.data_ptr(), 1.0, 32, 200, reset=True)
     assert O.rel_l2(host_alm(s), res.alm, 32) < TOL
@@ -115,7 +115,7 @@ def test_full_size_first_iteration_nside512(prec):
     p = I.wmap_problem(seed=1, nside=nside, lmax=lmax)
     rng = np.random.default_rng(7)
     d = rng.standard_normal(p.npix) * np.sqrt(p.noise_var) + 50.0 * np.cos(3 * np.arange(p.npix) / p.npix)
-    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(precision=prec))
+    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(**FP64_PATHS[prec]))
     lam = 4.0
     s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
     recs = P.iterate(dev(d).data_ptr(), s.data_ptr(), lam, lmax, 1, reset=True)

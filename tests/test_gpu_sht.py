@@ -7,18 +7,18 @@ from oracle import oracle as O
 from paper_1211_0585_gb300 import inputs as I
 from paper_1211_0585_gb300 import wf
 
-from gpu_util import dev, host_alm
+from gpu_util import FP64_PATHS, dev, host_alm
 
 pytestmark = pytest.mark.gpu
 
 CASES = [(1, 2), (2, 6), (4, 8), (4, 13), (8, 16), (16, 32), (16, 64), (32, 64), (64, 128), (64, 40)]
 
 
-PRECS = [wf.WF_PREC_FP64, wf.WF_PREC_FP64_NATIVE]
+PRECS = list(FP64_PATHS)
 
 
-def plan_for(nside, lmax, prec=wf.WF_PREC_FP64):
-    return wf.Plan(nside, lmax, np.ones(lmax + 1), np.ones(12 * nside * nside), opts=wf.options(precision=prec))
+def plan_for(nside, lmax, prec="fp64-table"):
+    return wf.Plan(nside, lmax, np.ones(lmax + 1), np.ones(12 * nside * nside), opts=wf.options(**FP64_PATHS[prec]))
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -52,14 +52,15 @@ def test_map2alm(nside, lmax, prec):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("nside,lmax,lsht", [(16, 48, 20), (32, 64, 0), (32, 64, 5)])
-def test_band_limited(nside, lmax, lsht):
+@pytest.mark.parametrize("prec", ["fp64-table", "fp64-recurrence"])
+@pytest.mark.parametrize("nside,lmax,lsht", [(16, 48, 20), (32, 64, 0), (32, 64, 5), (32, 64, 63)])
+def test_band_limited(nside, lmax, lsht, prec):
     """With band limit lsht only l <= lsht take part; analysis zeroes the rest."""
     import torch
     rng = np.random.default_rng(3)
     alm = I.draw_alm(np.ones(lmax + 1), rng)
     ref = O.alm2map(nside, lsht, O.truncate_alm(alm, lmax, lsht))
-    P = plan_for(nside, lmax)
+    P = plan_for(nside, lmax, prec)
     m = torch.empty(12 * nside * nside, dtype=torch.float64, device="cuda")
     P.alm2map(lsht, dev(alm).data_ptr(), m.data_ptr())
     f = rng.standard_normal(12 * nside * nside)
@@ -101,7 +102,7 @@ def test_sampled_full_size_nside512(prec):
     assert np.max(np.abs(got - refa)) <= 1e-11 * np.max(np.abs(host_alm(a)))
 
 
-@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("prec", ["fp64-recurrence", "fp64-native"])
 def test_sampled_full_size_nside2048(prec):
     """At the Planck-shaped size (Nside 2048, lmax 4096), where the polar rings
     with Bluestein buffers of 16384 points run their FFTs in global scratch and
@@ -136,3 +137,24 @@ def test_sampled_full_size_nside2048(prec):
     refa = O.map2alm_modes(nside, lmax, f, ls, ms)
     got = host_alm(a)[O.alm_index(lmax, ls, ms)]
     assert np.max(np.abs(got - refa)) <= 1e-10 * np.max(np.abs(host_alm(a)))
+
+
+def test_lambda_table_held_where_it_fits():
+    """The FP64 plan holds the precomputed lambda table when it fits the
+    option's limit (Nside 512 / lmax 1024: 4.3 GB), not at a limit of 0, not
+    for other precisions; one pass needs less of it than it holds (the rows
+    below the 2^-60 cut are never read)."""
+    ones = lambda n: np.ones(n)
+    nside, lmax = 512, 1024
+    P = wf.Plan(nside, lmax, ones(lmax + 1), ones(12 * nside * nside), opts=wf.options(precision=0))
+    held, per_pass = P.legendre_table(lmax)
+    rows = sum((lmax - m + 2) // 2 for m in range(lmax + 1))
+    assert held == rows * 2 * nside * 16  # 2 nside ring pairs: a multiple of 32
+    ev, full = P.legendre_terms(lmax)
+    assert ev * 8 <= per_pass < held
+    _, per_pass_low = P.legendre_table(100)
+    assert per_pass_low < per_pass
+    del P
+    for o in (dict(precision=0, legendre_table_bytes=0), dict(precision=2), dict(precision=1)):
+        Q = wf.Plan(64, 128, ones(129), ones(12 * 64 * 64), opts=wf.options(**o))
+        assert Q.legendre_table(128)[0] == 0
