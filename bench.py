@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-mixed and serving measurements")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--profile-fp64", type=int, nargs=3, metavar=("NSIDE", "LMAX", "ITERS"), default=None,
+                    help="profiling target: ITERS full-band FP64 iterations (wf_profile_iterations) of a "
+                         "WMAP-shaped problem at NSIDE / LMAX, the plan's default Legendre form")
     ap.add_argument("--profile-batch", type=int, nargs=2, metavar=("NRHS", "ITERS"), default=None,
                     help="profiling target: ITERS full-band iterations of the batched engine on NRHS right-hand "
                          "sides of the WMAP-shaped problem (cooling off), one text line, no JSON")
@@ -111,6 +114,10 @@ def make_problem(seed):
 
 
 LEGENDRE_DF_INSTR = 90    # FP32 instructions per evaluated (l, m, ring pair) term, both passes
+# DRAM bytes (read + write) per algorithmic byte of legendre_df_kernel<LEG_ITER, table>: 885.0 MB
+# measured by ncu for one launch of `bench.py --profile-fp64 256 512 4` against 864.0 MB algorithmic
+# (profiles/legendre_df_kernel_table_nside256_lmax512.md); the full-size launch is scaled by it
+TABLE_TRAFFIC_RATIO = 885.04e6 / 864049664
 
 
 def run_ours(args):
@@ -212,7 +219,9 @@ def run_ours(args):
         achieved = nbytes / t_leg / 1e9
         roofline = {"bound": "hbm", "kernel": "legendre_df_kernel<LEG_ITER, table> (double-float lambda table)",
                     "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                    "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                    "frac": round(achieved / hbm_peak, 4), "traffic": int(TABLE_TRAFFIC_RATIO * nbytes),
+                    "traffic_source": "ncu DRAM bytes of the same kernel at Nside 256 / lmax 512, scaled by "
+                                      "the algorithmic bytes",
                     "per_launch_ms": round(prof["legendre"], 4), "algorithmic_bytes_per_launch": nbytes,
                     "table_bytes_held": held, "table_bytes_per_pass": per_pass,
                     "evaluated_terms": evaluated, "full_triangle_terms": full, "peak_source": src,
@@ -487,8 +496,29 @@ def profile_batch(nrhs, iters, seed):
           f"({1e3 * dt / iters:.2f} ms / iteration, status {status})", flush=True)
 
 
+def profile_fp64(nside, lmax, iters, seed):
+    """A fixed amount of full-band FP64 work for ncu captures (lambda = 1,
+    lmax_SHT = lmax): one synthesis launch, then per iteration the ring,
+    Legendre and controller launches."""
+    import torch
+    from paper_1211_0585_gb300 import inputs as I
+    from paper_1211_0585_gb300 import wf
+    prob = I.wmap_problem(seed=seed, nside=nside, lmax=lmax)
+    P = wf.Plan(nside, lmax, prob.cl, prob.noise_var, prob.mask, wf.options())
+    d = torch.from_numpy(prob.data(np.zeros(prob.npix))).cuda()
+    s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
+    held, per_pass = P.legendre_table(lmax)
+    ms = P.profile(d.data_ptr(), s.data_ptr(), 1.0, lmax, iters)
+    print(f"full-band FP64 at Nside {nside} / lmax {lmax}: {iters} iterations, ms per launch "
+          f"{ {k: round(v, 4) for k, v in ms.items()} }, lambda table held {held} B, {per_pass} B per pass",
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_fp64:
+        profile_fp64(*args.profile_fp64, args.seed)
+        return
     if args.profile_batch:
         profile_batch(args.profile_batch[0], args.profile_batch[1], args.seed)
         return
