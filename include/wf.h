@@ -252,6 +252,15 @@ wf_status wf_submit(wf_server_t server, int nside, int lmax, const double *cl,
  * done; WF_ENOTFOUND for an unknown or already collected ticket. */
 wf_status wf_poll(wf_server_t server, uint64_t ticket, int *done, double *alm_out, wf_stats *stats);
 
+/* Make a shape resident before its requests arrive, as a serving system loads
+ * its models: precision WF_PREC_MIXED builds the shape's batched engine
+ * (tables, FP32 Lambda tables, autotuned ring tiles) on the server's worker,
+ * WF_PREC_FP64 adds one idle FP64 plan of the shape (geometry, Legendre and
+ * lambda tables) to the pool its FP64 requests run on. Blocks until done.
+ * WF_ENOMEM when the shape does not fit the budget now; WF_EINVAL for a bad
+ * shape or precision. */
+wf_status wf_server_warm(wf_server_t server, int nside, int lmax, int precision);
+
 /* Block until every admitted request has finished or timeout_ms passed
  * (WF_ETIMEOUT). */
 wf_status wf_server_drain(wf_server_t server, int timeout_ms);

@@ -336,6 +336,24 @@ wf_status Plan::ensure_hist(int cap) {
   return WF_OK;
 }
 
+wf_status plan_rebind(Plan *P, const double *cl, const double *w, double tau, long long n_obs) {
+  cudaStream_t s = P->stream;
+  P->h_cl.assign(cl, cl + P->lmax + 1);
+  P->tau = tau;
+  P->n_obs = n_obs;
+  std::vector<double> neg(P->R, -1.0);
+  WF_CUDA(cudaMemcpyAsync(P->d_cl, cl, sizeof(double) * (P->lmax + 1), cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_w, w, sizeof(double) * P->npix, cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_gainlam, neg.data(), sizeof(double) * P->R, cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  if (P->graph_exec) {  // the captured launches hold the old tau
+    cudaGraphExecDestroy(P->graph_exec);
+    P->graph_exec = nullptr;
+  }
+  P->fs_valid = false;
+  return WF_OK;
+}
+
 RingArgs Plan::ring_args() const {
   RingArgs a{};
   a.rings = d_rings; a.order = d_order; a.first = 0; a.scratch = d_ring_scratch; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;

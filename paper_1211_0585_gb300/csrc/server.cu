@@ -9,9 +9,19 @@
 //     of an engine by a block of iterations; finished slots are harvested and
 //     refilled before the next step, so a request that arrives while others
 //     iterate joins at the next step with its own lambda schedule.
-//   - tol <= 1e-7 (FP64 path): one at a time on a second worker with a plan
-//     of its own (double-float kernels), overlapping with the engines' work
-//     on the device.
+//   - tol <= 1e-7 (FP64 path): on kFp64Workers worker threads, each solve on
+//     a plan of its shape taken from a pool (created on first use within the
+//     budget, re-pointed at the request's C_l, noise and mask by plan_rebind,
+//     returned afterwards), so that geometry, Legendre and lambda tables stay
+//     resident; the workers' streams overlap with each other and with the
+//     engines' work on the device.
+//   - a mixed request whose shape's engine has no live slot runs on the FP64
+//     pool instead while two of its workers are free (one stays for the
+//     requests that need FP64): the engine's tensor-core GEMMs stream
+//     its whole FP32 table per iteration however few slots are live, which for
+//     one request costs more than the FP64 single solve (Nside 512: about
+//     3 ms against 1.7 ms per iteration), and the FP64 result meets any
+//     tolerance. Under load the engines fill and batch as above.
 // Latency is measured from wf_submit to the moment the result is on the host.
 #include <cuda_runtime.h>
 
@@ -36,6 +46,7 @@ using Clock = std::chrono::steady_clock;
 namespace {
 
 constexpr double kFp64Tol = 1e-7;
+constexpr int kFp64Workers = 3;
 
 struct Request {
   uint64_t ticket = 0;
@@ -51,7 +62,18 @@ struct Request {
   wf_status status = WF_OK;
   std::vector<double> alm;
   wf_stats stats{};
-  size_t fp64_bytes = 0;
+};
+
+struct WarmTask {
+  int nside = 0, lmax = 0;
+  bool done = false;
+  wf_status status = WF_OK;
+};
+
+struct IdlePlan {
+  Plan *plan = nullptr;
+  size_t bytes = 0;
+  Clock::time_point last_used;
 };
 
 struct ShapeRunner {
@@ -83,13 +105,17 @@ struct wf_server_s {
   uint64_t next_ticket = 1;
   std::deque<std::shared_ptr<Request>> pending;      // mixed requests not yet in a slot
   std::deque<std::shared_ptr<Request>> fp64_queue;   // FP64 requests
+  std::deque<std::shared_ptr<WarmTask>> warm_queue;  // shapes whose engine the worker builds next
   std::map<uint64_t, std::shared_ptr<Request>> all;  // every uncollected request
   int in_flight = 0;                                 // submitted and not finished
   std::vector<double> latencies_ms;
   int64_t completed = 0;
   std::map<std::pair<int, int>, std::unique_ptr<ShapeRunner>> runners;  // worker thread only
-  size_t fp64_bytes_in_use = 0;
-  std::thread worker, fp64_worker;
+  size_t fp64_bytes_in_use = 0;                      // every FP64 plan, busy or idle
+  int fp64_busy = 0;                                 // FP64 workers solving
+  std::map<std::pair<int, int>, std::vector<IdlePlan>> fp64_idle;  // FP64 plans not solving, per shape
+  std::thread worker;
+  std::vector<std::thread> fp64_workers;
   std::string worker_error;
 
   void finish(const std::shared_ptr<Request> &r) {
@@ -147,9 +173,31 @@ size_t fp64_bytes(int nside, int lmax) {
 }
 
 size_t bytes_in_use(wf_server_s *S) {
-  size_t b = S->fp64_bytes_in_use;
+  size_t b;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    b = S->fp64_bytes_in_use;
+  }
   for (auto &kv : S->runners) b += kv.second->bytes;
   return b;
+}
+
+// Take the least recently used idle FP64 plan out of the pool (caller holds mu
+// and destroys the plan without it); nullptr when none is idle.
+Plan *evict_idle_fp64(wf_server_s *S) {
+  auto best = S->fp64_idle.end();
+  size_t bi = 0;
+  for (auto it = S->fp64_idle.begin(); it != S->fp64_idle.end(); ++it)
+    for (size_t i = 0; i < it->second.size(); ++i)
+      if (best == S->fp64_idle.end() || it->second[i].last_used < best->second[bi].last_used) {
+        best = it;
+        bi = i;
+      }
+  if (best == S->fp64_idle.end()) return nullptr;
+  Plan *p = best->second[bi].plan;
+  S->fp64_bytes_in_use -= best->second[bi].bytes;
+  best->second.erase(best->second.begin() + bi);
+  return p;
 }
 
 // Find or create the runner of a shape within the budget (evicting idle ones).
@@ -165,7 +213,16 @@ ShapeRunner *runner_for(wf_server_s *S, int nside, int lmax) {
       if (jt->second->live() == 0 &&
           (victim == S->runners.end() || jt->second->last_used < victim->second->last_used))
         victim = jt;
-    if (victim == S->runners.end()) return nullptr;  // no room yet: wait for slots to free
+    if (victim == S->runners.end()) {
+      Plan *p = nullptr;  // no idle runner: an idle FP64 plan gives its memory back
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        p = evict_idle_fp64(S);
+      }
+      if (!p) return nullptr;  // no room yet: wait for slots to free
+      wf_plan_destroy(p);
+      continue;
+    }
     S->runners.erase(victim);
   }
   auto R = std::make_unique<ShapeRunner>();
@@ -190,18 +247,41 @@ void worker_loop(wf_server_s *S) {
   for (;;) {
     // admission
     std::vector<std::shared_ptr<Request>> take;
+    std::vector<std::shared_ptr<WarmTask>> warm;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       bool busy = false;
       for (auto &kv : S->runners) busy |= kv.second->live() > 0;
-      if (!busy) S->cv.wait_for(lk, std::chrono::milliseconds(20), [&] { return S->stop || !S->pending.empty(); });
+      if (!busy)
+        S->cv.wait_for(lk, std::chrono::milliseconds(20),
+                       [&] { return S->stop || !S->pending.empty() || !S->warm_queue.empty(); });
       if (S->stop) return;
       take.assign(S->pending.begin(), S->pending.end());
       S->pending.clear();
+      warm.assign(S->warm_queue.begin(), S->warm_queue.end());
+      S->warm_queue.clear();
+    }
+    for (auto &w : warm) {
+      const wf_status st = runner_for(S, w->nside, w->lmax) ? WF_OK : WF_ENOMEM;
+      std::lock_guard<std::mutex> lk(S->mu);
+      w->status = st;
+      w->done = true;
+      S->cv_done.notify_all();
     }
     std::vector<std::shared_ptr<Request>> keep;
     std::map<ShapeRunner *, bool> changed;
     for (auto &r : take) {
+      {
+        auto it = S->runners.find(std::make_pair(r->nside, r->lmax));
+        const bool idle_engine = it == S->runners.end() || it->second->live() == 0;
+        std::lock_guard<std::mutex> lk(S->mu);
+        // one worker stays free for the requests that need FP64
+        if (idle_engine && S->fp64_queue.empty() && S->fp64_busy < kFp64Workers - 1) {
+          S->fp64_queue.push_back(r);  // a lone request: the FP64 single solve is faster
+          S->cv.notify_all();
+          continue;
+        }
+      }
       ShapeRunner *R = runner_for(S, r->nside, r->lmax);
       int b = -1;
       if (R)
@@ -269,35 +349,69 @@ void worker_loop(wf_server_s *S) {
 void fp64_loop(wf_server_s *S) {
   for (;;) {
     std::shared_ptr<Request> r;
+    Plan *plan = nullptr;
+    size_t bytes = 0;
+    std::vector<Plan *> victims;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return S->stop || !S->fp64_queue.empty(); });
       if (S->stop) return;
       if (S->fp64_queue.empty()) continue;
       r = S->fp64_queue.front();
-      const size_t need = fp64_bytes(r->nside, r->lmax);
-      if (S->fp64_bytes_in_use + need > S->budget) continue;  // wait for room
+      auto &idle = S->fp64_idle[std::make_pair(r->nside, r->lmax)];
+      if (!idle.empty()) {  // a resident plan of the shape
+        plan = idle.back().plan;
+        bytes = idle.back().bytes;
+        idle.pop_back();
+      } else {
+        bytes = fp64_bytes(r->nside, r->lmax);
+        while (S->fp64_bytes_in_use + bytes > S->budget)
+          if (Plan *v = evict_idle_fp64(S)) victims.push_back(v);
+          else break;
+        if (S->fp64_bytes_in_use + bytes > S->budget) {  // wait for a plan to come back
+          lk.unlock();
+          for (Plan *v : victims) wf_plan_destroy(v);
+          std::unique_lock<std::mutex> lk2(S->mu);
+          S->cv.wait_for(lk2, std::chrono::milliseconds(20));
+          continue;
+        }
+        S->fp64_bytes_in_use += bytes;
+      }
       S->fp64_queue.pop_front();
-      S->fp64_bytes_in_use += need;
-      r->fp64_bytes = need;
+      ++S->fp64_busy;
     }
+    for (Plan *v : victims) wf_plan_destroy(v);
     wf_options o;
     wf_options_default(&o);
     o.tol = r->tol;
-    wf_plan_t p = nullptr;
-    wf_status st = wf_plan_create(r->nside, r->lmax, r->cl.data(), r->noise.data(),
-                                  r->mask.empty() ? nullptr : r->mask.data(), &o, &p);
+    wf_status st = WF_OK;
+    if (plan) {
+      st = plan_rebind(plan, r->cl.data(), r->w.data(), r->tau, r->n_obs);
+      if (st == WF_OK) st = wf_plan_set_options(plan, &o);
+    } else {
+      wf_plan_t p = nullptr;
+      st = wf_plan_create(r->nside, r->lmax, r->cl.data(), r->noise.data(),
+                          r->mask.empty() ? nullptr : r->mask.data(), &o, &p);
+      plan = static_cast<Plan *>(p);
+    }
     if (st == WF_OK) {
       r->alm.resize(2 * (size_t)(r->lmax + 1) * (r->lmax + 2) / 2);
-      st = wf_solve(p, r->d.data(), 0, r->alm.data(), 0, nullptr, &r->stats);
+      st = wf_solve(plan, r->d.data(), 0, r->alm.data(), 0, nullptr, &r->stats);
       r->stats.ms_device = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
-      wf_plan_destroy(p);
     }
     r->status = st;
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      S->fp64_bytes_in_use -= r->fp64_bytes;
+      --S->fp64_busy;
+      if (plan && (st == WF_OK || st == WF_ENOTCONVERGED || st == WF_ENUMERIC)) {
+        S->fp64_idle[std::make_pair(r->nside, r->lmax)].push_back(IdlePlan{plan, bytes, Clock::now()});
+        plan = nullptr;
+      } else {
+        S->fp64_bytes_in_use -= bytes;
+      }
     }
+    if (plan) wf_plan_destroy(plan);
+    S->cv.notify_all();
     S->finish(r);
   }
 }
@@ -322,7 +436,7 @@ wf_status wf_server_create(size_t hbm_budget_bytes, int max_batch, wf_server_t *
   S->budget = budget;
   S->max_batch = max_batch;
   S->worker = std::thread(worker_loop, S);
-  S->fp64_worker = std::thread(fp64_loop, S);
+  for (int i = 0; i < kFp64Workers; ++i) S->fp64_workers.emplace_back(fp64_loop, S);
   *out = S;
   return WF_OK;
 }
@@ -393,6 +507,46 @@ wf_status wf_poll(wf_server_t S, uint64_t ticket, int *done, double *alm_out, wf
   return r->status;
 }
 
+wf_status wf_server_warm(wf_server_t S, int nside, int lmax, int precision) {
+  if (!S) { set_error("wf_server_warm: NULL server"); return WF_EINVAL; }
+  if (nside < 1 || nside > 1024 || (nside & (nside - 1)) != 0 || lmax < 0 || lmax > 4 * nside) {
+    set_error("wf_server_warm: nside must be a power of two in [1, 1024] and 0 <= lmax <= 4 nside");
+    return WF_EINVAL;
+  }
+  if (precision == WF_PREC_MIXED) {
+    auto w = std::make_shared<WarmTask>();
+    w->nside = nside;
+    w->lmax = lmax;
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->warm_queue.push_back(w);
+    S->cv.notify_all();
+    S->cv_done.wait(lk, [&] { return w->done || S->stop; });
+    if (!w->done) { set_error("wf_server_warm: the server is shutting down"); return WF_ECANCELLED; }
+    if (w->status != WF_OK) set_error("wf_server_warm: the shape's engine does not fit the budget now");
+    return w->status;
+  }
+  if (precision != WF_PREC_FP64) { set_error("wf_server_warm: precision must be WF_PREC_MIXED or WF_PREC_FP64"); return WF_EINVAL; }
+  const size_t bytes = fp64_bytes(nside, lmax);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->fp64_bytes_in_use + bytes > S->budget) {
+      set_error("wf_server_warm: an FP64 plan of the shape does not fit the budget now");
+      return WF_ENOMEM;
+    }
+    S->fp64_bytes_in_use += bytes;
+  }
+  std::vector<double> unit(12LL * nside * nside, 1.0), cl(lmax + 1, 1.0);
+  wf_plan_t p = nullptr;
+  const wf_status st = wf_plan_create(nside, lmax, cl.data(), unit.data(), nullptr, nullptr, &p);
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (st != WF_OK) {
+    S->fp64_bytes_in_use -= bytes;
+    return st;
+  }
+  S->fp64_idle[std::make_pair(nside, lmax)].push_back(IdlePlan{static_cast<Plan *>(p), bytes, Clock::now()});
+  return WF_OK;
+}
+
 wf_status wf_server_drain(wf_server_t S, int timeout_ms) {
   if (!S) { set_error("wf_server_drain: NULL server"); return WF_EINVAL; }
   std::unique_lock<std::mutex> lk(S->mu);
@@ -425,9 +579,13 @@ wf_status wf_server_destroy(wf_server_t S) {
     S->stop = true;
   }
   S->cv.notify_all();
+  S->cv_done.notify_all();
   if (S->worker.joinable()) S->worker.join();
-  if (S->fp64_worker.joinable()) S->fp64_worker.join();
+  for (auto &t : S->fp64_workers)
+    if (t.joinable()) t.join();
   S->runners.clear();
+  for (auto &kv : S->fp64_idle)
+    for (auto &ip : kv.second) wf_plan_destroy(ip.plan);
   delete S;
   return WF_OK;
 }

@@ -90,6 +90,13 @@ struct Plan : wf_plan_s {
   double lambda_of(int l_iter) const;
 };
 
+// Re-point a plan at another problem of its shape: C_l ([lmax+1]), the inverse
+// noise w ([npix], 0 where masked), tau and the observed-pixel count. Every
+// table derived from the geometry (FFT, Legendre, lambda table) is kept; the
+// cached Eq. 3 gains and the captured iteration graph are dropped. Host
+// arrays are read before it returns.
+wf_status plan_rebind(Plan *P, const double *cl, const double *w, double tau, long long n_obs);
+
 // Mixed-precision solves through the plan's batched engine (batch.cu).
 wf_status solve_mixed(Plan *P, int nrhs, const double *d, int d_on_device, double *alm_out, int alm_on_device,
                       wf_stats *stats);

@@ -26,7 +26,7 @@ EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_
             "wf_plan_legendre_table", "wf_plan_kernels_per_iteration", "wf_plan_set_options",
             "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
             "wf_solve_history", "wf_solve_batch",
-            "wf_server_create", "wf_submit", "wf_poll", "wf_server_drain", "wf_server_stats",
+            "wf_server_create", "wf_submit", "wf_poll", "wf_server_warm", "wf_server_drain", "wf_server_stats",
             "wf_server_destroy", "wf_last_error"]
 
 
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "wf_submit": [_vp, _i, _i, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_uint64)],
         "wf_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(_i), _vp, ctypes.POINTER(Stats)],
         "wf_server_drain": [_vp, _i],
+        "wf_server_warm": [_vp, _i, _i, _i],
         "wf_server_stats": [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64)],
         "wf_server_destroy": [_vp],
     }
@@ -307,6 +308,10 @@ class Server:
         self._nalm.pop(ticket, None)
         _check(status, ok=(WF_OK, WF_ENOTCONVERGED))
         return out, st.as_dict(), status
+
+    def warm(self, nside, lmax, precision):
+        """Make a shape resident (WF_PREC_MIXED: its batched engine; WF_PREC_FP64: one pooled plan)."""
+        _check(load().wf_server_warm(self.handle, nside, lmax, precision))
 
     def drain(self, timeout_ms=600000):
         _check(load().wf_server_drain(self.handle, timeout_ms))

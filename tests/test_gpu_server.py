@@ -68,6 +68,29 @@ def test_server_mixed_and_fp64_requests():
     S.close()
 
 
+def test_server_fp64_plan_reuse():
+    """FP64 requests of one shape that arrive one after another run on the same
+    resident plan, re-pointed at each request's C_l, noise and mask: each
+    result is bitwise the result of a fresh plan for that request."""
+    S = wf.Server(hbm_budget_bytes=8 << 30, max_batch=1)
+    S.warm(32, 64, wf.WF_PREC_FP64)          # the first request already finds a resident plan
+    S.warm(16, 32, wf.WF_PREC_MIXED)
+    with pytest.raises(wf.WFError):
+        S.warm(16, 32, 7)
+    for i, seed in enumerate((301, 302, 303)):
+        r = make_request(seed, 32, 64)
+        if i == 1:
+            r["mask"] = None
+        t = S.submit(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"], r["d"], 1e-8)
+        S.drain(300000)
+        alm, _, status = S.poll(t)
+        assert status == wf.WF_OK
+        P = wf.Plan(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"], wf.options(precision=0, tol=1e-8))
+        alone, _, _, _ = P.solve(r["d"])
+        assert np.array_equal(alm, alone)
+    S.close()
+
+
 def test_server_rejects_bad_requests():
     S = wf.Server(hbm_budget_bytes=1 << 30, max_batch=1)
     npix = 12 * 4 * 4
