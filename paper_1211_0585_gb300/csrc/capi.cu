@@ -204,8 +204,23 @@ static wf_status build_geometry(Plan *P) {
     for (int i = next; i < R; ++i) lg = std::max(lg, rings[order[i]].logM);
     P->rsingle.push_back(RingClass{lg, next, R - next, 0});
   }
+  // the same launches in ring pairs (the two rings of a pair are adjacent in a class)
+  std::vector<int2> porder;
+  P->psingle.clear();
+  for (const RingClass &c : P->rsingle) {
+    RingClass g = c;
+    g.first = (int)porder.size();
+    for (int i = c.first; i < c.first + c.count;) {
+      const bool both = i + 1 < c.first + c.count && rings[order[i + 1]].pair == rings[order[i]].pair;
+      porder.push_back(make_int2(order[i], both ? order[i + 1] : -1));
+      i += both ? 2 : 1;
+    }
+    g.count = (int)porder.size() - g.first;
+    P->psingle.push_back(g);
+  }
   if ((st = P->dalloc((void **)&P->d_rings, sizeof(RingDev) * R))) return st;
   if ((st = P->dalloc((void **)&P->d_order, sizeof(int) * R))) return st;
+  if ((st = P->dalloc((void **)&P->d_porder, sizeof(int2) * porder.size()))) return st;
   if (scratch_elems > 0 && (st = P->dalloc(&P->d_ring_scratch, 16 * scratch_elems))) return st;
   if ((st = P->dalloc((void **)&P->d_hs, sizeof(double2) * hs.size()))) return st;
   if ((st = P->dalloc((void **)&P->d_chirp, sizeof(double2) * ch.size()))) return st;
@@ -215,6 +230,7 @@ static wf_status build_geometry(Plan *P) {
   cudaStream_t s = P->stream;
   WF_CUDA(cudaMemcpyAsync(P->d_rings, rings.data(), sizeof(RingDev) * R, cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_order, order.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_porder, porder.data(), sizeof(int2) * porder.size(), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_hs, hs.data(), sizeof(double2) * hs.size(), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_chirp, ch.data(), sizeof(double2) * ch.size(), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, s));
@@ -356,7 +372,7 @@ wf_status plan_rebind(Plan *P, const double *cl, const double *w, double tau, lo
 
 RingArgs Plan::ring_args() const {
   RingArgs a{};
-  a.rings = d_rings; a.order = d_order; a.first = 0; a.scratch = d_ring_scratch; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;
+  a.rings = d_rings; a.order = d_order; a.porder = d_porder; a.first = 0; a.scratch = d_ring_scratch; a.tw = d_tw; a.logMmax = logMmax; a.hs = d_hs; a.chirp = d_chirp; a.B = d_B;
   a.FS = d_FS; a.FT = d_FT; a.RP = RP; a.d = d_d; a.w = d_w; a.ring_part = d_ring_part; a.ctl = d_ctl;
   a.lsht = lmax; a.omega = omega; a.tau = tau; a.gain = d_gain; a.gainlam = d_gainlam;
   return a;

@@ -48,6 +48,8 @@ namespace wfk {
 constexpr int kNoStartD = 1 << 30;
 constexpr int kAnaChunk = 1024;   // ring pairs whose analysis state is held in shared memory at once
 constexpr int kTabTiles = kAnaChunk / 32;  // table form: tiles of 32 ring pairs per analysis chunk
+constexpr int kSynRows = 4;       // table form: rows per synthesis load batch (two batches in flight)
+constexpr int kTabBlocks = 3;     // table form: CTAs per SM the register budget is set for
 constexpr int kWarps = kThreads / 32;
 
 __device__ __forceinline__ size_t alm_idx_d(int lmax, int l, int m) {
@@ -216,7 +218,7 @@ __device__ __forceinline__ void df_xor_sum(float &S, float &C, int off) {
 }
 
 template <int MODE, bool TAB>
-__global__ void __launch_bounds__(kThreads, TAB ? 3 : 2) legendre_df_kernel(const LegArgs A, const LegDfArgs D) {
+__global__ void __launch_bounds__(kThreads, TAB ? kTabBlocks : 2) legendre_df_kernel(const LegArgs A, const LegDfArgs D) {
   extern __shared__ double2 dsm[];
   __shared__ double red[kThreads / 32][32];
   __shared__ double mred[kThreads / 32][3];
@@ -487,18 +489,18 @@ __global__ void __launch_bounds__(kThreads, TAB ? 3 : 2) legendre_df_kernel(cons
       float ERs = 0.f, ERc = 0.f, EIs = 0.f, EIc = 0.f, ORs = 0.f, ORc = 0.f, OIs = 0.f, OIc = 0.f;
       if (lw <= L) {
         const float4 *src = tm + (size_t)cg * npr * 32 + lane;
-        auto load = [&](int r, float4 (&v)[4]) {
+        auto load = [&](int r, float4 (&v)[kSynRows]) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < kSynRows; ++i)
             v[i] = (r + i <= rlast) ? __ldcs(src + (size_t)(r + i) * 32) : make_float4(0.f, 0.f, 0.f, 0.f);
         };
-        float4 cur[4], nxt[4];
+        float4 cur[kSynRows], nxt[kSynRows];
         int r = (lw - m) >> 1;
         load(r, cur);
-        for (; r <= rlast; r += 4) {
-          if (r + 4 <= rlast) load(r + 4, nxt);
+        for (; r <= rlast; r += kSynRows) {
+          if (r + kSynRows <= rlast) load(r + kSynRows, nxt);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < kSynRows; ++i) {
             if (r + i <= rlast) {
               const float4 ce = ss[2 * (r + i)], co = ss[2 * (r + i) + 1];
               const dfl le{cur[i].x, cur[i].y}, lo{cur[i].z, cur[i].w};
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, TAB ? 3 : 2) legendre_df_kernel(cons
             }
           }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
+          for (int i = 0; i < kSynRows; ++i) cur[i] = nxt[i];
         }
       }
       if (k < RP) {

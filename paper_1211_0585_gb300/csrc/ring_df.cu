@@ -73,19 +73,32 @@ __device__ void block_sum2(double &a, double &b, double *red) {
 
 }  // namespace
 
+// One CTA per ring pair: the two rings of a pair have the same length,
+// half-pixel shift and tables, and real pixel values, so they share one
+// complex transform (Sect. 2 basis change, both directions):
+//   synthesis  IDFT(G_N + i G_S) = f_N + i f_S
+//   analysis   Z = DFT(u_N + i u_S): U_N(q) = (Z_q + conj Z_{n-q}) / 2,
+//                                    U_S(q) = (Z_q - conj Z_{n-q}) / (2 i)
+// which halves the FFT work against one transform per ring. The equator is a
+// pair of one ring (its south half stays zero). Eq. 3 runs in place on the
+// inverse transform's output, which is the forward transform's input order.
+// 256 threads and three CTAs per SM (up to 64 KB of FFT buffer each at Nside
+// 512), so that one pair's barriers and global loads overlap another's work.
+constexpr int kRingDfThreads = 256;
 template <int MODE>
-__global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A, const RingDfArgs T) {
+__global__ void __launch_bounds__(kRingDfThreads, 3) ring_df_kernel(const RingArgs A, const RingDfArgs T) {
   extern __shared__ float4 rsm[];
-  const int r = A.order ? A.order[A.first + blockIdx.x] : A.first + blockIdx.x;
-  const RingDev rg = A.rings[r];
+  const int2 pr = A.porder[A.first + blockIdx.x];  // (north ring, south ring or -1)
+  const RingDev rg = A.rings[pr.x];
+  const bool two = pr.y >= 0;
+  const long long offS = two ? A.rings[pr.y].off : 0;
   const int n = rg.n;
   const int M = 1 << rg.logM;
   const int Mp = M;
   // [Mp] (swizzled, px): shared memory, or this CTA's part of the global scratch
   float4 *buf = A.scratch ? reinterpret_cast<float4 *>(A.scratch) + (size_t)blockIdx.x * M : rsm;
-  double *ureal = reinterpret_cast<double *>(A.scratch ? rsm : rsm + Mp);   // [n]
   __shared__ double red[64];
-  __shared__ double2 fold_part[kRingThreads];
+  __shared__ double4_16a fold_part[kRingDfThreads];
 
   int L = A.lsht;
   double lam = 1.0;
@@ -98,12 +111,11 @@ __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A,
   const float4 *ch = T.chirp + rg.ch_off;
   const float4 *Bf = T.B + rg.B_off;
   const int k = rg.pair;
-  const int slot = rg.side;
 
   if (MODE == RING_SYNTH || MODE == RING_ITER) {
-    // folding is a handful of additions: done in double
-    fold_ring(A.FS, A.RP, k, slot, rg.shifted, n, L, fold_part, [&](int q, double2 g) {
-      float4 acc = pack(mk(g.x), mk(g.y));
+    // folding is a handful of additions: done in double; Z = G_N + i G_S
+    fold_ring2(A.FS, A.RP, k, rg.shifted, n, L, fold_part, [&](int q, double2 gN, double2 gS) {
+      float4 acc = pack(mk(gN.x - gS.y), mk(gN.y + gS.x));
       if (rg.shifted) acc = cmul(acc, hs[q]);
       buf[px<OpsDF>(q)] = rg.blue ? cmul(cconj(acc), ch[q]) : acc;
     });
@@ -113,69 +125,94 @@ __global__ void __launch_bounds__(kRingThreads) ring_df_kernel(const RingArgs A,
     __syncthreads();
     if (rg.blue) bluestein4<OpsDF, 1>(buf, Mp, M, rg.logM, Bf, T.tw, A.logMmax);
     else fft_dif4<OpsDF, 1>(buf, Mp, M, rg.logM, +1, T.tw, A.logMmax);
-    if (MODE == RING_SYNTH) {
-      for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const dd f = rg.blue ? RE(cmul(ch[p], buf[px<OpsDF>(p)])) : RE(buf[px<OpsDF>(digitrev(p, rg.logM))]);
-        A.map_out[rg.off + p] = todbl(f);
-      }
-      return;
-    }
-    double c2n = 0.0, c2l = 0.0;
-    const bool fresh = A.gainlam[r] == lam;   // gains of this ring already at this lambda
-    const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
+  }
+  // pixel p of both rings: z = f_N + i f_S at buf[loc(p)] (Bluestein: conj of ch[p] buf[p])
+  auto loc = [&](int p) { return rg.blue ? px<OpsDF>(p) : px<OpsDF>(digitrev(p, rg.logM)); };
+  auto pixel = [&](int p) {
+    const float4 v = buf[loc(p)];
+    return rg.blue ? cconj(cmul(ch[p], v)) : v;
+  };
+  if (MODE == RING_SYNTH) {
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const dd sdf = rg.blue ? RE(cmul(ch[p], buf[px<OpsDF>(p)])) : RE(buf[px<OpsDF>(digitrev(p, rg.logM))]);
-      const double s = todbl(sdf);
-      const double w = A.w[rg.off + p];
-      const double res = A.d[rg.off + p] - s;
-      const double g = fresh ? A.gain[rg.off + p] : w / (1.0 + l1t * w);
-      if (!fresh) A.gain[rg.off + p] = g;
-      c2n += w * res * res;
-      c2l += g * res * res;
-      ureal[p] = lt * g * res;
+      const float4 z = pixel(p);
+      A.map_out[rg.off + p] = todbl(RE(z));
+      if (two) A.map_out[offS + p] = todbl(IM(z));
+    }
+    return;
+  }
+  if (MODE == RING_ITER) {
+    double c2n = 0.0, c2l = 0.0, c2nS = 0.0, c2lS = 0.0;
+    const bool fresh = A.gainlam[pr.x] == lam;   // gains of this pair already at this lambda
+    const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
+    auto update = [&](long long at, double s, double &cn, double &cl) {  // Eq. 3, returns u
+      const double w = A.w[at];
+      const double res = A.d[at] - s;
+      const double g = fresh ? A.gain[at] : w / (1.0 + l1t * w);
+      if (!fresh) A.gain[at] = g;
+      cn += w * res * res;
+      cl += g * res * res;
+      return lt * g * res;
+    };
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      const float4 z = pixel(p);
+      const double uN = update(rg.off + p, todbl(RE(z)), c2n, c2l);
+      const double uS = two ? update(offS + p, todbl(IM(z)), c2nS, c2lS) : 0.0;
+      const float4 u = pack(mk(uN), mk(uS));
+      buf[loc(p)] = rg.blue ? cmul(u, ch[p]) : u;
+    }
+    if (rg.blue) {
+      for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[px<OpsDF>(q)] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     block_sum2(c2n, c2l, red);
     if (threadIdx.x == 0) {
-      A.ring_part[2 * r] = c2n;
-      A.ring_part[2 * r + 1] = c2l;
-      if (!fresh) A.gainlam[r] = lam;   // after block_sum2's barrier: every gain of the ring is written
+      A.ring_part[2 * pr.x] = c2n;
+      A.ring_part[2 * pr.x + 1] = c2l;
     }
     __syncthreads();
-  } else {
-    for (int p = threadIdx.x; p < n; p += blockDim.x) ureal[p] = A.map_in[rg.off + p];
+    if (two) {
+      block_sum2(c2nS, c2lS, red);
+      if (threadIdx.x == 0) {
+        A.ring_part[2 * pr.y] = c2nS;
+        A.ring_part[2 * pr.y + 1] = c2lS;
+      }
+    }
+    if (threadIdx.x == 0 && !fresh) {  // after block_sum2's barrier: every gain of the pair is written
+      A.gainlam[pr.x] = lam;
+      if (two) A.gainlam[pr.y] = lam;
+    }
     __syncthreads();
-  }
-
-  if (rg.blue) {
+  } else {  // RING_ANALYSIS: u = the input maps
     for (int p = threadIdx.x; p < M; p += blockDim.x) {
       if (p < n) {
-        const dd u = mk(ureal[p]);
-        const float4 c = ch[p];
-        buf[px<OpsDF>(p)] = pack(dmul(u, RE(c)), dmul(u, IM(c)));
-      } else {
+        const float4 u = pack(mk(A.map_in[rg.off + p]), mk(two ? A.map_in[offS + p] : 0.0));
+        buf[loc(p)] = rg.blue ? cmul(u, ch[p]) : u;
+      } else if (rg.blue) {
         buf[px<OpsDF>(p)] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     __syncthreads();
-    bluestein4<OpsDF, 1>(buf, Mp, M, rg.logM, Bf, T.tw, A.logMmax);
-  } else {
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const dd u = mk(ureal[p]);
-      buf[px<OpsDF>(digitrev(p, rg.logM))] = make_float4(u.h, u.l, 0.f, 0.f);
-    }
-    __syncthreads();
-    fft_dit4<OpsDF, 1>(buf, Mp, M, rg.logM, -1, T.tw, A.logMmax);
   }
+
+  if (rg.blue) bluestein4<OpsDF, 1>(buf, Mp, M, rg.logM, Bf, T.tw, A.logMmax);
+  else fft_dit4<OpsDF, 1>(buf, Mp, M, rg.logM, -1, T.tw, A.logMmax);
   for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-    const int q = m % n, j = m / n;
-    float4 U = rg.blue ? cmul(ch[q], buf[px<OpsDF>(q)]) : buf[px<OpsDF>(q)];
+    const int q = m % n, j = m / n, qn = q ? n - q : 0;
+    const float4 Zq = rg.blue ? cmul(ch[q], buf[px<OpsDF>(q)]) : buf[px<OpsDF>(q)];
+    const float4 Zn = rg.blue ? cmul(ch[qn], buf[px<OpsDF>(qn)]) : buf[px<OpsDF>(qn)];
+    // U_N = (Z_q + conj Z_{n-q}) / 2, U_S = (Z_q - conj Z_{n-q}) / (2 i)
+    float4 UN = pack(dadd(RE(Zq), RE(Zn)), dadd(IM(Zq), dneg(IM(Zn))));
+    float4 US = pack(dadd(IM(Zq), IM(Zn)), dadd(RE(Zn), dneg(RE(Zq))));
+    UN = make_float4(0.5f * UN.x, 0.5f * UN.y, 0.5f * UN.z, 0.5f * UN.w);
+    US = make_float4(0.5f * US.x, 0.5f * US.y, 0.5f * US.z, 0.5f * US.w);
     if (rg.shifted) {
-      U = cmul(U, cconj(hs[q]));
-      if (j & 1) U = cneg(U);
+      UN = cmul(UN, cconj(hs[q]));
+      US = cmul(US, cconj(hs[q]));
+      if (j & 1) { UN = cneg(UN); US = cneg(US); }
     }
-    double *dst = reinterpret_cast<double *>(A.FT + (size_t)m * A.RP + k) + 2 * slot;
-    dst[0] = A.omega * todbl(RE(U));
-    dst[1] = A.omega * todbl(IM(U));
+    const double om = A.omega;
+    A.FT[(size_t)m * A.RP + k] = two ? make_double4_32a(om * todbl(RE(UN)), om * todbl(IM(UN)), om * todbl(RE(US)),
+                                                      om * todbl(IM(US)))
+                                     : make_double4_32a(om * todbl(RE(UN)), om * todbl(IM(UN)), 0.0, 0.0);
   }
 }
 
@@ -197,9 +234,7 @@ void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s) 
 template <int MODE>
 static void launch_ring_df_mode(const RingArgs &a, const RingDfArgs &t, const RingClass *cls, int ncls,
                                 cudaStream_t s) {
-  auto smem = [](const RingClass &c) {
-    return (c.global ? 0 : ((size_t)1 << c.logM) * sizeof(float4)) + ((size_t)1 << c.logM) * sizeof(double);
-  };
+  auto smem = [](const RingClass &c) { return c.global ? (size_t)16 : ((size_t)1 << c.logM) * sizeof(float4); };
   raise_smem_cap(reinterpret_cast<const void *>(ring_df_kernel<MODE>));
   for (int c = 0; c < ncls; ++c) {
     if (cls[c].count <= 0) continue;
@@ -207,7 +242,7 @@ static void launch_ring_df_mode(const RingArgs &a, const RingDfArgs &t, const Ri
     RingArgs ac = a;
     ac.first = cls[c].first;
     ac.scratch = cls[c].global ? a.scratch : nullptr;
-    ring_df_kernel<MODE><<<cls[c].count, kRingThreads, sm, s>>>(ac, t);
+    ring_df_kernel<MODE><<<cls[c].count, kRingDfThreads, sm, s>>>(ac, t);
   }
 }
 

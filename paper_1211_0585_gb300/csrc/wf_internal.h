@@ -89,6 +89,7 @@ enum { LEG_SYNTH = 0, LEG_ANALYSIS = 1, LEG_ITER = 2 };
 struct RingArgs {
   const RingDev *rings;
   const int *order;       // ring of CTA i is order[first + i] (nullptr: first + i)
+  const int2 *porder;     // double-float ring stage: (north ring, south ring or -1) of CTA i at porder[first + i]
   int first;
   void *scratch;          // global FFT buffers of a class that does not fit shared memory (else nullptr)
   const double2 *tw;      // e^{-2 pi i k / Mmax}, k < Mmax / 2

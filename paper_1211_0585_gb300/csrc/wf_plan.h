@@ -34,6 +34,8 @@ struct Plan : wf_plan_s {
   std::vector<RingClass> rclass;        // the classes (batched ring stage: one launch each)
   std::vector<RingClass> rsingle;       // single-solve ring stage: the classes whose 16-byte FFT buffers
                                         // do not fit shared memory (global scratch), then every other ring
+  std::vector<RingClass> psingle;       // the same classes in ring pairs (double-float ring stage)
+  int2 *d_porder = nullptr;             // pairs in class order: (north ring, south ring or -1)
   void *d_ring_scratch = nullptr;       // their FFT buffers
   double2 *d_tw = nullptr, *d_hs = nullptr, *d_chirp = nullptr, *d_B = nullptr;
   double *d_x = nullptr;
@@ -78,7 +80,7 @@ struct Plan : wf_plan_s {
   // the ring stage of the plan's precision
   void launch_rng(const RingArgs &a, cudaStream_t s, int mode) const {
     if (opt.precision == WF_PREC_FP64_NATIVE) launch_ring(a, rsingle.data(), (int)rsingle.size(), s, mode);
-    else launch_ring_df(a, ringdf_args(), rsingle.data(), (int)rsingle.size(), s, mode);
+    else launch_ring_df(a, ringdf_args(), psingle.data(), (int)psingle.size(), s, mode);
   }
   // the Legendre stage of the plan's precision
   void launch_leg(const LegArgs &a, cudaStream_t s, int mode) const {
