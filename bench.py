@@ -270,6 +270,7 @@ def run_ours(args):
         "gpu_launches": int(sum(launches_per_solve)),
         "clocks": clk.summary(),
         "final": {"chi2_per_dof": st["chi2_per_dof"], "rel_increment": st["rel_increment"],
+                  "rel_posterior_grad": st["rel_posterior_grad"],
                   "levels": st["levels"], "status": status},
     }
     if rank == 0 and world == 1 and not args.no_extras:

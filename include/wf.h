@@ -94,6 +94,8 @@ typedef struct {
                             bytes; the Legendre stage then reads it instead of running the recurrence.
                             Decided at wf_plan_create; 0 = always the recurrence (8 GiB: Nside <= 512
                             at lmax = 2 Nside) */
+  int posterior_grad;    /* 1: wf_solve on the FP64 paths also reports rel_posterior_grad (one synthesis
+                            and two analyses after the solve) (1) */
   void *stream;          /* cudaStream_t to run on; NULL = the plan's own stream */
 } wf_options;
 
@@ -110,6 +112,10 @@ typedef struct {
   double chi2_per_dof;   /* chi2 / n_obs */
   double rel_increment;  /* ||s_k - s_{k-1}|| / ||s_k|| of the last iteration */
   double ms_device;      /* device time of the solve, CUDA events */
+  double rel_posterior_grad; /* ||Y^T W (d - Y a) - C^-1 a|| / ||Y^T W d|| of the result (modes with C_l > 0,
+                            m > 0 counted twice; Y^T = map2alm / Omega): how far it is from the posterior
+                            mean on the grid (Eq. 2), bounded below by the quadrature error of the HEALPix
+                            analysis. FP64 paths with opt.posterior_grad = 1; -1 when not computed */
 } wf_stats;
 
 /* Per-iteration record written by wf_iterate / wf_solve_history. */

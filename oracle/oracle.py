@@ -243,6 +243,23 @@ def alm_norm2(alm, lmax):
     return float(np.sum(alm_weight(lmax) * np.abs(alm) ** 2))
 
 
+def posterior_residual(nside, lmax, alm, cl, noise_var, mask, d):
+    """How far alm is from the posterior mean of Eq. 2 on the grid: with
+    Y = synthesis, Y^T = map2alm / Omega and W = N^-1 (0 where masked), the
+    residual of the normal equations (S^-1 + Y^T W Y) a = Y^T W d,
+        r = Y^T W (d - Y a) - a / C_l        (modes with C_l > 0),
+    relative to b = Y^T W d, in the field's norm (m > 0 counted twice)."""
+    omega = 4.0 * np.pi / (12 * nside * nside)
+    w = inverse_noise(noise_var, mask)
+    c = np.asarray(cl, dtype=np.float64)[l_of_index(lmax)]
+    good = c > 0
+    r = map2alm(nside, lmax, w * (d - alm2map(nside, lmax, alm))) / omega
+    r[good] -= alm[good] / c[good]
+    b = map2alm(nside, lmax, w * d) / omega
+    wt = alm_weight(lmax)[good]
+    return float(np.sqrt(np.sum(wt * np.abs(r[good]) ** 2) / np.sum(wt * np.abs(b[good]) ** 2)))
+
+
 @dataclass
 class StepResult:
     s_alm: np.ndarray      # s^(k), lmax layout

@@ -340,6 +340,7 @@ static void fill_stats(wf_stats *st, const Ctl &c, const wf_iter_record &r, long
   st->chi2_per_dof = st->chi2 / (double)n_obs;
   st->rel_increment = c.last_rel;
   st->ms_device = ms;
+  st->rel_posterior_grad = -1.0;  // not computed on the mixed path
 }
 
 // Mixed-precision solves of nrhs data maps sharing the plan's C_l, noise and

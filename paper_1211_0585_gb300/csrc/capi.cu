@@ -321,6 +321,9 @@ wf_status Plan::alloc_work() {
   if ((st = dalloc((void **)&d_s, sizeof(double2) * nalm))) return st;
   if ((st = dalloc((void **)&d_gain, sizeof(double) * npix))) return st;
   if ((st = dalloc((void **)&d_gainlam, sizeof(double) * R))) return st;
+  if ((st = dalloc((void **)&d_pmap, sizeof(double) * 2 * npix))) return st;
+  if ((st = dalloc((void **)&d_palm, sizeof(double2) * 2 * nalm))) return st;
+  if ((st = dalloc((void **)&d_ppart, sizeof(double) * 2 * (lmax + 1)))) return st;
   {
     std::vector<double> neg(R, -1.0);
     WF_CUDA(cudaMemcpy(d_gainlam, neg.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
@@ -447,6 +450,7 @@ wf_status wf_options_default(wf_options *o) {
   o->graph_iters = 16;
   o->batch_slots = kBatchMax;
   o->legendre_table_bytes = (size_t)8 << 30;
+  o->posterior_grad = 1;
   o->stream = nullptr;
   return WF_OK;
 }
@@ -727,6 +731,38 @@ wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_d
   return WF_OK;
 }
 
+// rel_posterior_grad of the plan's state d_s against its data d_d (posterior.cu):
+// synthesis, W (d - Y a) and W d, two analyses, per-m norms summed in order.
+static wf_status posterior_grad(Plan *P, cudaStream_t s, double *rel) {
+  const long long npix = P->npix, nalm = P->nalm;
+  double *ya = P->d_pmap, *wd = P->d_pmap + npix;
+  double2 *ta = P->d_palm, *tb = P->d_palm + nalm;
+  LegArgs la = P->leg_args();
+  la.lsht = P->lmax;
+  la.alm_in = P->d_s;
+  P->launch_leg(la, s, LEG_SYNTH);
+  RingArgs ra = P->ring_args();
+  ra.lsht = P->lmax;
+  ra.map_out = ya;
+  P->launch_rng(ra, s, RING_SYNTH);
+  launch_posterior_maps(P->d_d, P->d_w, ya, wd, npix, s);
+  for (int i = 0; i < 2; ++i) {
+    ra.map_in = i ? wd : ya;
+    P->launch_rng(ra, s, RING_ANALYSIS);
+    la.alm = i ? tb : ta;
+    P->launch_leg(la, s, LEG_ANALYSIS);
+  }
+  launch_posterior_norms(P->d_s, ta, tb, P->d_cl, P->lmax, 1.0 / P->omega, P->d_ppart, s);
+  std::vector<double> part(2 * (P->lmax + 1));
+  WF_CUDA(cudaMemcpyAsync(part.data(), P->d_ppart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s));
+  WF_CUDA(cudaStreamSynchronize(s));
+  P->fs_valid = false;
+  double rr = 0.0, bb = 0.0;
+  for (int m = 0; m <= P->lmax; ++m) { rr += part[2 * m]; bb += part[2 * m + 1]; }
+  *rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+  return WF_OK;
+}
+
 static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *alm_out, int alm_on_device,
                             const double *alm_init, wf_stats *stats, wf_iter_record *records, int max_records,
                             int *n_records) {
@@ -789,6 +825,11 @@ static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *a
   WF_CUDA(cudaStreamSynchronize(s));
   if (n_records) *n_records = nrec;
   P->fs_valid = false;
+  double rel_pg = -1.0;
+  if (stats && P->opt.posterior_grad) {
+    wf_status st = posterior_grad(P, s, &rel_pg);
+    if (st) return st;
+  }
   if (stats) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, P->ev0, P->ev1);
@@ -803,6 +844,7 @@ static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *a
     stats->chi2_per_dof = stats->chi2 / (double)P->n_obs;
     stats->rel_increment = fin.last_rel;
     stats->ms_device = ms;
+    stats->rel_posterior_grad = rel_pg;
   }
   if (fin.numeric) { set_error("wf_solve: chi^2 is not finite"); return WF_ENUMERIC; }
   if (!fin.converged) { set_error("wf_solve: max_iter reached before the stop rule"); return WF_ENOTCONVERGED; }

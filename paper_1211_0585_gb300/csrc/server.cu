@@ -335,6 +335,7 @@ void worker_loop(wf_server_s *S) {
         r->stats.rel_increment = c.last_rel;
         r->stats.ms_device =
             std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+        r->stats.rel_posterior_grad = -1.0;  // not computed on the mixed path
         r->status = c.numeric ? WF_ENUMERIC : (c.converged ? WF_OK : WF_ENOTCONVERGED);
         R->engine->release_slot(b);
         S->finish(r);

@@ -208,6 +208,9 @@ void ring_classes(const RingDev *rings, int R, std::vector<int> &order, std::vec
 void launch_to_df(const double2 *src, float4 *dst, long long n, cudaStream_t s);
 void launch_legendre(const LegArgs &a, cudaStream_t s, int mode);
 void launch_legendre_df(const LegArgs &a, const LegDfArgs &d, cudaStream_t s, int mode);
+void launch_posterior_maps(const double *d, const double *w, double *ya, double *wd, long long npix, cudaStream_t s);
+void launch_posterior_norms(const double2 *a, const double2 *ta, const double2 *tb, const double *cl, int lmax,
+                            double inv_omega, double *part, cudaStream_t s);
 // rows of the precomputed double-float lambda table (sum over m of ceil((lmax - m + 1) / 2)),
 // each RP float4
 size_t lam_table_rows(int lmax);

@@ -62,6 +62,9 @@ struct Plan : wf_plan_s {
   int hist_cap = 0;
   double *d_d = nullptr;
   double *d_gain = nullptr, *d_gainlam = nullptr;  // cached Eq. 3 gains per pixel, lambda per ring
+  double *d_pmap = nullptr;             // posterior gradient: W (d - Y a) and W d [2][npix]
+  double2 *d_palm = nullptr;            // their analyses [2][nalm]
+  double *d_ppart = nullptr;            // per-m norms [lmax+1][2]
   double2 *d_s = nullptr;
   bool fs_valid = false;
   int fs_lsht = -1;

@@ -43,6 +43,7 @@ class Options(ctypes.Structure):
                 ("final_dchi2", ctypes.c_double), ("min_level_iters", ctypes.c_int),
                 ("max_level_iters", ctypes.c_int), ("graph_iters", ctypes.c_int),
                 ("batch_slots", ctypes.c_int), ("legendre_table_bytes", ctypes.c_size_t),
+                ("posterior_grad", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -51,7 +52,7 @@ class Stats(ctypes.Structure):
                 ("lmax_sht_final", ctypes.c_int), ("lambda_final", ctypes.c_double), ("chi2", ctypes.c_double),
                 ("chi2_prior", ctypes.c_double), ("chi2_noise", ctypes.c_double),
                 ("chi2_per_dof", ctypes.c_double), ("rel_increment", ctypes.c_double),
-                ("ms_device", ctypes.c_double)]
+                ("ms_device", ctypes.c_double), ("rel_posterior_grad", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

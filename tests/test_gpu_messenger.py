@@ -105,6 +105,25 @@ def test_solve_on_device_buffers_and_warm_start():
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_posterior_gradient_reported(prec):
+    """wf_stats.rel_posterior_grad of an FP64 solve is the oracle's posterior
+    residual of the returned a_lm (Eq. 2 normal equations on the grid); it is
+    not computed with posterior_grad = 0 or on the mixed path (-1)."""
+    p, d = problem("wmap", seed=4, nside=16, lmax=32)
+    P = wf.Plan(16, 32, p.cl, p.noise_var, p.mask, wf.options(**FP64_PATHS[prec], tol=1e-9))
+    alm, st, status, _ = P.solve(d)
+    assert status == wf.WF_OK
+    ref = O.posterior_residual(16, 32, alm, p.cl, p.noise_var, p.mask, d)
+    assert 0 < ref < 1e-6          # the fixed point solves the grid normal equations of Eq. 2
+    # r is a difference of two terms of size ||b||: rounding leaves about 1e-15 of absolute error
+    assert abs(st["rel_posterior_grad"] - ref) <= 1e-6 * ref + 1e-13
+    P.set_options(wf.options(**FP64_PATHS[prec], tol=1e-9, posterior_grad=0))
+    assert P.solve(d)[1]["rel_posterior_grad"] == -1.0
+    Q = wf.Plan(16, 32, p.cl, p.noise_var, p.mask, wf.options(precision=wf.WF_PREC_MIXED, batch_slots=1))
+    assert Q.solve(d)[1]["rel_posterior_grad"] == -1.0
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_full_size_first_iteration_nside512(prec):
     """WMAP-shaped Nside 512 / lmax 1024 at the bench's launch shapes: the
     first iteration from s = 0 is s_lm = f_l (Y^dagger a d)_lm; sampled

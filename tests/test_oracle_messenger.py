@@ -216,3 +216,33 @@ def test_cooled_solve_reaches_wiener_filter():
     assert res.converged and res.history[-1]["lam"] == 1.0
     assert len(O.schedule_of(res)) >= 2
     assert O.rel_l2(res.alm, D.unpack(xwf, lmax), lmax) < 1e-8
+
+
+def test_posterior_residual_against_dense_normal_equations():
+    """The posterior residual of a solution, from the oracle's transforms, is
+    the residual of the dense normal equations of Eq. 2 (built from scipy's
+    spherical harmonics at the pixel centres): zero at the dense Wiener
+    filter, and equal to the dense value, mapped to complex modes, for a
+    perturbed solution."""
+    nside, lmax = 4, 8
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, 31, noise=1e-2)
+    Y, Yd, f_dof, a_pix, w, tau, omega = dense_setup(nside, lmax, cl, var, mask, z, phi, 1.0)
+    cl_dof, wgt = cl[D.dof_l(lmax)], D.dof_weight(lmax)
+    xwf = D.posterior_wf(Y, w, cl_dof, wgt, d)
+    assert O.posterior_residual(nside, lmax, D.unpack(xwf, lmax), cl, var, mask, d) < 1e-10
+    rng = np.random.default_rng(7)
+    x = xwf + 1e-3 * rng.standard_normal(xwf.size) * (cl_dof > 0)
+
+    def to_modes(v):  # real degrees of freedom -> complex modes: m > 0 parts carry a factor 2
+        return np.array(D.unpack(v / wgt, lmax))
+
+    good = cl_dof > 0
+    r_dof = Y.T @ (w * (d - Y @ x))
+    r_dof[good] -= wgt[good] * x[good] / cl_dof[good]
+    r_dof[~good] = 0.0
+    b_dof = np.where(good, Y.T @ (w * d), 0.0)
+    wt = O.alm_weight(lmax)
+    rel_dense = np.sqrt(np.sum(wt * np.abs(to_modes(r_dof)) ** 2) / np.sum(wt * np.abs(to_modes(b_dof)) ** 2))
+    rel = O.posterior_residual(nside, lmax, D.unpack(x, lmax), cl, var, mask, d)
+    assert rel > 1e-6
+    assert abs(rel - rel_dense) <= 1e-9 * rel_dense
