@@ -96,6 +96,10 @@ typedef struct {
                             at lmax = 2 Nside) */
   int posterior_grad;    /* 1: wf_solve on the FP64 paths also reports rel_posterior_grad (one synthesis
                             and two analyses after the solve) (1) */
+  int synthesis_table;   /* batched engine: 1 keeps the synthesis-ordered FP32 Legendre table resident;
+                            0 rebuilds it band by band of m from the analysis table every iteration (half
+                            the table memory, one transpose pass more); -1 chooses 1 when the engine fits
+                            the free device memory with it (-1) */
   void *stream;          /* cudaStream_t to run on; NULL = the plan's own stream */
 } wf_options;
 

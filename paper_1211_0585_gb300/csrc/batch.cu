@@ -62,11 +62,12 @@ size_t Engine::bytes_needed(int nside, int lmax, int nslots) {
   const size_t operands = (L1 * 2 * RPp + 32 * nchunks) * Nc * sizeof(float);                 // XT, SPT
   const size_t per_slot = 2 * nF * sizeof(float4)                                             // FS, FT
                           + nalm * (sizeof(double2) + sizeof(float4))                          // s, sdf
-                          + npix * 2 * (sizeof(double) + sizeof(float))                         // d, w, FP32 copies
+                          + npix * 2 * sizeof(float)                                           // (d, w) in FP32
                           + L1 * (sizeof(double) + sizeof(float2) + sizeof(float))              // C_l, filter tables
                           + R * 2 * sizeof(double) + ntiles * 3 * sizeof(double)                // partials
                           + sizeof(Ctl) + sizeof(wf_iter_record) + 8;
-  return tables + operands + B * per_slot + (ntiles + L1 * RPp / 128 + 2 * L1) * 16;
+  return tables + operands + B * per_slot + npix * 2 * sizeof(double)  // d, w staging of one slot
+         + (ntiles + L1 * RPp / 128 + 2 * L1) * 16;
 }
 
 wf_status Engine::dalloc(void **p, size_t bytes) {
@@ -117,6 +118,11 @@ TcArgs Engine::tc_args() const {
   t.XT = XT;
   t.SPT = SPT;
   t.err = err;
+  t.tile0 = 0;
+  t.qbase = 0;
+  t.chunk_info = chunk_info;
+  t.lamA = lamA;
+  t.lamTs = lamTs;
   return t;
 }
 
@@ -138,8 +144,45 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ntstiles = (int)syn.size();
   const size_t nXT = (size_t)(lmax + 1) * 2 * RPp * Nc, nSPT = (size_t)nchunks * 32 * Nc;
   wf_status st;
+  // the synthesis-ordered table: resident, or rebuilt band by band of m from the
+  // analysis table each iteration (half the table memory; Nside 2048 needs it)
+  int mode = geo->opt.synthesis_table;
+  if (mode < 0) {
+    size_t fr = 0, tot = 0;
+    ENG_CUDA(cudaMemGetInfo(&fr, &tot));
+    mode = bytes_needed(geo->nside, lmax, nslots) + ((size_t)1 << 30) <= fr ? 1 : 0;
+  }
+  std::vector<int4> cinfo;
+  size_t band_chunks = 0;
+  bands.clear();
+  if (mode == 0) {
+    size_t row = 0;
+    std::vector<int> per_m(lmax + 1, 0);
+    for (int m = 0; m <= lmax; ++m)
+      for (int p = 0; p < 2; ++p) {
+        const int np = n_par(m, p, lmax);
+        for (int i0 = 0; i0 < np; i0 += 32) cinfo.push_back(make_int4((int)(row + i0), std::min(32, np - i0), m, 0));
+        per_m[m] += (np + 31) / 32;
+        row += np;
+      }
+    const int ntk = (RPp + 127) / 128;  // synthesis tiles per m
+    size_t cap = std::max<size_t>(((size_t)nchunks + 7) / 8, (size_t)*std::max_element(per_m.begin(), per_m.end()));
+    for (int m = 0; m <= lmax;) {
+      SynBand bd{off[2 * m], 0, m * ntk, 0};
+      size_t c = 0;
+      int m1 = m;
+      while (m1 <= lmax && (m1 == m || c + per_m[m1] <= cap)) c += per_m[m1++];
+      bd.q1 = bd.q0 + (int)c;
+      bd.tile1 = m1 * ntk;
+      bands.push_back(bd);
+      band_chunks = std::max(band_chunks, c);
+      m = m1;
+    }
+  }
   if ((st = dalloc((void **)&lamA, sizeof(float) * nalm * RPp)) ||
-      (st = dalloc((void **)&lamT, sizeof(float) * (size_t)nchunks * 32 * RPp)) ||
+      (mode == 1 && (st = dalloc((void **)&lamT, sizeof(float) * (size_t)nchunks * 32 * RPp))) ||
+      (mode == 0 && (st = dalloc((void **)&lamTs, sizeof(float) * band_chunks * 32 * RPp))) ||
+      (mode == 0 && (st = dalloc((void **)&chunk_info, sizeof(int4) * cinfo.size()))) ||
       (st = dalloc((void **)&XT, sizeof(float) * nXT)) || (st = dalloc((void **)&SPT, sizeof(float) * nSPT)) ||
       (st = dalloc((void **)&atiles, sizeof(int4) * ana.size())) ||
       (st = dalloc((void **)&tstiles, sizeof(int2) * syn.size())) ||
@@ -148,7 +191,7 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
       (st = dalloc((void **)&tw2, sizeof(float2) * std::max<long long>(geo->n_tw, 1))) ||
       (st = dalloc((void **)&Bf2, sizeof(float2) * std::max<long long>(geo->n_B, 1))) ||
       (st = dalloc((void **)&FS, sizeof(float4) * nF * B)) || (st = dalloc((void **)&FT, sizeof(float4) * nF * B)) ||
-      (st = dalloc((void **)&d, sizeof(double) * npix * B)) || (st = dalloc((void **)&w, sizeof(double) * npix * B)) ||
+      (st = dalloc((void **)&d, sizeof(double) * npix)) || (st = dalloc((void **)&w, sizeof(double) * npix)) ||
       (st = dalloc((void **)&dw32, sizeof(float2) * npix * B)) ||
       (st = dalloc((void **)&cl, sizeof(double) * (lmax + 1) * B)) ||
       (st = dalloc((void **)&s, sizeof(double2) * nalm * B)) || (st = dalloc((void **)&sdf, sizeof(float4) * nalm * B)) ||
@@ -160,7 +203,7 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
       (st = dalloc((void **)&bstate, sizeof(int) * 2)) || (st = dalloc((void **)&last, sizeof(wf_iter_record) * B)))
     return st;
   if (!make_tc_map(&maps.A, lamA, RPp, nalm, 128) || !make_tc_map(&maps.X, XT, 32, nXT / 32, (unsigned)Nc) ||
-      !make_tc_map(&maps.T, lamT, 32, (size_t)nchunks * RPp, 128) ||
+      !make_tc_map(&maps.T, mode == 1 ? lamT : lamTs, 32, (mode == 1 ? (size_t)nchunks : band_chunks) * RPp, 128) ||
       !make_tc_map(&maps.S, SPT, 32, (size_t)nchunks * Nc, (unsigned)Nc)) {
     set_error("batched engine: cuTensorMapEncodeTiled failed");
     return WF_ECUDA;
@@ -174,6 +217,8 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ENG_CUDA(cudaMemcpyAsync(atiles, ana.data(), sizeof(int4) * ana.size(), cudaMemcpyHostToDevice, stream));
   ENG_CUDA(cudaMemcpyAsync(tstiles, syn.data(), sizeof(int2) * syn.size(), cudaMemcpyHostToDevice, stream));
   ENG_CUDA(cudaMemcpyAsync(offTc, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, stream));
+  if (mode == 0)
+    ENG_CUDA(cudaMemcpyAsync(chunk_info, cinfo.data(), sizeof(int4) * cinfo.size(), cudaMemcpyHostToDevice, stream));
   {
     // state rows in the analysis table's order: (m, parity of l - m, (l - m) / 2)
     std::vector<int> a_of_r(nalm);
@@ -182,7 +227,7 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
       for (int p = 0; p < 2; ++p)
         for (int l = m + p; l <= lmax; l += 2) a_of_r[r++] = (int)((size_t)m * (2 * lmax + 1 - m) / 2 + l);
     ENG_CUDA(cudaMemcpyAsync(alm_of_row, a_of_r.data(), sizeof(int) * nalm, cudaMemcpyHostToDevice, stream));
-    ENG_CUDA(cudaStreamSynchronize(stream));   // a_of_r is released at the end of this block
+    ENG_CUDA(cudaStreamSynchronize(stream));   // a_of_r and cinfo are released by then
   }
   launch_hi_table(geo->d_twf, tw2, geo->n_tw, stream);
   launch_hi_table(geo->d_Bf, Bf2, geo->n_B, stream);
@@ -198,7 +243,7 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ENG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) * B, stream));
   ENG_CUDA(cudaMemsetAsync(active, 0, sizeof(int) * B, stream));
   ENG_CUDA(cudaMemsetAsync(last, 0, sizeof(wf_iter_record) * B, stream));
-  launch_lam_tc_tables(geo->d_x, geo->legdf_args(), lmax, RP, RPp, offTc, lamA, lamT, stream);
+  launch_lam_tc_tables(geo->d_x, geo->legdf_args(), lmax, RP, RPp, offTc, lamA, mode == 1 ? lamT : nullptr, stream);
   launch_batch_state(args(), bstate, stream);
   ENG_CUDA(cudaGetLastError());
   ENG_CUDA(cudaStreamSynchronize(stream));
@@ -251,9 +296,10 @@ wf_status Engine::load_slot(int b, const double *dsrc, int d_on_device, const do
   const int lmax = geo->lmax;
   const size_t npix = geo->npix;
   launch_batch_zero_slot(args(), tc_args(), nchunks, b, stream);
-  ENG_CUDA(cudaMemcpyAsync(d + b * npix, dsrc, sizeof(double) * npix,
+  // d, w: one staging slot, converted into the slot's FP32 (d, w) in stream order
+  ENG_CUDA(cudaMemcpyAsync(d, dsrc, sizeof(double) * npix,
                            d_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
-  ENG_CUDA(cudaMemcpyAsync(w + b * npix, wsrc_dev, sizeof(double) * npix, cudaMemcpyDeviceToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(w, wsrc_dev, sizeof(double) * npix, cudaMemcpyDeviceToDevice, stream));
   launch_batch_convert_slot(args(), b, stream);
   ENG_CUDA(cudaMemcpyAsync(cl + (size_t)b * (lmax + 1), cl_host, sizeof(double) * (lmax + 1), cudaMemcpyHostToDevice,
                            stream));
@@ -269,8 +315,8 @@ wf_status Engine::load_slot_host(int b, const double *d_host, const double *w_ho
   const int lmax = geo->lmax;
   const size_t npix = geo->npix;
   launch_batch_zero_slot(args(), tc_args(), nchunks, b, stream);
-  ENG_CUDA(cudaMemcpyAsync(d + b * npix, d_host, sizeof(double) * npix, cudaMemcpyHostToDevice, stream));
-  ENG_CUDA(cudaMemcpyAsync(w + b * npix, w_host, sizeof(double) * npix, cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(d, d_host, sizeof(double) * npix, cudaMemcpyHostToDevice, stream));
+  ENG_CUDA(cudaMemcpyAsync(w, w_host, sizeof(double) * npix, cudaMemcpyHostToDevice, stream));
   launch_batch_convert_slot(args(), b, stream);
   ENG_CUDA(cudaMemcpyAsync(cl + (size_t)b * (lmax + 1), cl_host, sizeof(double) * (lmax + 1), cudaMemcpyHostToDevice,
                            stream));
@@ -305,7 +351,8 @@ wf_status Engine::step() {
     ENG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < graph_iters; ++i)
       launch_batch_iteration(args(), tc_args(), maps, geo->rclass.data(), (int)geo->rclass.size(),
-                             ring_groups.empty() ? nullptr : ring_groups.data(), bstate, stream);
+                             ring_groups.empty() ? nullptr : ring_groups.data(), bstate, stream, bands.data(),
+                             (int)bands.size());
     ENG_CUDA(cudaStreamEndCapture(stream, &g));
     cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
     cudaGraphDestroy(g);

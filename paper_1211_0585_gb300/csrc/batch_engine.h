@@ -22,8 +22,10 @@ struct TcMaps {
 
 bool make_tc_map(CUtensorMap *map, const float *base, unsigned long long inner, unsigned long long rows,
                  unsigned box_rows);
-// which = 0: FT -> XT and the analysis GEMM with Eq. 4; 1: the synthesis GEMM
-void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which);
+// which = 0: FT -> XT and the analysis GEMM with Eq. 4; 1: the synthesis GEMM (with a
+// streamed synthesis table, band by band)
+void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which,
+                           const SynBand *bands, int nbands);
 
 struct Engine {
   Plan *geo = nullptr;  // tables of the shape (not owned)
@@ -36,6 +38,10 @@ struct Engine {
   float2 *tw2 = nullptr, *Bf2 = nullptr;   // FP32 twiddle / Bluestein tables
   // tensor-core Legendre stage
   float *lamA = nullptr, *lamT = nullptr, *XT = nullptr, *SPT = nullptr;
+  // streamed synthesis table (when both tables do not fit): scratch for one band of m at a time
+  float *lamTs = nullptr;
+  int4 *chunk_info = nullptr;
+  std::vector<SynBand> bands;
   int4 *atiles = nullptr;
   int2 *tstiles = nullptr;
   int *offTc = nullptr;

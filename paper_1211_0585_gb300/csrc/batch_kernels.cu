@@ -375,7 +375,7 @@ void launch_batch_export_slot(const BatchArgs &a, int b, cudaStream_t s) {
 // FP32 copies of slot b's data and inverse noise for the ring stage
 __global__ void bconvert_slot_kernel(const BatchArgs A, int b) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.npix; i += (long long)gridDim.x * blockDim.x) {
-    A.dw32[(size_t)b * A.npix + i] = make_float2((float)A.d[(size_t)b * A.npix + i], (float)A.w[(size_t)b * A.npix + i]);
+    A.dw32[(size_t)b * A.npix + i] = make_float2((float)A.d[i], (float)A.w[i]);   // d, w: one staging slot
   }
 }
 
@@ -428,11 +428,11 @@ void launch_batch_ring_class(const BatchArgs &a, const RingClass &c, int G, cuda
 }
 
 void launch_batch_iteration(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, const RingClass *cls, int ncls,
-                            const int *groups, int *bstate, cudaStream_t s) {
+                            const int *groups, int *bstate, cudaStream_t s, const SynBand *bands, int nbands) {
   for (int c = 0; c < ncls; ++c) launch_batch_ring_class(a, cls[c], groups ? groups[c] : 0, s);
   bfilter_kernel<<<a.B, 256, 0, s>>>(a);
-  launch_batch_gemms_tc(a, t, maps, s, 0);   // FT -> XT, analysis GEMM, Eq. 4
-  launch_batch_gemms_tc(a, t, maps, s, 1);   // synthesis GEMM
+  launch_batch_gemms_tc(a, t, maps, s, 0, bands, nbands);   // FT -> XT, analysis GEMM, Eq. 4
+  launch_batch_gemms_tc(a, t, maps, s, 1, bands, nbands);   // synthesis GEMM
   bctl_kernel<<<a.B, 256, 0, s>>>(a);
   bstate_kernel<<<1, kBatchMax, 0, s>>>(a, bstate);
 }

@@ -161,8 +161,9 @@ __device__ __forceinline__ void mma_chunk(uint32_t dmain, uint32_t dcorr, uint8_
 // ---------------------------------------------------------------- tables
 // One thread per (m, k): the double-float recurrence from the start values
 // writes lambda_lm(x_k) (rounded to 22 bits, 0 below l_start) into both table
-// layouts; rows of the transposed layout are written 32 values at a time from
-// registers.
+// layouts (only the analysis layout when lamT is nullptr: the synthesis rows are
+// then rebuilt per band, lamt_band_kernel); rows of the transposed layout are
+// written 32 values at a time from registers.
 __global__ void lam_tc_tables_kernel(const double *xk, const LegDfArgs D, int lmax, int RP, int RPp,
                                      const int *offTc, float *lamA, float *lamT) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,7 +176,7 @@ __global__ void lam_tc_tables_kernel(const double *xk, const LegDfArgs D, int lm
     for (int p = 0; p < 2; ++p) {
       const int np = n_par(m, p, lmax);
       for (int i = 0; i < np; ++i) lamA[(base + (p ? n0 + i : i)) * (size_t)RPp + k] = 0.f;
-      for (int ic = 0; ic < (np + 31) / 32; ++ic) {
+      for (int ic = 0; lamT && ic < (np + 31) / 32; ++ic) {
         float4 *dst = reinterpret_cast<float4 *>(lamT + ((size_t)(offTc[2 * m + p] + ic) * RPp + k) * 32);
         for (int j = 0; j < 8; ++j) dst[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -208,13 +209,32 @@ __global__ void lam_tc_tables_kernel(const double *xk, const LegDfArgs D, int lm
     lamA[(base + (p ? n0 + i : i)) * (size_t)RPp + k] = v;
     buf[p][i & 31] = v;
     const int np = n_par(m, p, lmax);
-    if ((i & 31) == 31 || i == np - 1) {   // a chunk of 32 values of i is complete: write its row
+    if (lamT && ((i & 31) == 31 || i == np - 1)) {   // a chunk of 32 values of i is complete: write its row
       for (int j = (i & 31) + 1; j < 32; ++j) buf[p][j] = 0.f;
       float4 *dst = reinterpret_cast<float4 *>(lamT + ((size_t)(offTc[2 * m + p] + (i >> 5)) * RPp + k) * 32);
 #pragma unroll
       for (int j = 0; j < 8; ++j) dst[j] = make_float4(buf[p][4 * j], buf[p][4 * j + 1], buf[p][4 * j + 2], buf[p][4 * j + 3]);
     }
   }
+}
+
+// Streamed synthesis table: the rows of the chunks [q0, q0 + gridDim.x) in the
+// synthesis order (32 values of i contiguous per ring pair) from the analysis
+// table (ring pairs contiguous per i), into the scratch from chunk q0. One CTA
+// per (chunk, 32 ring pairs): a 32 x 32 transpose through shared memory; the
+// values are lamA's, so the GEMM sees the same operand as with the resident
+// table. Chunks of m above the live band limit are skipped (the GEMM skips them).
+__global__ void __launch_bounds__(256) lamt_band_kernel(const TcArgs T, int q0, const int *bstate) {
+  __shared__ float tile[32][33];
+  const int q = q0 + blockIdx.x, kb = blockIdx.y;
+  const int4 ci = T.chunk_info[q];
+  if (ci.z > bstate[0]) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < 32; j += 8)
+    tile[j][tx] = j < ci.y ? T.lamA[((size_t)ci.x + j) * T.RPp + 32 * kb + tx] : 0.f;
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8)
+    T.lamTs[((size_t)(q - T.qbase) * T.RPp + 32 * kb + r) * 32 + tx] = tile[tx][r];
 }
 
 // ---------------------------------------------------------------- FT -> XT
@@ -536,7 +556,7 @@ __global__ void __launch_bounds__(kSynThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int2 tile = T.stiles[blockIdx.x];
+  const int2 tile = T.stiles[T.tile0 + blockIdx.x];
   const int m = tile.x, k0 = tile.y;
   const int B = A.B, RP = A.RP, Nc = T.Nc;
   const int Lact = A.bstate[0];
@@ -580,7 +600,7 @@ __global__ void __launch_bounds__(kSynThreads, 1)
       const int p = qi < nc0 ? 0 : 1, ic = p ? nc0 + nc1 - 1 - qi : nc0 - 1 - qi;
       const long long q = (long long)T.offTc[2 * m + p] + ic;
       tc::mbar_arrive_expect_tx(&full[s], kTileBytes + bbytes);
-      tc::tma_load_2d(Smem::raw(tsm, s, 0), &mapT, 0, (int)(q * T.RPp + k0), &full[s]);
+      tc::tma_load_2d(Smem::raw(tsm, s, 0), &mapT, 0, (int)((q - T.qbase) * T.RPp + k0), &full[s]);
       tc::tma_load_2d(Smem::raw(tsm, s, 1), &mapS, 0, (int)(q * Nc), &full[s]);
       issued = qi + 1;
     }
@@ -710,19 +730,30 @@ bool make_tc_map(CUtensorMap *map, const float *base, unsigned long long inner, 
 }
 
 void launch_lam_tc_tables(const double *x, const LegDfArgs &D, int lmax, int RP, int RPp, const int *offTc,
-                          float *lamA, float *lamT, cudaStream_t s) {
+                          float *lamA, float *lamT, cudaStream_t s) {  // lamT nullptr: analysis table only
   const long long n = (long long)(lmax + 1) * RPp;
   lam_tc_tables_kernel<<<(int)((n + 127) / 128), 128, 0, s>>>(x, D, lmax, RP, RPp, offTc, lamA, lamT);
 }
 
-void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which) {
+void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which,
+                           const SynBand *bands, int nbands) {
   raise_smem_cap(reinterpret_cast<const void *>(bana_tc_kernel));
   raise_smem_cap(reinterpret_cast<const void *>(bsyn_tc_kernel));
   if (which == 0) {
     xt_kernel<<<dim3(t.nkc, a.lmax + 1), 256, 0, s>>>(a, t);
     bana_tc_kernel<<<t.natiles, kAnaThreads, gemm_smem(), s>>>(maps.A, maps.X, a, t);
-  } else {
+  } else if (!t.lamTs) {
     bsyn_tc_kernel<<<t.nstiles, kSynThreads, gemm_smem(), s>>>(maps.T, maps.S, a, t);
+  } else {
+    // band by band: rebuild the band's synthesis-ordered rows, then its GEMM tiles
+    for (int i = 0; i < nbands; ++i) {
+      const SynBand &b = bands[i];
+      TcArgs tb = t;
+      tb.qbase = b.q0;
+      tb.tile0 = b.tile0;
+      lamt_band_kernel<<<dim3(b.q1 - b.q0, t.nkc), 256, 0, s>>>(tb, b.q0, a.bstate);
+      bsyn_tc_kernel<<<b.tile1 - b.tile0, kSynThreads, gemm_smem(), s>>>(maps.T, maps.S, a, tb);
+    }
   }
 }
 

@@ -321,9 +321,6 @@ wf_status Plan::alloc_work() {
   if ((st = dalloc((void **)&d_s, sizeof(double2) * nalm))) return st;
   if ((st = dalloc((void **)&d_gain, sizeof(double) * npix))) return st;
   if ((st = dalloc((void **)&d_gainlam, sizeof(double) * R))) return st;
-  if ((st = dalloc((void **)&d_pmap, sizeof(double) * 2 * npix))) return st;
-  if ((st = dalloc((void **)&d_palm, sizeof(double2) * 2 * nalm))) return st;
-  if ((st = dalloc((void **)&d_ppart, sizeof(double) * 2 * (lmax + 1)))) return st;
   {
     std::vector<double> neg(R, -1.0);
     WF_CUDA(cudaMemcpy(d_gainlam, neg.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
@@ -451,6 +448,7 @@ wf_status wf_options_default(wf_options *o) {
   o->batch_slots = kBatchMax;
   o->legendre_table_bytes = (size_t)8 << 30;
   o->posterior_grad = 1;
+  o->synthesis_table = -1;
   o->stream = nullptr;
   return WF_OK;
 }
@@ -735,6 +733,12 @@ wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_d
 // synthesis, W (d - Y a) and W d, two analyses, per-m norms summed in order.
 static wf_status posterior_grad(Plan *P, cudaStream_t s, double *rel) {
   const long long npix = P->npix, nalm = P->nalm;
+  if (!P->d_pmap) {  // on first use: plans that never report it (mixed) do not hold the buffers
+    wf_status st;
+    if ((st = P->dalloc((void **)&P->d_pmap, sizeof(double) * 2 * npix))) return st;
+    if ((st = P->dalloc((void **)&P->d_palm, sizeof(double2) * 2 * nalm))) return st;
+    if ((st = P->dalloc((void **)&P->d_ppart, sizeof(double) * 2 * (P->lmax + 1)))) return st;
+  }
   double *ya = P->d_pmap, *wd = P->d_pmap + npix;
   double2 *ta = P->d_palm, *tb = P->d_palm + nalm;
   LegArgs la = P->leg_args();

@@ -169,7 +169,9 @@ size_t fp64_bytes(int nside, int lmax) {
   wf_options o;
   wf_options_default(&o);
   const size_t tab = lam_table_rows(lmax) * (size_t)((2 * nside + 31) / 32 * 32) * 16;
-  return engine_bytes(nside, lmax, 1) + (tab <= o.legendre_table_bytes ? tab : 0);
+  const size_t npix = 12 * (size_t)nside * nside, nalm = (size_t)(lmax + 1) * (lmax + 2) / 2;
+  const size_t posterior = 2 * npix * sizeof(double) + 2 * nalm * 16;  // rel_posterior_grad buffers
+  return engine_bytes(nside, lmax, 1) + posterior + (tab <= o.legendre_table_bytes ? tab : 0);
 }
 
 size_t bytes_in_use(wf_server_s *S) {

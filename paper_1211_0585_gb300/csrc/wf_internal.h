@@ -184,6 +184,18 @@ struct TcArgs {
   const int *offTc;          // [2 (lmax+1)] first 32-wide i chunk of (m, parity)
   float *XT, *SPT;           // analysis / synthesis B operands
   int *err;                  // set when a pipeline wait gave up
+  // streamed synthesis table: a launch covers synthesis tiles from tile0 and reads the
+  // synthesis-ordered rows of chunks from qbase, rebuilt from lamA into a scratch array
+  int tile0, qbase;
+  const int4 *chunk_info;    // [nchunks] (first lamA row of the chunk, rows in it, m, 0)
+  const float *lamA;
+  float *lamTs;              // scratch of the streamed synthesis table (nullptr: resident lamT)
+};
+
+// A band of m whose synthesis table is rebuilt and used in one step: chunks
+// [q0, q1) and synthesis tiles [tile0, tile1).
+struct SynBand {
+  int q0, q1, tile0, tile1;
 };
 
 void launch_lam_tc_tables(const double *x, const LegDfArgs &D, int lmax, int RP, int RPp, const int *offTc,
@@ -191,7 +203,7 @@ void launch_lam_tc_tables(const double *x, const LegDfArgs &D, int lmax, int RP,
 struct TcMaps;
 // groups: slots per ring-stage CTA for each class (0 or nullptr: the default rule)
 void launch_batch_iteration(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, const RingClass *cls, int ncls,
-                            const int *groups, int *bstate, cudaStream_t s);
+                            const int *groups, int *bstate, cudaStream_t s, const SynBand *bands, int nbands);
 void launch_batch_ring_class(const BatchArgs &a, const RingClass &c, int G, cudaStream_t s);
 bool batch_ring_group_ok(int logM, int G);
 void launch_batch_state(const BatchArgs &a, int *bstate, cudaStream_t s);

@@ -11,7 +11,8 @@ from gpu_util import FP64_PATHS, dev, host_alm
 
 pytestmark = pytest.mark.gpu
 
-CASES = [(1, 2), (2, 6), (4, 8), (4, 13), (8, 16), (16, 32), (16, 64), (32, 64), (64, 128), (64, 40)]
+CASES = [(1, 2), (2, 6), (4, 8), (4, 13), (8, 16), (16, 32), (16, 64), (32, 64), (64, 128), (64, 40),
+         (1, 0), (1, 4), (2, 8), (8, 0), (8, 32)]  # degenerate: lmax 0, lmax = 4 nside
 
 
 PRECS = list(FP64_PATHS)
