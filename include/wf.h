@@ -96,6 +96,11 @@ typedef struct {
                             at lmax = 2 Nside) */
   int posterior_grad;    /* 1: wf_solve on the FP64 paths also reports rel_posterior_grad (one synthesis
                             and two analyses after the solve) (1) */
+  int refine_iters;      /* WF_PREC_MIXED: after the batched solve of each right-hand side, up to this many
+                            FP64 iterations (double-float kernels) at lambda = 1 from its result, stopping
+                            early once the relative increment is <= refine_tol; the result, chi^2 and
+                            rel_posterior_grad are then the refined ones (0 = none) (0) */
+  double refine_tol;     /* stop rule of the refinement (0 = run all refine_iters) (0) */
   int synthesis_table;   /* batched engine: 1 keeps the synthesis-ordered FP32 Legendre table resident;
                             0 rebuilds it band by band of m from the analysis table every iteration (half
                             the table memory, one transpose pass more); -1 chooses 1 when the engine fits

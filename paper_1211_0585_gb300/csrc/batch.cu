@@ -438,9 +438,17 @@ wf_status solve_mixed(Plan *P, int nrhs, const double *dsrc, int d_on_device, do
       ENG_CUDA(cudaMemcpyAsync(alm_out + (size_t)i * 2 * P->nalm, E->s + (size_t)b * P->nalm,
                                sizeof(double2) * P->nalm,
                                alm_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, E->stream));
-      fill_stats(stats ? stats + i : nullptr, E->h_ctl[b], E->h_last[b], P->n_obs, ms);
-      any_not_conv |= !E->h_ctl[b].converged;
+      wf_stats tmp{};
+      wf_stats *sr = stats ? stats + i : &tmp;
+      fill_stats(sr, E->h_ctl[b], E->h_last[b], P->n_obs, ms);
       any_numeric |= E->h_ctl[b].numeric != 0;
+      if (P->opt.refine_iters > 0 && !E->h_ctl[b].numeric) {  // FP64 iterations from the mixed result
+        const double *from = reinterpret_cast<const double *>(E->s + (size_t)b * P->nalm);
+        if ((st = refine_fp64(P, dsrc + (size_t)i * P->npix, d_on_device, from, alm_out + (size_t)i * 2 * P->nalm,
+                              alm_on_device, sr)))
+          return st;
+      }
+      any_not_conv |= !sr->converged;
       if ((st = E->release_slot(b))) return st;
       ++finished;
       if ((st = admit(b))) return st;

@@ -449,6 +449,8 @@ wf_status wf_options_default(wf_options *o) {
   o->legendre_table_bytes = (size_t)8 << 30;
   o->posterior_grad = 1;
   o->synthesis_table = -1;
+  o->refine_iters = 0;
+  o->refine_tol = 0.0;
   o->stream = nullptr;
   return WF_OK;
 }
@@ -461,7 +463,8 @@ static wf_status check_options(const wf_options *o) {
   if (!(o->tol >= 0.0) || o->max_iter < 1 || o->l_iter0 < 1 || o->lmax_margin < 0 || o->min_level_iters < 1 ||
       o->max_level_iters < 1 || o->graph_iters < 1 || o->graph_iters > 1024 || o->batch_slots < 1 ||
       o->batch_slots > kBatchMax || !(o->plateau_eps >= 0.0) ||
-      !(o->final_dchi2 >= 0.0)) {
+      !(o->final_dchi2 >= 0.0) || o->refine_iters < 0 || !(o->refine_tol >= 0.0) || o->synthesis_table < -1 ||
+      o->synthesis_table > 1 || (o->posterior_grad != 0 && o->posterior_grad != 1)) {
     set_error("wf_options: value out of range");
     return WF_EINVAL;
   }
@@ -599,7 +602,9 @@ wf_status wf_plan_set_options(wf_plan_t plan, const wf_options *opt) {
   if (!plan || !opt) { set_error("wf_plan_set_options: NULL"); return WF_EINVAL; }
   if (check_options(opt)) return WF_EINVAL;
   Plan *P = static_cast<Plan *>(plan);
-  const bool regraph = opt->graph_iters != P->opt.graph_iters || opt->stream != P->opt.stream;
+  // the captured iteration holds the kernels of the precision and the launch shape
+  const bool regraph = opt->graph_iters != P->opt.graph_iters || opt->stream != P->opt.stream ||
+                       opt->precision != P->opt.precision;
   P->opt = *opt;
   wf_status st = P->ensure_hist(opt->max_iter + 1);
   if (st) return st;
@@ -769,6 +774,51 @@ static wf_status posterior_grad(Plan *P, cudaStream_t s, double *rel) {
 
 static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *alm_out, int alm_on_device,
                             const double *alm_init, wf_stats *stats, wf_iter_record *records, int max_records,
+                            int *n_records);
+
+}  // extern "C"
+
+namespace wfk {
+
+wf_status refine_fp64(Plan *P, const double *d, int d_on_device, const double *alm_dev, double *alm_out,
+                      int alm_on_device, wf_stats *stats) {
+  const wf_options saved = P->opt;
+  if (P->graph_exec && P->graph_prec != WF_PREC_FP64) {  // a graph of other kernels
+    cudaGraphExecDestroy(P->graph_exec);
+    P->graph_exec = nullptr;
+  }
+  wf_status hs = P->ensure_hist(saved.refine_iters + 1);  // the last record is read back
+  if (hs) return hs;
+  P->opt.precision = WF_PREC_FP64;
+  P->opt.cooling = 0;
+  P->opt.max_iter = saved.refine_iters;
+  P->opt.tol = saved.refine_tol;
+  wf_stats rs{};
+  wf_status st = solve_impl(P, d, d_on_device, alm_out, alm_on_device, alm_dev, &rs, nullptr, 0, nullptr);
+  P->opt = saved;
+  if (st == WF_ENOTCONVERGED) st = WF_OK;  // at most refine_iters iterations by design
+  if (st == WF_OK && stats) {
+    stats->iters += rs.iters;
+    stats->converged = stats->converged || rs.converged;
+    stats->lambda_final = 1.0;
+    stats->lmax_sht_final = P->lmax;
+    stats->chi2 = rs.chi2;
+    stats->chi2_prior = rs.chi2_prior;
+    stats->chi2_noise = rs.chi2_noise;
+    stats->chi2_per_dof = rs.chi2_per_dof;
+    stats->rel_increment = rs.rel_increment;
+    stats->ms_device += rs.ms_device;
+    stats->rel_posterior_grad = rs.rel_posterior_grad;
+  }
+  return st;
+}
+
+}  // namespace wfk
+
+extern "C" {
+
+static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *alm_out, int alm_on_device,
+                            const double *alm_init, wf_stats *stats, wf_iter_record *records, int max_records,
                             int *n_records) {
   if (P->opt.precision == WF_PREC_MIXED) {
     if (n_records) *n_records = 0;
@@ -782,9 +832,8 @@ static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *a
   const double lam0 = P->opt.cooling ? P->lambda_of(P->opt.l_iter0) : 1.0;
   const int lb = P->opt.l_iter0 + P->opt.lmax_margin;
   const int lsht0 = (lam0 <= 1.0 || !P->opt.band_limit) ? P->lmax : (lb < P->lmax ? lb : P->lmax);
-  if (alm_init) {
-    const auto k2 = alm_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    WF_CUDA(cudaMemcpyAsync(P->d_s, alm_init, sizeof(double2) * P->nalm, k2, s));
+  if (alm_init) {  // host or device (the refinement of a mixed solve starts from device state)
+    WF_CUDA(cudaMemcpyAsync(P->d_s, alm_init, sizeof(double2) * P->nalm, cudaMemcpyDefault, s));
     LegArgs la = P->leg_args();
     la.lsht = lsht0;
     la.alm_in = P->d_s;
@@ -805,6 +854,7 @@ static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *a
     cudaError_t e = cudaGraphInstantiate(&P->graph_exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
+    P->graph_prec = P->opt.precision;
   }
   const int max_launch = (P->opt.max_iter + P->opt.graph_iters - 1) / P->opt.graph_iters + 1;
   for (int it = 0; it < max_launch; ++it) {

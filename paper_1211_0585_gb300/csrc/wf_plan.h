@@ -69,6 +69,7 @@ struct Plan : wf_plan_s {
   bool fs_valid = false;
   int fs_lsht = -1;
   cudaGraphExec_t graph_exec = nullptr;
+  int graph_prec = -1;                  // precision whose kernels graph_exec holds
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   ~Plan() override;
@@ -101,6 +102,12 @@ struct Plan : wf_plan_s {
 // cached Eq. 3 gains and the captured iteration graph are dropped. Host
 // arrays are read before it returns.
 wf_status plan_rebind(Plan *P, const double *cl, const double *w, double tau, long long n_obs);
+
+// FP64 refinement of a mixed result: up to opt.refine_iters double-float
+// iterations at lambda = 1 from alm_dev (device a_lm), written to alm_out; the
+// refined figures replace those of stats (iterations and time are added).
+wf_status refine_fp64(Plan *P, const double *d, int d_on_device, const double *alm_dev, double *alm_out,
+                      int alm_on_device, wf_stats *stats);
 
 // Mixed-precision solves through the plan's batched engine (batch.cu).
 wf_status solve_mixed(Plan *P, int nrhs, const double *d, int d_on_device, double *alm_out, int alm_on_device,

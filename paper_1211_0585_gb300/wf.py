@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("final_dchi2", ctypes.c_double), ("min_level_iters", ctypes.c_int),
                 ("max_level_iters", ctypes.c_int), ("graph_iters", ctypes.c_int),
                 ("batch_slots", ctypes.c_int), ("legendre_table_bytes", ctypes.c_size_t),
-                ("posterior_grad", ctypes.c_int), ("synthesis_table", ctypes.c_int),
+                ("posterior_grad", ctypes.c_int), ("refine_iters", ctypes.c_int), ("refine_tol", ctypes.c_double), ("synthesis_table", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 

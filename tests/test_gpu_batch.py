@@ -108,3 +108,32 @@ def test_streamed_synthesis_table(nside, lmax):
         assert status == wf.WF_OK
         out.append(alm)
     assert np.array_equal(out[0], out[1])
+
+
+def test_fp64_refinement_of_mixed_solves():
+    """refine_iters: FP64 iterations at lambda = 1 from each mixed result remove
+    the FP32 floor of the mixed solve. The refined a_lm agree with the FP64
+    solve far below the mixed bar, and their posterior residual (Eq. 2 on the
+    grid) falls from the mixed level to the FP64 solve's."""
+    nside, lmax = 16, 32
+    p, _ = problem("wmap", seed=13, nside=nside, lmax=lmax)
+    D = rhs_set(p, 3)
+    P64 = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(precision=0, tol=1e-11))
+    ref = [P64.solve(D[i])[0] for i in range(3)]
+    Pm = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(precision=wf.WF_PREC_MIXED, tol=1e-6))
+    mixed, _, status = Pm.solve_batch(D)
+    assert status == wf.WF_OK
+    Pr = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask,
+                 wf.options(precision=wf.WF_PREC_MIXED, tol=1e-6, refine_iters=4000, refine_tol=1e-11))
+    refined, stats, status = Pr.solve_batch(D)
+    assert status == wf.WF_OK
+    for i in range(3):
+        err_mixed = O.rel_l2(mixed[i], ref[i], lmax)
+        err_ref = O.rel_l2(refined[i], ref[i], lmax)
+        assert err_mixed > 1e-9
+        assert err_ref < 1e-8 and err_ref < 1e-2 * err_mixed
+        pr_mixed = O.posterior_residual(nside, lmax, mixed[i], p.cl, p.noise_var, p.mask, D[i])
+        pr_ref = O.posterior_residual(nside, lmax, refined[i], p.cl, p.noise_var, p.mask, D[i])
+        assert pr_ref < 1e-2 * pr_mixed
+        assert abs(stats[i]["rel_posterior_grad"] - pr_ref) <= 1e-6 * pr_ref + 1e-13
+        assert stats[i]["converged"] == 1
