@@ -304,7 +304,8 @@ def mixed_batched(prob, dmap, P64, out64, flush, nrhs=64):
     Pm = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask,
                  wf.options(precision=wf.WF_PREC_MIXED, tol=TOL, max_iter=20000, batch_slots=min(nrhs, 64)))
     outm = torch.empty((nrhs, 2 * P64.nalm), dtype=torch.float64, device="cuda")
-    Pm.solve_batch(D[:1].data_ptr(), on_device=True, alm_out=outm.data_ptr(), nrhs=1)   # engine + table build
+    # engine, tables and ring-stage autotuning for nrhs slots (as a server loads its model), then the timed run
+    Pm.solve_batch(D.data_ptr(), on_device=True, alm_out=outm.data_ptr(), nrhs=nrhs)
     flush.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -396,7 +396,8 @@ static void fill_stats(wf_stats *st, const Ctl &c, const wf_iter_record &r, long
 wf_status solve_mixed(Plan *P, int nrhs, const double *dsrc, int d_on_device, double *alm_out, int alm_on_device,
                       wf_stats *stats) {
   const int want = std::min(nrhs, P->opt.batch_slots);
-  if (!P->engine || P->engine->B != want) {
+  // an engine serves every batch up to its slot count (rounded to 8): rebuilt only to grow
+  if (!P->engine || P->engine->B < round_up(want, 8)) {
     delete P->engine;
     P->engine = new (std::nothrow) Engine();
     if (!P->engine) { set_error("out of host memory"); return WF_ENOMEM; }
