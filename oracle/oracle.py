@@ -27,7 +27,7 @@ What it computes, in the paper's order and notation:
   to 1); the band limit lmax_SHT = l_iter + 100 while lambda > 1; the stop
   rule at lambda = 1.
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
   the ratio that sets lambda is C_l / (tau Omega), clamped to >= 1, so that
   the harmonic filter f_l has its half-power point at l_iter; sigma_chi2 =
   sqrt(2 n_obs); the plateau test is |chi2_k - chi2_{k-1}| < eps * sigma_chi2
