@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--profile-fp64", type=int, nargs=3, metavar=("NSIDE", "LMAX", "ITERS"), default=None,
                     help="profiling target: ITERS full-band FP64 iterations (wf_profile_iterations) of a "
                          "WMAP-shaped problem at NSIDE / LMAX, the plan's default Legendre form")
+    ap.add_argument("--profile-shape", type=int, nargs=2, metavar=("NSIDE", "LMAX"), default=None,
+                    help="shape of --profile-batch (default: the bench's Nside 512 / lmax 1024)")
     ap.add_argument("--profile-batch", type=int, nargs=2, metavar=("NRHS", "ITERS"), default=None,
                     help="profiling target: ITERS full-band iterations of the batched engine on NRHS right-hand "
                          "sides of the WMAP-shaped problem (cooling off), one text line, no JSON")
@@ -178,7 +180,11 @@ def run_ours(args):
     value = world * args.steps / total
     graph_iters = opts.graph_iters
     per_iter = P.kernels_per_iteration()
-    launches_per_solve = [math.ceil(i / graph_iters) * graph_iters * per_iter for i in iters]
+    # the iterations' graphs (controller-stopped launches return at once but count), then the posterior
+    # gradient: one synthesis, the pixel kernel, two analyses, the norms (r = ring-stage launches)
+    r = per_iter - 2
+    posterior = (5 + 3 * r) if opts.posterior_grad else 0
+    launches_per_solve = [math.ceil(i / graph_iters) * graph_iters * per_iter + posterior for i in iters]
 
     # SHT pair at full lmax (alm2map + map2alm), events on the stream
     m2 = torch.empty_like(dmap)
@@ -486,13 +492,15 @@ def run_reference(args):
 DEFAULT_LEVELS = [[6.1793721184416155, 120, 5], [1.575, 140, 4], [1.0, 1024, 342]]
 
 
-def profile_batch(nrhs, iters, seed):
+def profile_batch(nrhs, iters, seed, shape=None):
     """A fixed amount of full-band batched work for ncu captures: every
     iteration runs at lambda = 1 and lmax_SHT = lmax (cooling off)."""
     import torch
+    from paper_1211_0585_gb300 import inputs as I
     from paper_1211_0585_gb300 import wf
-    prob = make_problem(seed)
-    P64 = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask, wf.options())
+    NSIDE, LMAX = shape if shape else (globals()["NSIDE"], globals()["LMAX"])
+    prob = I.wmap_problem(seed=seed, nside=NSIDE, lmax=LMAX)
+    P64 = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask, wf.options(legendre_table_bytes=0))
     Pm = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask,
                  wf.options(tol=0.0, max_iter=iters, cooling=0, precision=wf.WF_PREC_MIXED,
                             batch_slots=min(64, nrhs)))
@@ -536,7 +544,7 @@ def main():
         profile_fp64(*args.profile_fp64, args.seed)
         return
     if args.profile_batch:
-        profile_batch(args.profile_batch[0], args.profile_batch[1], args.seed)
+        profile_batch(args.profile_batch[0], args.profile_batch[1], args.seed, args.profile_shape)
         return
     if args.impl == "reference":
         run_reference(args)
