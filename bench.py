@@ -56,6 +56,22 @@ def parse():
     return ap.parse_args()
 
 
+def job_rate(local_seconds, steps, dist=None, device=None):
+    """Whole-job rate of `steps` solves on every rank: the slowest rank's time
+    (max over ranks) sets it, value = world * steps / that time; a barrier
+    closes the timed region on every rank. Returns (value, max seconds)."""
+    total = float(local_seconds)
+    world = 1
+    if dist is not None:
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([total], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+        dist.barrier()
+    return world * steps / total, total
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -171,13 +187,7 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1) / 1e3)
             iters.append(st["iters"])
     torch.cuda.synchronize()
-    total = sum(times)
-    if dist:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-        dist.barrier()
-    value = world * args.steps / total
+    value, total = job_rate(sum(times), args.steps, dist, device="cuda")
     graph_iters = opts.graph_iters
     per_iter = P.kernels_per_iteration()
     # the iterations' graphs (controller-stopped launches return at once but count), then the posterior
