@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-mixed and serving measurements")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--fp64-form", choices=["table", "recurrence", "native"], default="table",
+                    help="form of the FP64 solve: double-float kernels reading the precomputed lambda table "
+                         "(the plan's default where it fits), the same running the recurrence, or native FP64")
     ap.add_argument("--profile-fp64", type=int, nargs=3, metavar=("NSIDE", "LMAX", "ITERS"), default=None,
                     help="profiling target: ITERS full-band FP64 iterations (wf_profile_iterations) of a "
                          "WMAP-shaped problem at NSIDE / LMAX, the plan's default Legendre form")
@@ -54,6 +57,9 @@ def parse():
                     help="profiling target: ITERS full-band iterations of the batched engine on NRHS right-hand "
                          "sides of the WMAP-shaped problem (cooling off), one text line, no JSON")
     return ap.parse_args()
+
+
+FP64_FORMS = {"table": {}, "recurrence": {"legendre_table_bytes": 0}, "native": {"precision": 2}}
 
 
 def job_rate(local_seconds, steps, dist=None, device=None):
@@ -150,7 +156,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prob = make_problem(args.seed + rank)
     stream = torch.cuda.Stream()
-    opts = wf.options(tol=TOL, max_iter=20000, stream=stream.cuda_stream)
+    opts = wf.options(tol=TOL, max_iter=20000, stream=stream.cuda_stream, **FP64_FORMS[args.fp64_form])
     P = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask, opts)
     # synthetic data d = Y a + n, synthesised by the library itself (setup, untimed)
     a_true = torch.from_numpy(prob.alm_true.view(np.float64).copy()).cuda()
@@ -242,6 +248,19 @@ def run_ours(args):
                     "table_bytes_held": held, "table_bytes_per_pass": per_pass,
                     "evaluated_terms": evaluated, "full_triangle_terms": full, "peak_source": src,
                     "kernel_ms": {k: round(v, 4) for k, v in prof.items()}}
+    elif args.fp64_form == "native":
+        # native FP64: per evaluated term and pass 8 flops of contraction + 3 of recurrence, two passes
+        flops = 22.0 * evaluated
+        fp64_peak = alu.get("fp64_tflops") or 1.25
+        achieved = flops / t_leg / 1e12
+        roofline = {"bound": "alu", "kernel": "legendre_kernel<LEG_ITER> (native FP64)",
+                    "achieved": round(achieved, 4), "peak": round(fp64_peak, 3), "unit": "TFLOP/s",
+                    "frac": round(achieved / fp64_peak, 4), "traffic": None,
+                    "per_launch_ms": round(prof["legendre"], 4), "algorithmic_flops_per_launch": flops,
+                    "evaluated_terms": evaluated, "full_triangle_terms": full,
+                    "peak_source": "FP64 FMA rate measured by paper_1211_0585_gb300/probe/alu_peak.cu in this run"
+                    if alu.get("fp64_tflops") else "recorded FP64 FMA probe value (probe unavailable)",
+                    "kernel_ms": {k: round(v, 4) for k, v in prof.items()}}
     else:
         flops = 2.0 * LEGENDRE_DF_INSTR * evaluated
         achieved = flops / t_leg / 1e12
@@ -274,10 +293,11 @@ def run_ours(args):
     result = {
         "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "npix": prob.npix, "tol": TOL,
-                   "precision": "fp64 (double-float Legendre and ring FFTs, double updates and reductions)"
-                   + ("; Legendre stage reads a precomputed double-float lambda table" if held else ""),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.fp64_form == "native" else "f32x2+f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "nside": NSIDE, "lmax": LMAX, "npix": prob.npix, "tol": TOL,
+                   "precision": ("fp64 native (every step on the FP64 pipe)" if args.fp64_form == "native" else
+                                 "fp64 (double-float Legendre and ring FFTs, double updates and reductions)"
+                                 + ("; Legendre stage reads a precomputed double-float lambda table" if held else "")),
                    "iterations_per_solve": iters, "parallelism": f"replicas{world}",
                    "l2": "flushed (512 MiB write) between timed solves", "seed": args.seed},
         "sht_pair_ms": round(sht_pair_ms, 4),
@@ -530,7 +550,7 @@ def profile_batch(nrhs, iters, seed, shape=None):
           f"({1e3 * dt / iters:.2f} ms / iteration, status {status})", flush=True)
 
 
-def profile_fp64(nside, lmax, iters, seed):
+def profile_fp64(nside, lmax, iters, seed, form="table"):
     """A fixed amount of full-band FP64 work for ncu captures (lambda = 1,
     lmax_SHT = lmax): one synthesis launch, then per iteration the ring,
     Legendre and controller launches."""
@@ -538,7 +558,7 @@ def profile_fp64(nside, lmax, iters, seed):
     from paper_1211_0585_gb300 import inputs as I
     from paper_1211_0585_gb300 import wf
     prob = I.wmap_problem(seed=seed, nside=nside, lmax=lmax)
-    P = wf.Plan(nside, lmax, prob.cl, prob.noise_var, prob.mask, wf.options())
+    P = wf.Plan(nside, lmax, prob.cl, prob.noise_var, prob.mask, wf.options(**FP64_FORMS[form]))
     d = torch.from_numpy(prob.data(np.zeros(prob.npix))).cuda()
     s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
     held, per_pass = P.legendre_table(lmax)
@@ -551,7 +571,7 @@ def profile_fp64(nside, lmax, iters, seed):
 def main():
     args = parse()
     if args.profile_fp64:
-        profile_fp64(*args.profile_fp64, args.seed)
+        profile_fp64(*args.profile_fp64, args.seed, args.fp64_form)
         return
     if args.profile_batch:
         profile_batch(args.profile_batch[0], args.profile_batch[1], args.seed, args.profile_shape)
