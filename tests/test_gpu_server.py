@@ -99,3 +99,35 @@ def test_server_rejects_bad_requests():
     with pytest.raises(wf.WFError):
         S.submit(3, 8, np.ones(9), np.ones(108), None, np.zeros(108), 1e-6)
     S.close()
+
+
+def test_server_lone_mixed_request_runs_on_fp64_pool():
+    """A mixed-tolerance request that finds its shape's engine without live
+    slots runs on the FP64 pool (faster for one request than a near-empty
+    engine): its result is the FP64 solve's at its tolerance."""
+    r = make_request(401, 32, 64)
+    S = wf.Server(hbm_budget_bytes=8 << 30, max_batch=4)
+    t = S.submit(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"], r["d"], 1e-6)
+    S.drain(300000)
+    alm, stats, status = S.poll(t)
+    assert status == wf.WF_OK
+    P = wf.Plan(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"], wf.options(precision=0, tol=1e-6))
+    alone, _, _, _ = P.solve(r["d"])
+    assert np.array_equal(alm, alone)
+    assert stats["rel_posterior_grad"] > 0      # computed: the FP64 path ran
+    S.close()
+
+
+def test_server_fp64_pool_evicts_idle_plans_for_other_shapes():
+    """With a budget that holds one FP64 plan of these shapes, a request of a
+    second shape evicts the idle plan of the first; both results are right."""
+    reqs = [make_request(501, 16, 32), make_request(502, 32, 64), make_request(503, 16, 32)]
+    S = wf.Server(hbm_budget_bytes=7_600_000, max_batch=1)  # FP64 plans: about 1.6 MB and 6.9 MB
+    for r in reqs:
+        t = S.submit(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"], r["d"], 1e-8)
+        S.drain(300000)
+        alm, _, status = S.poll(t)
+        assert status == wf.WF_OK
+        P = wf.Plan(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"], wf.options(precision=0, tol=1e-8))
+        assert np.array_equal(alm, P.solve(r["d"])[0])
+    S.close()
