@@ -321,10 +321,16 @@ wf_status Plan::alloc_work() {
   if ((st = dalloc((void **)&d_s, sizeof(double2) * nalm))) return st;
   if ((st = dalloc((void **)&d_gain, sizeof(double) * npix))) return st;
   if ((st = dalloc((void **)&d_gainlam, sizeof(double) * R))) return st;
+  if ((st = dalloc((void **)&d_ddf, sizeof(float2) * npix))) return st;
+  if ((st = dalloc((void **)&d_wdf, sizeof(float2) * npix))) return st;
+  if ((st = dalloc((void **)&d_gdf, sizeof(float2) * npix))) return st;
+  if ((st = dalloc((void **)&d_gainlam_df, sizeof(double) * R))) return st;
   {
     std::vector<double> neg(R, -1.0);
     WF_CUDA(cudaMemcpy(d_gainlam, neg.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
+    WF_CUDA(cudaMemcpy(d_gainlam_df, neg.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
   }
+  WF_CUDA(cudaMemsetAsync(d_ddf, 0, sizeof(float2) * npix, stream));
   WF_CUDA(cudaMemsetAsync(d_FS, 0, sizeof(double4_32a) * nF, stream));
   WF_CUDA(cudaMemsetAsync(d_FT, 0, sizeof(double4_32a) * nF, stream));
   WF_CUDA(cudaMallocHost((void **)&h_ctl, sizeof(Ctl)));
@@ -361,6 +367,8 @@ wf_status plan_rebind(Plan *P, const double *cl, const double *w, double tau, lo
   WF_CUDA(cudaMemcpyAsync(P->d_cl, cl, sizeof(double) * (P->lmax + 1), cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_w, w, sizeof(double) * P->npix, cudaMemcpyHostToDevice, s));
   WF_CUDA(cudaMemcpyAsync(P->d_gainlam, neg.data(), sizeof(double) * P->R, cudaMemcpyHostToDevice, s));
+  WF_CUDA(cudaMemcpyAsync(P->d_gainlam_df, neg.data(), sizeof(double) * P->R, cudaMemcpyHostToDevice, s));
+  launch_to_df2(P->d_w, P->d_wdf, P->npix, s);
   WF_CUDA(cudaStreamSynchronize(s));
   if (P->graph_exec) {  // the captured launches hold the old tau
     cudaGraphExecDestroy(P->graph_exec);
@@ -525,6 +533,10 @@ wf_status wf_plan_create(int nside, int lmax, const double *cl, const double *no
     return st;
   }
   e = cudaMemcpyAsync(P->d_w, w.data(), sizeof(double) * npix, cudaMemcpyHostToDevice, P->stream);
+  if (e == cudaSuccess) {
+    launch_to_df2(P->d_w, P->d_wdf, npix, P->stream);  // the double-float ring stage's copy
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(P->d_cl, cl, sizeof(double) * (lmax + 1), cudaMemcpyHostToDevice, P->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
@@ -664,6 +676,7 @@ wf_status wf_iterate(wf_plan_t plan, const double *d_dev, double *s_dev, double 
   if (st) return st;
   cudaStream_t s = P->run_stream();
   WF_CUDA(cudaMemcpyAsync(P->d_d, d_dev, sizeof(double) * P->npix, cudaMemcpyDeviceToDevice, s));
+  P->stage_data(s);
   WF_CUDA(cudaMemcpyAsync(P->d_s, s_dev, sizeof(double2) * P->nalm, cudaMemcpyDeviceToDevice, s));
   if (reset_state || !P->fs_valid || P->fs_lsht != lsht) {
     LegArgs la = P->leg_args();
@@ -699,6 +712,7 @@ wf_status wf_profile_iterations(wf_plan_t plan, const double *d_dev, double *s_d
   if (st) return st;
   cudaStream_t s = P->run_stream();
   WF_CUDA(cudaMemcpyAsync(P->d_d, d_dev, sizeof(double) * P->npix, cudaMemcpyDeviceToDevice, s));
+  P->stage_data(s);
   WF_CUDA(cudaMemcpyAsync(P->d_s, s_dev, sizeof(double2) * P->nalm, cudaMemcpyDeviceToDevice, s));
   LegArgs la = P->leg_args();
   la.lsht = lsht;
@@ -829,6 +843,7 @@ static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *a
   const auto kind_in = d_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   WF_CUDA(cudaEventRecord(P->ev0, s));
   WF_CUDA(cudaMemcpyAsync(P->d_d, d, sizeof(double) * P->npix, kind_in, s));
+  P->stage_data(s);
   const double lam0 = P->opt.cooling ? P->lambda_of(P->opt.l_iter0) : 1.0;
   const int lb = P->opt.l_iter0 + P->opt.lmax_margin;
   const int lsht0 = (lam0 <= 1.0 || !P->opt.band_limit) ? P->lmax : (lb < P->lmax ? lb : P->lmax);

@@ -141,25 +141,38 @@ __global__ void __launch_bounds__(kRingDfThreads, 3) ring_df_kernel(const RingAr
     return;
   }
   if (MODE == RING_ITER) {
-    double c2n = 0.0, c2l = 0.0, c2nS = 0.0, c2lS = 0.0;
-    const bool fresh = A.gainlam[pr.x] == lam;   // gains of this pair already at this lambda
-    const double lt = lam * A.tau, l1t = (lam - 1.0) * A.tau;
-    auto update = [&](long long at, double s, double &cn, double &cl) {  // Eq. 3, returns u
-      const double w = A.w[at];
-      const double res = A.d[at] - s;
-      const double g = fresh ? A.gain[at] : w / (1.0 + l1t * w);
-      if (!fresh) A.gain[at] = g;
-      cn += w * res * res;
-      cl += g * res * res;
-      return lt * g * res;
+    // Eq. 3 and the chi^2 partials in double-float (the FP64 pipe is 1/63 of the
+    // FP32 one); the per-thread partials become doubles for the block sums
+    dd cnN{0.f, 0.f}, clN{0.f, 0.f}, cnS{0.f, 0.f}, clS{0.f, 0.f};
+    const bool fresh = T.gainlam[pr.x] == lam;   // gains of this pair already at this lambda
+    const dd ltd = mk(lam * A.tau);
+    const double l1t = (lam - 1.0) * A.tau;
+    auto update = [&](long long at, dd s, dd &cn, dd &cl) {  // Eq. 3, returns u
+      const float2 d2 = T.d[at], w2 = T.w[at];
+      const dd dv{d2.x, d2.y}, wv{w2.x, w2.y};
+      dd g;
+      if (fresh) {
+        const float2 g2 = T.gain[at];
+        g = dd{g2.x, g2.y};
+      } else {  // the first pass at a new lambda: the gain from w in double
+        const double w = A.w[at];
+        g = mk(w / (1.0 + l1t * w));
+        T.gain[at] = make_float2(g.h, g.l);
+      }
+      const dd res = dadd(dv, dneg(s));
+      const dd r2 = dmul(res, res);
+      cn = dadd(cn, dmul(wv, r2));
+      cl = dadd(cl, dmul(g, r2));
+      return dmul(dmul(ltd, g), res);
     };
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
       const float4 z = pixel(p);
-      const double uN = update(rg.off + p, todbl(RE(z)), c2n, c2l);
-      const double uS = two ? update(offS + p, todbl(IM(z)), c2nS, c2lS) : 0.0;
-      const float4 u = pack(mk(uN), mk(uS));
+      const dd uN = update(rg.off + p, RE(z), cnN, clN);
+      const dd uS = two ? update(offS + p, IM(z), cnS, clS) : dd{0.f, 0.f};
+      const float4 u = pack(uN, uS);
       buf[loc(p)] = rg.blue ? cmul(u, ch[p]) : u;
     }
+    double c2n = todbl(cnN), c2l = todbl(clN), c2nS = todbl(cnS), c2lS = todbl(clS);
     if (rg.blue) {
       for (int q = n + threadIdx.x; q < M; q += blockDim.x) buf[px<OpsDF>(q)] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -177,8 +190,8 @@ __global__ void __launch_bounds__(kRingDfThreads, 3) ring_df_kernel(const RingAr
       }
     }
     if (threadIdx.x == 0 && !fresh) {  // after block_sum2's barrier: every gain of the pair is written
-      A.gainlam[pr.x] = lam;
-      if (two) A.gainlam[pr.y] = lam;
+      T.gainlam[pr.x] = lam;
+      if (two) T.gainlam[pr.y] = lam;
     }
     __syncthreads();
   } else {  // RING_ANALYSIS: u = the input maps
@@ -214,6 +227,21 @@ __global__ void __launch_bounds__(kRingDfThreads, 3) ring_df_kernel(const RingAr
                                                       om * todbl(IM(US)))
                                      : make_double4_32a(om * todbl(RE(UN)), om * todbl(IM(UN)), 0.0, 0.0);
   }
+}
+
+// double -> double-float (hi, lo) per element
+__global__ void to_df2_kernel(const double *src, float2 *dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const dd v = mk(src[i]);
+    dst[i] = make_float2(v.h, v.l);
+  }
+}
+
+void launch_to_df2(const double *src, float2 *dst, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  to_df2_kernel<<<(int)blocks, 256, 0, s>>>(src, dst, n);
 }
 
 // double -> double-float table conversion

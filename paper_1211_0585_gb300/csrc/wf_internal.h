@@ -139,7 +139,11 @@ struct LegDfArgs {
 // (re hi, re lo, im hi, im lo).
 struct RingDfArgs {
   const float4 *tw, *hs, *chirp, *B;
+  const float2 *d, *w;    // [npix] data and inverse noise as double-float (RING_ITER)
+  float2 *gain;           // [npix] cached Eq. 3 gains as double-float
+  double *gainlam;        // [R] lambda the cached gains of each ring belong to (-1: none)
 };
+void launch_to_df2(const double *src, float2 *dst, long long n, cudaStream_t s);
 
 // Batched engine (batch_kernels.cu): B slots of one shape in lockstep.
 constexpr int kBatchMax = 64;

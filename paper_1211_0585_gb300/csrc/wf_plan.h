@@ -62,6 +62,9 @@ struct Plan : wf_plan_s {
   int hist_cap = 0;
   double *d_d = nullptr;
   double *d_gain = nullptr, *d_gainlam = nullptr;  // cached Eq. 3 gains per pixel, lambda per ring
+  // the double-float ring stage's copies: data, inverse noise, cached gains (own lambda cache)
+  float2 *d_ddf = nullptr, *d_wdf = nullptr, *d_gdf = nullptr;
+  double *d_gainlam_df = nullptr;
   double *d_pmap = nullptr;             // posterior gradient: W (d - Y a) and W d [2][npix]
   double2 *d_palm = nullptr;            // their analyses [2][nalm]
   double *d_ppart = nullptr;            // per-m norms [lmax+1][2]
@@ -80,7 +83,11 @@ struct Plan : wf_plan_s {
   RingArgs ring_args() const;
   LegArgs leg_args() const;
   LegDfArgs legdf_args() const { return LegDfArgs{d_dfA, d_dfg, d_dfls, d_dfsv, d_tab, d_poff}; }
-  RingDfArgs ringdf_args() const { return RingDfArgs{d_twf, d_hsf, d_chf, d_Bf}; }
+  RingDfArgs ringdf_args() const {
+    return RingDfArgs{d_twf, d_hsf, d_chf, d_Bf, d_ddf, d_wdf, d_gdf, d_gainlam_df};
+  }
+  // d_d was (re)written: its double-float copy for the ring stage, in stream order
+  void stage_data(cudaStream_t s) const { launch_to_df2(d_d, d_ddf, npix, s); }
   // the ring stage of the plan's precision
   void launch_rng(const RingArgs &a, cudaStream_t s, int mode) const {
     if (opt.precision == WF_PREC_FP64_NATIVE) launch_ring(a, rsingle.data(), (int)rsingle.size(), s, mode);
