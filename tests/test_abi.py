@@ -38,24 +38,26 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_struct_layouts_match_header():
-    code = r'''
-#include <stdio.h>
-#include <stddef.h>
-#include "wf.h"
-int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(wf_options), sizeof(wf_stats), sizeof(wf_iter_record),
-         offsetof(wf_options, stream), offsetof(wf_stats, ms_device), offsetof(wf_iter_record, level));
-  return 0;
-}
-'''
+    """Every field of the binding's structs sits where the C compiler puts it
+    (the header is compiled by gcc, offsets printed per field)."""
+    structs = {"wf_options": wf.Options, "wf_stats": wf.Stats, "wf_iter_record": wf.IterRecord}
+    lines = []
+    want = []
+    for cname, py in structs.items():
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(py))
+        for fname, _ in py._fields_:
+            cfield = fname[:-1] if fname.endswith("_") else fname  # lambda_: a Python keyword in C's name
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {cfield}));')
+            want.append(getattr(py, fname).offset)
+    code = "#include <stdio.h>\n#include <stddef.h>\n#include \"wf.h\"\nint main(void) {\n" + \
+        "\n".join(lines) + "\nreturn 0;\n}\n"
     with tempfile.TemporaryDirectory() as td:
         c = os.path.join(td, "t.c")
         exe = os.path.join(td, "t")
         open(c, "w").write(code)
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         got = [int(x) for x in subprocess.check_output([exe]).split()]
-    want = [ctypes.sizeof(wf.Options), ctypes.sizeof(wf.Stats), ctypes.sizeof(wf.IterRecord),
-            wf.Options.stream.offset, wf.Stats.ms_device.offset, wf.IterRecord.level.offset]
     assert got == want
 
 
