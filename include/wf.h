@@ -62,10 +62,14 @@ typedef enum {
   WF_ENOTFOUND = 9        /* unknown ticket */
 } wf_status;
 
-/* WF_PREC_FP64        FP64-accurate: the Legendre stage in double-float arithmetic (pairs of
- *                     floats with error-free transformations, 48-bit significands) because
- *                     GB300 runs FP64 at 1/63 of its FP32 rate; everything else in double.
- * WF_PREC_MIXED       FP32 transforms with FP64 residuals and refinement.
+/* WF_PREC_FP64        FP64-accurate: the Legendre stage, the ring FFTs and the Eq. 3 update in
+ *                     double-float arithmetic (pairs of floats with error-free transformations,
+ *                     48-bit significands) because GB300 runs FP64 at 1/63 of its FP32 rate;
+ *                     lambda_lm read from a precomputed table where it fits
+ *                     (legendre_table_bytes); reductions, Eq. 4 and the controller in double.
+ * WF_PREC_MIXED       the batched engine: FP32 ring FFTs, Legendre contractions on tensor cores
+ *                     (tf32 with exact splits), double-float state and Eq. 4, double reductions;
+ *                     optional FP64 refinement of each result (refine_iters).
  * WF_PREC_FP64_NATIVE every step in native double arithmetic (the plain reference kernels). */
 typedef enum { WF_PREC_FP64 = 0, WF_PREC_MIXED = 1, WF_PREC_FP64_NATIVE = 2 } wf_precision;
 
@@ -257,7 +261,9 @@ wf_status wf_solve_batch(wf_plan_t plan, int nrhs, const double *d, int d_on_dev
 wf_status wf_server_create(size_t hbm_budget_bytes, int max_batch, wf_server_t *out);
 
 /* Submit a request (host arrays, copied). tol <= 1e-7 selects the FP64 path,
- * larger tol the mixed path. Never blocks on the GPU. */
+ * larger tol the mixed path (a mixed request that finds its shape's engine
+ * without live requests may run on the FP64 pool instead, which meets any
+ * tolerance). Never blocks on the GPU. */
 wf_status wf_submit(wf_server_t server, int nside, int lmax, const double *cl,
                     const double *noise_var, const uint8_t *mask, const double *d, double tol,
                     uint64_t *ticket);
