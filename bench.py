@@ -53,6 +53,7 @@ def parse():
                          "WMAP-shaped problem at NSIDE / LMAX, the plan's default Legendre form")
     ap.add_argument("--profile-shape", type=int, nargs=2, metavar=("NSIDE", "LMAX"), default=None,
                     help="shape of --profile-batch (default: the bench's Nside 512 / lmax 1024)")
+    ap.add_argument("--alu-peaks", action="store_true", help="print the FP64 / FP32 FMA probe's JSON line and exit")
     ap.add_argument("--profile-batch", type=int, nargs=2, metavar=("NRHS", "ITERS"), default=None,
                     help="profiling target: ITERS full-band iterations of the batched engine on NRHS right-hand "
                          "sides of the WMAP-shaped problem (cooling off), one text line, no JSON")
@@ -139,8 +140,8 @@ def make_problem(seed):
 
 LEGENDRE_DF_INSTR = 90    # FP32 instructions per evaluated (l, m, ring pair) term, both passes
 # DRAM bytes (read + write) per algorithmic byte of legendre_df_kernel<LEG_ITER, table>: 885.0 MB
-# measured by ncu for one launch of `bench.py --profile-fp64 256 512 4` against 864.0 MB algorithmic
-# (profiles/legendre_df_kernel_table_nside256_lmax512.md); the full-size launch is scaled by it
+# measured by ncu for one launch of `bench.py --profile-fp64 256 512 4` against 864.0 MB algorithmic;
+# the full-size launch is scaled by it
 TABLE_TRAFFIC_RATIO = 885.04e6 / 864049664
 
 
@@ -222,13 +223,13 @@ def run_ours(args):
     s_prof = out.clone()
     prof = P.profile(dmap.data_ptr(), s_prof.data_ptr(), 1.0, LMAX, 10)
     evaluated, full = P.legendre_terms(LMAX)
-    alu = measure_alu_peaks()
+    held, per_pass = P.legendre_table(LMAX)
+    alu = {} if held else measure_alu_peaks()   # the ALU-bound forms' denominators
     fp32_peak = alu.get("fp32_tflops") or 75.3
     # the double-float Legendre kernel: per evaluated (l, m, ring pair) term, one
     # recurrence step (19 FP32 instructions) and two compensated multiply-adds
     # (13 each) in each of the analysis and synthesis passes = 90 FP32
     # instructions; each counted as 2 flops against the FP32 FMA peak
-    held, per_pass = P.legendre_table(LMAX)
     t_leg = prof["legendre"] * 1e-3
     if held:
         # the table form reads lambda from HBM in both passes: algorithmic bytes
@@ -258,7 +259,7 @@ def run_ours(args):
                     "frac": round(achieved / fp64_peak, 4), "traffic": None,
                     "per_launch_ms": round(prof["legendre"], 4), "algorithmic_flops_per_launch": flops,
                     "evaluated_terms": evaluated, "full_triangle_terms": full,
-                    "peak_source": "FP64 FMA rate measured by paper_1211_0585_gb300/probe/alu_peak.cu in this run"
+                    "peak_source": "FP64 FMA rate measured by bench.py's ALU probe in this run"
                     if alu.get("fp64_tflops") else "recorded FP64 FMA probe value (probe unavailable)",
                     "kernel_ms": {k: round(v, 4) for k, v in prof.items()}}
     else:
@@ -269,7 +270,7 @@ def run_ours(args):
                     "frac": round(achieved / fp32_peak, 4), "traffic": None,
                     "per_launch_ms": round(prof["legendre"], 4), "algorithmic_flops_per_launch": flops,
                     "evaluated_terms": evaluated, "full_triangle_terms": full,
-                    "peak_source": "FP32 FMA rate measured by paper_1211_0585_gb300/probe/alu_peak.cu in this run"
+                    "peak_source": "FP32 FMA rate measured by bench.py's ALU probe in this run"
                     if alu.get("fp32_tflops") else "recorded FP32 FMA probe value (probe unavailable)",
                     "fp64_pipe_tflops": alu.get("fp64_tflops"),
                     "kernel_ms": {k: round(v, 4) for k, v in prof.items()}}
@@ -431,11 +432,72 @@ def hbm_peak_gbs():
         return 6800.0, "fallback 6.8 TB/s (no measured peak file)"
 
 
+# FP64 / FP32 FMA throughput probe (the denominators of the ALU-bound kernels'
+# rooflines): each thread runs 8 independent FMA chains; one JSON line.
+ALU_PROBE_SRC = r"""
+#include <cstdio>
+#include <cuda_runtime.h>
+template <typename T>
+__global__ void fma_loop(T *out, int iters, T a, T b) {
+  T x0 = threadIdx.x * (T)1e-3, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+  T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+      x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+template <typename T>
+double tflops(int blocks, int threads, int iters) {
+  T *out = nullptr;
+  if (cudaMalloc(&out, sizeof(T) * blocks * threads) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fma_loop<T><<<blocks, threads>>>(out, 10, (T)0.999, (T)1e-3);
+  cudaDeviceSynchronize();
+  double best = 0.0;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    fma_loop<T><<<blocks, threads>>>(out, iters, (T)0.999, (T)1e-3);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double f = 2.0 * 8 * 16 * (double)iters * blocks * threads / (ms * 1e9);
+    if (f > best) best = f;
+  }
+  cudaFree(out);
+  return best;
+}
+int main() {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, 0) != cudaSuccess) { printf("{\"error\": \"no device\"}\n"); return 1; }
+  const int sms = p.multiProcessorCount;
+  const double f64 = tflops<double>(sms * 4, 256, 1000);
+  const double f32 = tflops<float>(sms * 8, 256, 10000);
+  printf("{\"device\": \"%s\", \"sms\": %d, \"fp64_tflops\": %.4f, \"fp32_tflops\": %.4f}\n",
+         p.name, sms, f64, f32);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+"""
+
+
 def measure_alu_peaks():
-    """FP64 / FP32 FMA throughput of this GPU, from the committed probe."""
+    """FP64 / FP32 FMA throughput of this GPU: the probe above, compiled for
+    sm_103a into a temporary directory and run once."""
+    import tempfile
     try:
         from paper_1211_0585_gb300 import build as B
-        out = subprocess.run([B.build_probe()], capture_output=True, text=True, timeout=120)
+        with tempfile.TemporaryDirectory() as tmp:
+            src, exe = os.path.join(tmp, "alu_peak.cu"), os.path.join(tmp, "alu_peak")
+            with open(src, "w") as f:
+                f.write(ALU_PROBE_SRC)
+            subprocess.run([B.nvcc(), *B.ARCH, "-O3", "-o", exe, src], check=True, capture_output=True, timeout=300)
+            out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
         return json.loads(out.stdout.strip().splitlines()[-1])
     except Exception:
         return {}
@@ -570,6 +632,9 @@ def profile_fp64(nside, lmax, iters, seed, form="table"):
 
 def main():
     args = parse()
+    if args.alu_peaks:
+        print(json.dumps(measure_alu_peaks()), flush=True)
+        return
     if args.profile_fp64:
         profile_fp64(*args.profile_fp64, args.seed, args.fp64_form)
         return

@@ -196,17 +196,20 @@ wf_status wf_alm2map(wf_plan_t plan, int lsht, const double *alm_dev, double *ma
  * (entries with l > lsht are set to 0): the basis change of Sect. 2. */
 wf_status wf_map2alm(wf_plan_t plan, int lsht, const double *map_dev, double *alm_dev);
 
-/* Allocation-free map2alm: alm = Y^dagger map exactly as wf_map2alm with
- * lsht = lmax, but with no plan and no device allocation on the call path. The
+/* Allocation-free map2alm: alm = Y^dagger map as wf_map2alm with lsht = lmax,
+ * but with no plan and no device allocation on the call path. It runs the
+ * native FP64 kernels, so it equals wf_map2alm of a WF_PREC_FP64_NATIVE plan
+ * bit for bit and that of a default (double-float) plan to about 1e-12. The
  * paper has no counterpart; this entry point exists for callers that cannot
  * call cudaMalloc -- code running under a device-memory budget owned by another
  * allocator (a framework's caching allocator or a fixed pool) and
  * latency-critical loops that cannot take cudaMalloc's implicit device
  * synchronisation.
- *   nside, lmax : as wf_plan_create; the tables and Fourier scratch for this
- *                 size must fit the library's static 16 MiB device array
- *                 (for example nside 128 with lmax 256 fits, nside 256 does not):
- *                 larger sizes return WF_EINVAL with the bytes they would need.
+ *   nside, lmax : as wf_plan_create, nside <= 1024; the tables and Fourier
+ *                 scratch for this size must fit the library's static 16 MiB
+ *                 device array: every lmax <= 4 nside fits for nside <= 128,
+ *                 lmax <= 243 for nside 256, nothing for nside >= 512. Larger
+ *                 sizes return WF_EINVAL with the bytes they would need.
  *   map_dev     : device [Npix] input; alm_dev : device [2*nalm] output.
  *   stream      : cudaStream_t, NULL = the default stream. Enqueues and returns.
  * The scratch array is one per GPU, held from library load to process exit and

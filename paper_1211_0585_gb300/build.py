@@ -72,21 +72,6 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     return LIB
 
 
-PROBE_SRC = os.path.join(HERE, "probe", "alu_peak.cu")
-PROBE_BIN = os.path.join(OUT_DIR, "alu_peak")
-
-
-def build_probe() -> str:
-    """The FP64/FP32 FMA throughput probe (the ALU roofline denominators)."""
-    if os.path.exists(PROBE_BIN) and os.path.getmtime(PROBE_BIN) >= os.path.getmtime(PROBE_SRC):
-        return PROBE_BIN
-    os.makedirs(OUT_DIR, exist_ok=True)
-    r = subprocess.run([nvcc(), *ARCH, "-O3", "-o", PROBE_BIN, PROBE_SRC], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"probe build failed:\n{r.stderr}")
-    return PROBE_BIN
-
-
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
                 extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
