@@ -291,6 +291,24 @@ def run_ours(args):
     e2e = {"value": round(args.steps / sum(e2e_t), 6), "unit": "solves/s",
            "h2d_bytes_per_step": prob.npix * 8, "d2h_bytes_per_step": P.nalm * 16}
 
+    # accuracy of the timed result (untimed): against the same solve on the native FP64 kernels, and
+    # against the converged solution (the same solve to a relative increment of 1e-9)
+    ours = out.cpu().numpy().view(np.complex128).copy()
+    accuracy = {}
+    if rank == 0 and not args.no_extras:
+        Pn = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask,
+                     wf.options(tol=TOL, max_iter=20000, precision=wf.WF_PREC_FP64_NATIVE))
+        ref_n, st_n, _, _ = Pn.solve(dmap.cpu().numpy())
+        Pn.close()
+        P.set_options(wf.options(tol=1e-9, max_iter=20000, stream=stream.cuda_stream, **FP64_FORMS[args.fp64_form]))
+        ref_c, st_c, _, _ = P.solve(dmap.cpu().numpy())
+        P.set_options(opts)
+        accuracy = {"rel_l2_vs_fp64_native": rel_l2_alm(ours, ref_n), "fp64_native_iterations": st_n["iters"],
+                    "rel_l2_vs_converged_tol1e-9": rel_l2_alm(ours, ref_c), "converged_iterations": st_c["iters"],
+                    "note": "a_lm relative L2 (m > 0 weighted x2) of the timed solve's result against the same "
+                            "problem solved by the native FP64 kernels, and against the same form run to a "
+                            "relative increment of 1e-9"}
+
     result = {
         "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
@@ -300,6 +318,8 @@ def run_ours(args):
                                  "fp64 (double-float Legendre and ring FFTs, double updates and reductions)"
                                  + ("; Legendre stage reads a precomputed double-float lambda table" if held else "")),
                    "iterations_per_solve": iters, "parallelism": f"replicas{world}",
+                   "stop_rule": "relative increment ||s_k - s_(k-1)|| / ||s_k|| <= 1e-6 at lambda = 1 (the "
+                                "distance to the converged solution is in final.accuracy)",
                    "l2": "flushed (512 MiB write) between timed solves", "seed": args.seed},
         "sht_pair_ms": round(sht_pair_ms, 4),
         "roofline": roofline,
@@ -308,7 +328,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "final": {"chi2_per_dof": st["chi2_per_dof"], "rel_increment": st["rel_increment"],
                   "rel_posterior_grad": st["rel_posterior_grad"],
-                  "levels": st["levels"], "status": status},
+                  "levels": st["levels"], "status": status, "accuracy": accuracy},
     }
     if rank == 0 and world == 1 and not args.no_extras:
         result["mixed_batched"] = mixed_batched(prob, dmap, P, out, flush, nrhs=64)
@@ -349,18 +369,19 @@ def mixed_batched(prob, dmap, P64, out64, flush, nrhs=64):
     _, stats, status = Pm.solve_batch(D.data_ptr(), on_device=True, alm_out=outm.data_ptr(), nrhs=nrhs)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    # FP64 solve of right-hand side 0 for the error
-    P64.solve(D[0].data_ptr(), out64.data_ptr(), on_device=True)
-    torch.cuda.synchronize()
-    ref = out64.cpu().numpy().view(np.complex128)
-    got = outm[0].cpu().numpy().view(np.complex128)
-    m = np.concatenate([np.full(LMAX + 1 - mm, mm) for mm in range(LMAX + 1)])
-    wgt = np.where(m == 0, 1.0, 2.0)
-    err = float(np.sqrt(np.sum(wgt * np.abs(got - ref) ** 2) / np.sum(wgt * np.abs(ref) ** 2)))
+    # FP64 solves of the first n_err right-hand sides (spread over the engine's slots) for the error
+    n_err = min(nrhs, 8)
+    errs = []
+    for i in range(n_err):
+        P64.solve(D[i].data_ptr(), out64.data_ptr(), on_device=True)
+        torch.cuda.synchronize()
+        errs.append(rel_l2_alm(outm[i].cpu().numpy().view(np.complex128), out64.cpu().numpy().view(np.complex128)))
     iters = [s["iters"] for s in stats]
     Pm.close()
     return {"solves_per_s": round(nrhs / dt, 4), "nrhs": nrhs, "seconds": round(dt, 3), "status": status,
-            "iterations_mean": round(float(np.mean(iters)), 1), "rel_l2_vs_fp64_rhs0": err,
+            "iterations_mean": round(float(np.mean(iters)), 1),
+            "rel_l2_vs_fp64_max": max(errs), "rel_l2_vs_fp64_mean": float(np.mean(errs)),
+            "rel_l2_vs_fp64_n": n_err,
             "precision": "FP32 ring FFTs (two slots per complex FFT); Legendre GEMMs on tcgen05 tensor cores "
                          "(kind::tf32, 22-bit tables, exact 3-way split of the FP32 data, five products, "
                          "double-float chunk sums); double-float state and Eq. 4; FP32 Eq. 3; double "
@@ -409,7 +430,7 @@ def serving_run(seconds=8.0, rate=4.0, seed=3):
     lat = {"fp64": [], "mixed": []}
     for t, tol, ns in tickets:  # each request's latency (submit -> result on the host)
         res = S.poll(t)
-        lat["fp64" if tol <= 1e-7 else "mixed"].append(res[1]["ms_device"])
+        lat["fp64" if tol <= 1e-7 else "mixed"].append(res[1]["ms_latency"])
     S.close()
     by_path = {k: {"n": len(v), "p50_ms": round(float(np.percentile(v, 50)), 1),
                    "max_ms": round(float(np.max(v)), 1)} for k, v in lat.items() if v}
@@ -419,6 +440,13 @@ def serving_run(seconds=8.0, rate=4.0, seed=3):
             "warm_s": round(t_warm, 2),
             "note": "inputs generated (%.1f s) and the three shapes made resident (wf_server_warm, mixed engine and "
                     "one FP64 plan each) before the stream starts" % t_gen}
+
+
+def rel_l2_alm(a, b):
+    """Relative L2 distance of two lmax = LMAX a_lm vectors, m > 0 weighted x2."""
+    m = np.concatenate([np.full(LMAX + 1 - mm, mm) for mm in range(LMAX + 1)])
+    wgt = np.where(m == 0, 1.0, 2.0)
+    return float(np.sqrt(np.sum(wgt * np.abs(a - b) ** 2) / np.sum(wgt * np.abs(b) ** 2)))
 
 
 def hbm_peak_gbs():

@@ -124,11 +124,15 @@ typedef struct {
   double chi2_noise;     /* (d - s)^+ N^-1 (d - s) part */
   double chi2_per_dof;   /* chi2 / n_obs */
   double rel_increment;  /* ||s_k - s_{k-1}|| / ||s_k|| of the last iteration */
-  double ms_device;      /* device time of the solve, CUDA events */
+  double ms_device;      /* time of the solve on the device: CUDA events around wf_solve's work; for a
+                            mixed solve in the batched engine (wf_solve_batch, served requests), the
+                            time its slot was occupied, from admission to harvest (host clock) */
   double rel_posterior_grad; /* ||Y^T W (d - Y a) - C^-1 a|| / ||Y^T W d|| of the result (modes with C_l > 0,
                             m > 0 counted twice; Y^T = map2alm / Omega): how far it is from the posterior
                             mean on the grid (Eq. 2), bounded below by the quadrature error of the HEALPix
                             analysis. FP64 paths with opt.posterior_grad = 1; -1 when not computed */
+  double ms_latency;     /* served requests (wf_poll): from wf_submit to the result on the host; 0 for
+                            direct solves */
 } wf_stats;
 
 /* Per-iteration record written by wf_iterate / wf_solve_history. */
@@ -198,8 +202,9 @@ wf_status wf_map2alm(wf_plan_t plan, int lsht, const double *map_dev, double *al
 
 /* Allocation-free map2alm: alm = Y^dagger map as wf_map2alm with lsht = lmax,
  * but with no plan and no device allocation on the call path. It runs the
- * native FP64 kernels, so it equals wf_map2alm of a WF_PREC_FP64_NATIVE plan
- * bit for bit and that of a default (double-float) plan to about 1e-12. The
+ * native FP64 kernels: it agrees with wf_map2alm of a WF_PREC_FP64_NATIVE plan
+ * to rounding (1e-14) and with that of a default (double-float) plan to about
+ * 1e-12. The
  * paper has no counterpart; this entry point exists for callers that cannot
  * call cudaMalloc -- code running under a device-memory budget owned by another
  * allocator (a framework's caching allocator or a fixed pool) and
@@ -266,7 +271,9 @@ wf_status wf_server_create(size_t hbm_budget_bytes, int max_batch, wf_server_t *
 /* Submit a request (host arrays, copied). tol <= 1e-7 selects the FP64 path,
  * larger tol the mixed path (a mixed request that finds its shape's engine
  * without live requests may run on the FP64 pool instead, which meets any
- * tolerance). Never blocks on the GPU. */
+ * tolerance; so does one whose shape's engine exceeds the whole budget).
+ * Never blocks on the GPU. WF_ENOMEM at once when no path for the request
+ * fits the server's whole HBM budget (it could never be admitted). */
 wf_status wf_submit(wf_server_t server, int nside, int lmax, const double *cl,
                     const double *noise_var, const uint8_t *mask, const double *d, double tol,
                     uint64_t *ticket);
@@ -275,6 +282,15 @@ wf_status wf_submit(wf_server_t server, int nside, int lmax, const double *cl,
  * request finished; *done = 0 otherwise. Returns the request's own status once
  * done; WF_ENOTFOUND for an unknown or already collected ticket. */
 wf_status wf_poll(wf_server_t server, uint64_t ticket, int *done, double *alm_out, wf_stats *stats);
+
+/* Cancel a request. A request still queued is dropped at once; one in a slot of
+ * a batched engine leaves it at the end of the current step; one being solved
+ * on the FP64 path stops after the current block of iterations. wf_poll then
+ * reports it done with WF_ECANCELLED and no a_lm. Returns WF_OK when the
+ * cancellation is recorded, WF_EINVAL (nothing changed) when the request had
+ * already finished -- its result stands --, WF_ENOTFOUND for an unknown or
+ * collected ticket. The paper has no counterpart (serving control). */
+wf_status wf_cancel(wf_server_t server, uint64_t ticket);
 
 /* Make a shape resident before its requests arrive, as a serving system loads
  * its models: precision WF_PREC_MIXED builds the shape's batched engine

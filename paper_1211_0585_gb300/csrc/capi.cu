@@ -872,11 +872,18 @@ static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *a
     P->graph_prec = P->opt.precision;
   }
   const int max_launch = (P->opt.max_iter + P->opt.graph_iters - 1) / P->opt.graph_iters + 1;
+  bool cancelled = false;
   for (int it = 0; it < max_launch; ++it) {
     WF_CUDA(cudaGraphLaunch(P->graph_exec, s));
     WF_CUDA(cudaMemcpyAsync(P->h_ctl, P->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     WF_CUDA(cudaStreamSynchronize(s));
     if (P->h_ctl->done) break;
+    if (P->cancel && P->cancel->load()) { cancelled = true; break; }
+  }
+  if (cancelled) {
+    P->fs_valid = false;
+    set_error("wf_solve: cancelled");
+    return WF_ECANCELLED;
   }
   const auto kind_out = alm_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   WF_CUDA(cudaMemcpyAsync(alm_out, P->d_s, sizeof(double2) * P->nalm, kind_out, s));

@@ -11,8 +11,9 @@
 // (16 MiB), which every GPU that loads this library holds until the process
 // exits (every lmax <= 4 nside fits it for nside <= 128, lmax <= 243 for
 // nside 256). The kernels are the native FP64 ring and Legendre kernels that
-// wf_map2alm runs for a WF_PREC_FP64_NATIVE plan, so the two agree bit for
-// bit; a default (double-float) plan's wf_map2alm agrees to about 1e-12.
+// wf_map2alm runs for a WF_PREC_FP64_NATIVE plan, so the two agree to
+// rounding (the tables here are built on the device, one ring class over all
+// rings); a default (double-float) plan's wf_map2alm agrees to about 1e-12.
 #include <cuda_runtime.h>
 
 #include <cmath>

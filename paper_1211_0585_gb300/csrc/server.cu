@@ -22,10 +22,14 @@
 //     one request costs more than the FP64 single solve (Nside 512: about
 //     3 ms against 1.7 ms per iteration), and the FP64 result meets any
 //     tolerance. Under load the engines fill and batch as above.
-// Latency is measured from wf_submit to the moment the result is on the host.
+// Latency is measured from wf_submit to the moment the result is on the host
+// (wf_stats.ms_latency). wf_cancel drops a queued request, takes a running
+// one out of its slot after the current step, or stops its FP64 solve after
+// the current block of iterations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -56,7 +60,8 @@ struct Request {
   std::vector<uint8_t> mask;
   double tau = 0.0;
   long long n_obs = 0;
-  Clock::time_point t_submit;
+  Clock::time_point t_submit, t_slot;
+  std::atomic<int> cancel{0};
   // result
   bool done = false;
   wf_status status = WF_OK;
@@ -118,13 +123,22 @@ struct wf_server_s {
   std::vector<std::thread> fp64_workers;
   std::string worker_error;
 
-  void finish(const std::shared_ptr<Request> &r) {
-    std::lock_guard<std::mutex> lk(mu);
+  // caller holds mu
+  void finish_locked(const std::shared_ptr<Request> &r) {
     r->done = true;
-    latencies_ms.push_back(std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count());
-    ++completed;
+    r->stats.ms_latency = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+    if (r->status == WF_ECANCELLED) {
+      r->alm.clear();
+    } else {
+      latencies_ms.push_back(r->stats.ms_latency);
+      ++completed;
+    }
     --in_flight;
     cv_done.notify_all();
+  }
+  void finish(const std::shared_ptr<Request> &r) {
+    std::lock_guard<std::mutex> lk(mu);
+    finish_locked(r);
   }
 };
 
@@ -273,6 +287,11 @@ void worker_loop(wf_server_s *S) {
     std::vector<std::shared_ptr<Request>> keep;
     std::map<ShapeRunner *, bool> changed;
     for (auto &r : take) {
+      if (r->cancel.load()) {
+        r->status = WF_ECANCELLED;
+        S->finish(r);
+        continue;
+      }
       {
         auto it = S->runners.find(std::make_pair(r->nside, r->lmax));
         const bool idle_engine = it == S->runners.end() || it->second->live() == 0;
@@ -297,6 +316,7 @@ void worker_loop(wf_server_s *S) {
         continue;
       }
       R->slot[b] = r;
+      r->t_slot = Clock::now();
       changed[R] = true;
     }
     if (!keep.empty()) {
@@ -317,6 +337,14 @@ void worker_loop(wf_server_s *S) {
       bool any = false;
       for (int b = 0; b < (int)R->slot.size(); ++b) {
         auto &r = R->slot[b];
+        if (r && r->cancel.load()) {  // cancelled while in its slot: leave without a result
+          r->status = WF_ECANCELLED;
+          R->engine->release_slot(b);
+          S->finish(r);
+          r.reset();
+          any = true;
+          continue;
+        }
         if (!r || !R->engine->h_ctl[b].done) continue;
         const Ctl &c = R->engine->h_ctl[b];
         const wf_iter_record &last = R->engine->h_last[b];
@@ -335,8 +363,7 @@ void worker_loop(wf_server_s *S) {
         r->stats.chi2 = last.chi2_prior + last.chi2_noise;
         r->stats.chi2_per_dof = r->stats.chi2 / (double)r->n_obs;
         r->stats.rel_increment = c.last_rel;
-        r->stats.ms_device =
-            std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+        r->stats.ms_device = std::chrono::duration<double, std::milli>(Clock::now() - r->t_slot).count();
         r->stats.rel_posterior_grad = -1.0;  // not computed on the mixed path
         r->status = c.numeric ? WF_ENUMERIC : (c.converged ? WF_OK : WF_ENOTCONVERGED);
         R->engine->release_slot(b);
@@ -399,14 +426,15 @@ void fp64_loop(wf_server_s *S) {
     }
     if (st == WF_OK) {
       r->alm.resize(2 * (size_t)(r->lmax + 1) * (r->lmax + 2) / 2);
+      plan->cancel = &r->cancel;  // the solve stops after its current block of iterations once set
       st = wf_solve(plan, r->d.data(), 0, r->alm.data(), 0, nullptr, &r->stats);
-      r->stats.ms_device = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+      plan->cancel = nullptr;
     }
     r->status = st;
     {
       std::lock_guard<std::mutex> lk(S->mu);
       --S->fp64_busy;
-      if (plan && (st == WF_OK || st == WF_ENOTCONVERGED || st == WF_ENUMERIC)) {
+      if (plan && (st == WF_OK || st == WF_ENOTCONVERGED || st == WF_ENUMERIC || st == WF_ECANCELLED)) {
         S->fp64_idle[std::make_pair(r->nside, r->lmax)].push_back(IdlePlan{plan, bytes, Clock::now()});
         plan = nullptr;
       } else {
@@ -478,13 +506,22 @@ wf_status wf_submit(wf_server_t S, int nside, int lmax, const double *cl, const 
   }
   if (r->n_obs == 0) { set_error("wf_submit: no observed pixel"); return WF_EINVAL; }
   r->tau = tau;
+  // a request no path of which fits the whole budget could never be admitted
+  const bool fp64_fits = fp64_bytes(nside, lmax) <= S->budget;
+  const bool engine_fits = engine_bytes(nside, lmax, S->max_batch) <= S->budget;
+  const bool to_fp64 = tol <= kFp64Tol || !engine_fits;
+  if (to_fp64 && !fp64_fits) {
+    set_error("wf_submit: the request's " + std::string(tol <= kFp64Tol ? "FP64 plan" : "engine and FP64 plan") +
+              " exceed the server's HBM budget");
+    return WF_ENOMEM;
+  }
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(S->mu);
     r->ticket = S->next_ticket++;
     S->all[r->ticket] = r;
     ++S->in_flight;
-    if (tol <= kFp64Tol) S->fp64_queue.push_back(r);
+    if (to_fp64) S->fp64_queue.push_back(r);
     else S->pending.push_back(r);
   }
   S->cv.notify_all();
@@ -508,6 +545,27 @@ wf_status wf_poll(wf_server_t S, uint64_t ticket, int *done, double *alm_out, wf
   if (stats) *stats = r->stats;
   if (r->status != WF_OK) set_error("wf_poll: request finished with an error status");
   return r->status;
+}
+
+wf_status wf_cancel(wf_server_t S, uint64_t ticket) {
+  if (!S) { set_error("wf_cancel: NULL server"); return WF_EINVAL; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) { set_error("wf_cancel: unknown ticket"); return WF_ENOTFOUND; }
+  std::shared_ptr<Request> r = it->second;
+  if (r->done) { set_error("wf_cancel: the request had already finished"); return WF_EINVAL; }
+  r->cancel.store(1);
+  // still queued: drop it now; otherwise its worker ends it
+  for (auto *q : {&S->pending, &S->fp64_queue}) {
+    auto jt = std::find(q->begin(), q->end(), r);
+    if (jt != q->end()) {
+      q->erase(jt);
+      r->status = WF_ECANCELLED;
+      S->finish_locked(r);
+      break;
+    }
+  }
+  return WF_OK;
 }
 
 wf_status wf_server_warm(wf_server_t S, int nside, int lmax, int precision) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <vector>
 
 #include "wf_internal.h"
@@ -74,6 +75,7 @@ struct Plan : wf_plan_s {
   cudaGraphExec_t graph_exec = nullptr;
   int graph_prec = -1;                  // precision whose kernels graph_exec holds
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  const std::atomic<int> *cancel = nullptr;  // set by the server: wf_solve stops between graph launches
 
   ~Plan() override;
   wf_status dalloc(void **p, size_t bytes);

@@ -189,12 +189,14 @@ def small_problem(seed: int = 1, nside: int = 16, lmax: int = 32) -> Problem:
 
 
 def wmap_problem(seed: int = 1, nside: int = 512, lmax: int = 1024, ndisc: int = 500,
-                 fwhm_arcmin: float = 13.0) -> Problem:
+                 fwhm_arcmin: float = 13.0, noise_scale: float = 1.0) -> Problem:
+    """noise_scale multiplies every pixel variance; (nside / 512)^2 keeps the
+    noise power per steradian of the Nside 512 map at a smaller nside."""
     rng = np.random.default_rng(seed)
     cl = cl_lcdm_like(lmax, fwhm_arcmin)
     z, phi = pixel_centres(nside)
     h = 1.0 + 7.0 * np.abs(sin_ecliptic_latitude(z, phi))
-    var = 2200.0 ** 2 / h
+    var = 2200.0 ** 2 / h * noise_scale
     mask = mask_band(z, 0.2)
     mask = mask_discs(z, phi, mask, ndisc, 0.5, rng)
     alm = draw_alm(cl, rng)

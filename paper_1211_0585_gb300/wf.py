@@ -26,7 +26,7 @@ EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_
             "wf_plan_legendre_table", "wf_plan_kernels_per_iteration", "wf_plan_set_options",
             "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
             "wf_solve_history", "wf_solve_batch",
-            "wf_server_create", "wf_submit", "wf_poll", "wf_server_warm", "wf_server_drain", "wf_server_stats",
+            "wf_server_create", "wf_submit", "wf_poll", "wf_cancel", "wf_server_warm", "wf_server_drain", "wf_server_stats",
             "wf_server_destroy", "wf_last_error"]
 
 
@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("lmax_sht_final", ctypes.c_int), ("lambda_final", ctypes.c_double), ("chi2", ctypes.c_double),
                 ("chi2_prior", ctypes.c_double), ("chi2_noise", ctypes.c_double),
                 ("chi2_per_dof", ctypes.c_double), ("rel_increment", ctypes.c_double),
-                ("ms_device", ctypes.c_double), ("rel_posterior_grad", ctypes.c_double)]
+                ("ms_device", ctypes.c_double), ("rel_posterior_grad", ctypes.c_double),
+                ("ms_latency", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +104,7 @@ def load(path: str = LIB_PATH):
         "wf_server_create": [ctypes.c_size_t, _i, ctypes.POINTER(_vp)],
         "wf_submit": [_vp, _i, _i, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_uint64)],
         "wf_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(_i), _vp, ctypes.POINTER(Stats)],
+        "wf_cancel": [_vp, ctypes.c_uint64],
         "wf_server_drain": [_vp, _i],
         "wf_server_warm": [_vp, _i, _i, _i],
         "wf_server_stats": [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64)],
@@ -307,8 +309,13 @@ class Server:
             _check(status, ok=(WF_OK, WF_EBUSY))
             return None
         self._nalm.pop(ticket, None)
-        _check(status, ok=(WF_OK, WF_ENOTCONVERGED))
-        return out, st.as_dict(), status
+        _check(status, ok=(WF_OK, WF_ENOTCONVERGED, WF_ECANCELLED))
+        return (None if status == WF_ECANCELLED else out), st.as_dict(), status
+
+    def cancel(self, ticket):
+        """Cancel a request; returns the status (WF_OK: recorded, WF_EINVAL: it had already
+        finished, WF_ENOTFOUND: unknown ticket). Raises on other errors."""
+        return _check(load().wf_cancel(self.handle, ticket), ok=(WF_OK, WF_EINVAL, WF_ENOTFOUND))
 
     def warm(self, nside, lmax, precision):
         """Make a shape resident (WF_PREC_MIXED: its batched engine; WF_PREC_FP64: one pooled plan)."""

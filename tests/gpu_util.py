@@ -33,7 +33,52 @@ def problem(kind, seed=1, nside=16, lmax=32):
         p = I.small_problem(seed=seed, nside=nside, lmax=lmax)
     elif kind == "wmap":
         p = I.wmap_problem(seed=seed, nside=nside, lmax=lmax, ndisc=max(5, 12 * nside * nside // 6000))
+    elif kind == "wmap-cooled":
+        # the WMAP-shaped problem with the noise power per steradian of the Nside 512 map, so that
+        # lambda starts above 1 and the solve cools through levels as the bench's does
+        p = I.wmap_problem(seed=seed, nside=nside, lmax=lmax, ndisc=max(5, 12 * nside * nside // 6000),
+                           noise_scale=(nside / 512.0) ** 2)
     else:
         raise ValueError(kind)
     d = p.data(O.alm2map(p.nside, p.lmax, p.alm_true))
     return p, d
+
+
+def _oracle_solve(args):
+    """One oracle solve in a worker process (see oracle_solves): the stopping
+    iteration k and the iterates k - extra .. k + extra (the last ones by
+    further iterations at lambda = 1 and full band, as the solve's last level)."""
+    nside, lmax, cl, var, mask, d, opts, extra = args
+    keep = {}
+    res = O.solve(nside, lmax, cl, var, mask, d, O.Options(**opts),
+                  callback=lambda k, rec, s: keep.__setitem__(k, s.copy()))
+    k = res.iters
+    states = {i: keep[i] for i in range(max(1, k - extra), k + 1)}
+    if extra:
+        import math
+        tau = O.messenger_tau(var, mask)
+        w = O.inverse_noise(var, mask)
+        omega = 4.0 * math.pi / (12 * nside * nside)
+        s = res.alm
+        for i in range(k + 1, k + extra + 1):
+            s = O.messenger_step(nside, lmax, lmax, s, d, w, O.pixel_gain(1.0, tau, w),
+                                 O.harmonic_filter(1.0, tau, omega, cl), cl, 1.0, tau).s_alm
+            states[i] = s
+    return k, states
+
+
+def _one_thread():
+    import os
+    os.environ["OMP_NUM_THREADS"] = "1"
+
+
+def oracle_solves(jobs, workers=None):
+    """Oracle solves of many small problems in parallel, one OpenMP thread per
+    worker process. The pool is started with `spawn`, so it is safe after the
+    test process has used the GPU."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    n = workers or max(1, min(len(jobs), os.cpu_count() or 1))
+    with ProcessPoolExecutor(n, mp_context=mp.get_context("spawn"), initializer=_one_thread) as ex:
+        return list(ex.map(_oracle_solve, jobs))

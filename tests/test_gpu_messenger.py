@@ -152,3 +152,74 @@ def test_full_size_first_iteration_nside512(prec):
     chi2n = float(np.sum(w * d * d))
     assert recs[0]["chi2_noise"] == pytest.approx(chi2n, rel=1e-12)
     assert recs[0]["chi2_prior"] == 0.0
+
+
+# lambda levels of the bench's cooled solve (WMAP-shaped, Nside 512 / lmax 1024, seed 1): (lambda, lmax_SHT)
+BENCH_LEVELS = [(6.1793721184416155, 120), (1.575, 140), (1.0, 1024)]
+
+
+def test_full_vector_iterations_nside512_bench_levels():
+    """The bench's problem and launch shapes (Nside 512, lmax 1024, every FP64
+    form): three iterations at each lambda level / band limit of its cooled
+    solve, every one of the 525,825 a_lm of every iterate against the oracle's
+    messenger step, element by element, plus the chi^2 records."""
+    import torch
+    from paper_1211_0585_gb300 import inputs as I
+    nside, lmax = 512, 1024
+    p = I.wmap_problem(seed=1, nside=nside, lmax=lmax)
+    d = p.data(O.alm2map(nside, lmax, p.alm_true))
+    schedule = [(lam, lsht, 3) for lam, lsht in BENCH_LEVELS]
+    res, states = run_oracle_schedule(p, d, schedule)
+    dd = dev(d)
+    for prec in PRECS:
+        P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(**FP64_PATHS[prec]))
+        s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
+        k = 0
+        for li, (lam, lsht, n) in enumerate(schedule):
+            for j in range(n):
+                rec = P.iterate(dd.data_ptr(), s.data_ptr(), lam, lsht, 1, reset=(k == 0))[0]
+                got, ref = host_alm(s), states[k]
+                scale = np.max(np.abs(ref))
+                assert np.max(np.abs(got - ref)) <= 1e-10 * scale, (prec, k)
+                assert O.rel_l2(got, ref, lmax) < TOL, (prec, k)
+                h = res.history[k]
+                for key in ("chi2_prior", "chi2_noise", "chi2_lambda"):
+                    assert rec[key] == pytest.approx(h[key], rel=TOL, abs=1e-300), (prec, k, key)
+                k += 1
+        P.close()
+
+
+def test_cooled_solve_nside128_matches_oracle():
+    """A whole cooled solve at Nside 128 / lmax 256 (noise power per steradian
+    of the Nside 512 map, so lambda cools through three levels as in the
+    bench): same levels, band limits and iteration count as the oracle's
+    controller, and the result within 1e-10."""
+    nside, lmax = 128, 256
+    p, d = problem("wmap-cooled", seed=5, nside=nside, lmax=lmax)
+    opts = dict(tol=1e-6, max_iter=3000)
+    ores = O.solve(nside, lmax, p.cl, p.noise_var, p.mask, d, O.Options(**opts))
+    assert len(O.schedule_of(ores)) >= 3
+    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(**opts))
+    alm, st, status, recs = P.solve(d, history=opts["max_iter"] + 1)
+    assert status == wf.WF_OK and st["iters"] == ores.iters
+    assert [(r["lam"], r["lsht"]) for r in recs] == [(h["lam"], h["lsht"]) for h in ores.history]
+    assert O.rel_l2(alm, ores.alm, lmax) < TOL
+    assert st["chi2"] == pytest.approx(ores.history[-1]["chi2"], rel=TOL)
+
+
+@pytest.mark.parametrize("prec", ["fp64-table", "fp64-native"])
+def test_paper_stop_rule_stops_on_oracle_iteration(prec):
+    """Sect. 3's stop rule alone (Delta chi^2 < 1e-4 sigma_chi2 at lambda = 1,
+    the increment rule off): a cooled solve on the device stops on the
+    oracle's iteration with the oracle's result."""
+    nside, lmax = 32, 64
+    p, d = problem("wmap-cooled", seed=8, nside=nside, lmax=lmax)
+    opts = dict(tol=0.0, final_dchi2=1e-4, max_iter=5000)
+    ores = O.solve(nside, lmax, p.cl, p.noise_var, p.mask, d, O.Options(**opts))
+    assert ores.converged and ores.iters < opts["max_iter"]
+    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(**FP64_PATHS[prec], **opts))
+    alm, st, status, recs = P.solve(d, history=opts["max_iter"] + 1)
+    assert status == wf.WF_OK and st["converged"] == 1
+    assert st["iters"] == ores.iters
+    assert [(r["lam"], r["lsht"]) for r in recs] == [(h["lam"], h["lsht"]) for h in ores.history]
+    assert O.rel_l2(alm, ores.alm, lmax) < TOL

@@ -246,3 +246,43 @@ def test_posterior_residual_against_dense_normal_equations():
     rel = O.posterior_residual(nside, lmax, D.unpack(x, lmax), cl, var, mask, d)
     assert rel > 1e-6
     assert abs(rel - rel_dense) <= 1e-9 * rel_dense
+
+
+@pytest.mark.parametrize("nside,lmax,seed,noise", [(4, 8, 41, 2e-3), (8, 16, 42, 5e-4)])
+def test_paper_stop_rule_matches_dense_chi2_sequence(nside, lmax, seed, noise):
+    """Sect. 3's stop rule, Delta chi^2 < 1e-4 sigma_chi2 at lambda = 1 with
+    sigma_chi2 = sqrt(2 n_obs): the stopping iteration is derived here from
+    the chi^2 sequence of the dense iteration x_k = G x_{k-1} + b (step k
+    reports the chi^2 of its input x_{k-1}; a difference is taken from the
+    third step of the level on), and the oracle's controller, with the
+    increment rule off (tol = 0), must stop on exactly that step (157 and 1561
+    here). The same derivation with sigma_chi2 = sqrt(n_obs), or a threshold
+    of 1e-3, stops elsewhere on both cases."""
+    cl, var, mask, d, z, phi = tiny_problem(nside, lmax, seed, noise=noise)
+    Y, Yd, f_dof, a_pix, w, tau, omega = dense_setup(nside, lmax, cl, var, mask, z, phi, 1.0)
+    wgt, cl_dof = D.dof_weight(lmax), cl[D.dof_l(lmax)]
+    G, b = D.affine_map(Y, Yd, a_pix, f_dof, d)
+    n_obs = int(np.count_nonzero(mask))
+
+    def stop_step(sigma, eps=1e-4, kmax=5000):
+        x = np.zeros(G.shape[0])
+        chi = []
+        for k in range(1, kmax + 1):
+            chi.append(D.chi2(x, Y, w, d, cl_dof, wgt))     # chi^2 of step k's input state
+            if k >= 3 and abs(chi[-1] - chi[-2]) < eps * sigma:
+                return k
+            x = G @ x + b
+        return None
+
+    k_ref = stop_step(math.sqrt(2.0 * n_obs))
+    assert k_ref is not None and k_ref > 4
+    res = O.solve(nside, lmax, cl, var, mask, d,
+                  O.Options(tol=0.0, final_dchi2=1e-4, cooling=False, max_iter=5000))
+    assert res.converged and res.iters == k_ref
+    # the step's state is the dense iterate x_{k_ref}
+    x = np.zeros(G.shape[0])
+    for _ in range(k_ref):
+        x = G @ x + b
+    assert np.allclose(D.pack(res.alm, lmax), x, rtol=0, atol=1e-11 * np.abs(x).max())
+    assert stop_step(math.sqrt(float(n_obs))) != k_ref
+    assert stop_step(math.sqrt(2.0 * n_obs), eps=1e-3) != k_ref

@@ -5,9 +5,10 @@ loop that cannot take cudaMalloc's implicit device synchronisation).
 
 Two calls in a row on fresh maps (every call reuses the same static scratch)
 must match the oracle's map2alm within the transforms' parity bar (1e-12 of
-the largest coefficient), and equal, bit for bit, wf_map2alm of a plan that
-runs the same native FP64 kernels. The largest sizes the static scratch
-accepts are included. This file is collected last so that a failure here
+the largest coefficient), and wf_map2alm of a plan that runs the same native
+FP64 kernels to rounding (1e-14: the plan builds its FFT tables and ring
+classes on its own). The largest sizes the static scratch accepts are
+included. This file is collected last so that a failure here
 comes after every other test has run."""
 import numpy as np
 import pytest
@@ -36,8 +37,8 @@ def test_noalloc_matches_oracle_and_native_plan(nside, lmax):
         got = torch.full((2 * nalm,), 3.0, dtype=torch.float64, device="cuda")
         wf.map2alm_noalloc(nside, lmax, f.data_ptr(), got.data_ptr())
         torch.cuda.synchronize()
-        g = got.cpu().numpy()
-        assert np.array_equal(g, ref.cpu().numpy()), f"call {call}: differs from the native FP64 plan"
+        g, r = got.cpu().numpy(), ref.cpu().numpy()
+        assert np.max(np.abs(g - r)) <= 1e-14 * np.max(np.abs(r)), f"call {call}: native FP64 plan"
         orc = O.map2alm(nside, lmax, f_host).view(np.float64)
         assert np.max(np.abs(g - orc)) <= 1e-12 * np.max(np.abs(orc)), f"call {call}: oracle"
     P.close()
