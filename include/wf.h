@@ -262,6 +262,30 @@ wf_status wf_solve_history(wf_plan_t plan, const double *d, int d_on_device, dou
 wf_status wf_solve_batch(wf_plan_t plan, int nrhs, const double *d, int d_on_device,
                          double *alm_out, int alm_on_device, wf_stats *stats);
 
+/* Constrained realisations (Sect. 3, WMAP analysis: the Wiener filter map plus
+ * a fluctuation map is a constrained realisation with the correct signal
+ * variance; the power-spectra figure):
+ *     s_CR,i = s_WF(d) + xi_i - s_WF(Y xi_i + n_i),   i = 0 .. nreal-1,
+ * a draw from the posterior of s given d, with xi_i ~ N(0, S) (a_l0 = sqrt(C_l) z,
+ * a_lm = sqrt(C_l / 2)(z + i z') for m > 0) and n_i ~ N(0, N) (sigma_p z on
+ * observed pixels, 0 where masked) drawn on the device. The normals are a
+ * function of (seed, realisation, entry) alone: Philox4x64-10 (Salmon et al.,
+ * SC 2011) with key (seed, 0) and counter (block, kind, i, 0), kind 0 for the
+ * signal (normals 2q, 2q + 1 for a_lm entry q) and 1 for the noise (normal p
+ * for pixel p), four normals per block by Box-Muller on the uniforms
+ * ((x >> 11) + 1/2) 2^-53 of words (0, 1) and (2, 3). The nreal + 1 Wiener
+ * filters (d first) run as one wf_solve_batch in the plan's precision and
+ * options.
+ *   d       : [Npix] data, host or device (d_on_device)
+ *   cr_out  : [nreal][2*nalm] realisations, host or device (out_on_device)
+ *   wf_out  : [2*nalm] s_WF(d), same memory kind as cr_out, or NULL
+ *   stats   : [nreal + 1] or NULL: the solve of d, then of each fluctuation map
+ * Allocates its working buffers ((nreal + 1) maps and 3 nreal + 1 a_lm vectors)
+ * for the call. Returns WF_OK, or WF_ENOTCONVERGED (results written) and the
+ * errors of wf_solve_batch. */
+wf_status wf_constrained_realisations(wf_plan_t plan, int nreal, uint64_t seed, const double *d, int d_on_device,
+                                      double *cr_out, int out_on_device, double *wf_out, wf_stats *stats);
+
 /* Serving: continuous batching of solve requests of any (nside, lmax, C_l,
  * noise, mask) under a device-memory budget.
  *   hbm_budget_bytes : admission limit for plans + per-request buffers (0 = 90 % of free memory)

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENOMEM", 3: "WF_ECUDA", 4: "W
 EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_info", "wf_plan_legendre_terms",
             "wf_plan_legendre_table", "wf_plan_kernels_per_iteration", "wf_plan_set_options",
             "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
-            "wf_solve_history", "wf_solve_batch",
+            "wf_solve_history", "wf_solve_batch", "wf_constrained_realisations",
             "wf_server_create", "wf_submit", "wf_poll", "wf_cancel", "wf_server_warm", "wf_server_drain", "wf_server_stats",
             "wf_server_destroy", "wf_last_error"]
 
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "wf_solve_history": [_vp, _vp, _i, _vp, _i, ctypes.POINTER(Stats), ctypes.POINTER(IterRecord), _i,
                              ctypes.POINTER(_i)],
         "wf_solve_batch": [_vp, _i, _vp, _i, _vp, _i, ctypes.POINTER(Stats)],
+        "wf_constrained_realisations": [_vp, _i, ctypes.c_uint64, _vp, _i, _vp, _i, _vp, ctypes.POINTER(Stats)],
         "wf_server_create": [ctypes.c_size_t, _i, ctypes.POINTER(_vp)],
         "wf_submit": [_vp, _i, _i, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_uint64)],
         "wf_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(_i), _vp, ctypes.POINTER(Stats)],
@@ -276,6 +277,19 @@ class Plan:
         status = L.wf_solve_batch(self.handle, nrhs, _host_ptr(dh), 0, out.ctypes.data_as(ctypes.c_void_p), 0, stats)
         _check(status, ok=(WF_OK, WF_ENOTCONVERGED))
         return out, [stats[i].as_dict() for i in range(nrhs)], status
+
+
+    def constrained_realisations(self, d, nreal, seed, with_wf=True):
+        """nreal constrained realisations s_WF(d) + xi_i - s_WF(Y xi_i + n_i) of host data d.
+        Returns (cr [nreal, nalm] complex, s_WF(d) or None, stats of the nreal + 1 solves, status)."""
+        dh = np.ascontiguousarray(d, dtype=np.float64)
+        cr = np.empty((nreal, self.nalm), dtype=np.complex128)
+        wfo = np.empty(self.nalm, dtype=np.complex128) if with_wf else None
+        stats = (Stats * (nreal + 1))()
+        status = load().wf_constrained_realisations(self.handle, nreal, ctypes.c_uint64(seed), _host_ptr(dh), 0,
+                                                    cr.ctypes.data_as(ctypes.c_void_p), 0, _host_ptr(wfo), stats)
+        _check(status, ok=(WF_OK, WF_ENOTCONVERGED))
+        return cr, wfo, [stats[i].as_dict() for i in range(nreal + 1)], status
 
 
 class Server:
