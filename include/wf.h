@@ -286,6 +286,40 @@ wf_status wf_solve_batch(wf_plan_t plan, int nrhs, const double *d, int d_on_dev
 wf_status wf_constrained_realisations(wf_plan_t plan, int nreal, uint64_t seed, const double *d, int d_on_device,
                                       double *cr_out, int out_on_device, double *wf_out, wf_stats *stats);
 
+/* Several messenger fields (Sect. 4, Conclusion: more than one messenger field
+ * to combine several observations, e.g. of different detectors, in one
+ * analysis). ndet maps of one sky on one grid, d_k = Y B_k s + n_k, each with
+ * a beam B_k = diag(b_k,l), noise N_k (diagonal in pixel space, masked
+ * pixels N_k^-1 = 0) and its own messenger t_k with T_k = tau_k 1,
+ * tau_k = min diag(N_k). One iteration solves Eq. 3 per map and pixel,
+ *     t_k = Y B_k s + a_k (d_k - Y B_k s),
+ * and Eq. 4 with every messenger, per mode,
+ *     s_lm = sum_k g_k b_k,l t_k,lm / (1 / C_l + sum_k g_k b_k,l^2),  g_k = 1 / (lambda tau_k Omega),
+ * the basis change applied to t_k - Y B_k s, so that the result at lambda = 1 is
+ * the joint Wiener filter (S^-1 + sum_k B_k Y^T N_k^-1 Y B_k) s = sum_k B_k Y^T N_k^-1 d_k.
+ * The chi^2 monitor sums every map's noise term; cooling (Sect. 3) sets lambda
+ * at scale l to C_l sum_k b_k,l^2 / (tau_k Omega), clamped to >= 1; the band
+ * limit stays at lmax (opt->band_limit is ignored).
+ *   ndet      : 1 .. 16 maps
+ *   cl        : host [lmax+1] sky spectrum (beams NOT folded in)
+ *   beams     : host [ndet][lmax+1] b_k,l, or NULL for b = 1
+ *   noise_var : host [ndet][Npix]; mask : host [ndet][Npix] or NULL (all observed)
+ *   opt       : as wf_plan_create; precision WF_PREC_FP64 or WF_PREC_FP64_NATIVE
+ *               (WF_EINVAL for WF_PREC_MIXED)
+ * One plan per map is created inside (its noise, mask and buffers); the first
+ * holds the Legendre tables every map's transforms read. */
+typedef struct wf_multi_s *wf_multi_t;
+wf_status wf_multi_create(int nside, int lmax, int ndet, const double *cl, const double *beams,
+                          const double *noise_var, const uint8_t *mask, const wf_options *opt, wf_multi_t *out);
+
+/* Joint solve of the ndet maps d ([ndet][Npix], host or device): alm_out [2*nalm]
+ * (host or device), stats and up to max_records per-iteration records (both
+ * may be NULL). Returns WF_OK, WF_ENOTCONVERGED (result written) or WF_ENUMERIC. */
+wf_status wf_multi_solve(wf_multi_t multi, const double *d, int d_on_device, double *alm_out, int alm_on_device,
+                         wf_stats *stats, wf_iter_record *records, int max_records, int *n_records);
+
+wf_status wf_multi_destroy(wf_multi_t multi);
+
 /* Serving: continuous batching of solve requests of any (nside, lmax, C_l,
  * noise, mask) under a device-memory budget.
  *   hbm_budget_bytes : admission limit for plans + per-request buffers (0 = 90 % of free memory)

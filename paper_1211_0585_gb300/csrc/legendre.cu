@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kThreads) legendre_kernel(const LegArgs A) {
   const int lmax = A.lmax, RP = A.RP;
   int L = A.lsht;
   double lam = 1.0;
+  if (MODE != LEG_ITER && A.gate && A.gate->done) return;
   if (MODE == LEG_ITER) {
     if (A.ctl->done) return;
     L = A.ctl->lsht;

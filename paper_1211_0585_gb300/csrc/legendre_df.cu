@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, TAB ? kTabBlocks : 2) legendre_df_ke
   const int lmax = A.lmax, RP = A.RP;
   int L = A.lsht;
   double lam = 1.0;
+  if (MODE != LEG_ITER && A.gate && A.gate->done) return;
   if (MODE == LEG_ITER) {
     if (A.ctl->done) return;
     L = A.ctl->lsht;

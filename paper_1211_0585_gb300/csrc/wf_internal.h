@@ -121,6 +121,8 @@ struct LegArgs {
   const double2 *alm_in;  // LEG_SYNTH input
   double *m_part;         // LEG_ITER: [lmax+1][3] chi2_S, incr2, norm2
   const Ctl *ctl;
+  const Ctl *gate;        // LEG_SYNTH / LEG_ANALYSIS inside a controlled iteration: skip once gate->done
+                          // (nullptr for the standalone transforms)
   int lsht, lmax, RP;
   double omega, tau;
 };

@@ -26,6 +26,7 @@ EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_
             "wf_plan_legendre_table", "wf_plan_kernels_per_iteration", "wf_plan_set_options",
             "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
             "wf_solve_history", "wf_solve_batch", "wf_constrained_realisations",
+            "wf_multi_create", "wf_multi_solve", "wf_multi_destroy",
             "wf_server_create", "wf_submit", "wf_poll", "wf_cancel", "wf_server_warm", "wf_server_drain", "wf_server_stats",
             "wf_server_destroy", "wf_last_error"]
 
@@ -102,6 +103,10 @@ def load(path: str = LIB_PATH):
                              ctypes.POINTER(_i)],
         "wf_solve_batch": [_vp, _i, _vp, _i, _vp, _i, ctypes.POINTER(Stats)],
         "wf_constrained_realisations": [_vp, _i, ctypes.c_uint64, _vp, _i, _vp, _i, _vp, ctypes.POINTER(Stats)],
+        "wf_multi_create": [_i, _i, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(Options), ctypes.POINTER(_vp)],
+        "wf_multi_solve": [_vp, _vp, _i, _vp, _i, ctypes.POINTER(Stats), ctypes.POINTER(IterRecord), _i,
+                           ctypes.POINTER(_i)],
+        "wf_multi_destroy": [_vp],
         "wf_server_create": [ctypes.c_size_t, _i, ctypes.POINTER(_vp)],
         "wf_submit": [_vp, _i, _i, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_uint64)],
         "wf_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(_i), _vp, ctypes.POINTER(Stats)],
@@ -290,6 +295,51 @@ class Plan:
                                                     cr.ctypes.data_as(ctypes.c_void_p), 0, _host_ptr(wfo), stats)
         _check(status, ok=(WF_OK, WF_ENOTCONVERGED))
         return cr, wfo, [stats[i].as_dict() for i in range(nreal + 1)], status
+
+
+class Multi:
+    """Owns a wf_multi_t: the joint Wiener filter of several maps of one sky
+    (one messenger field per map)."""
+
+    def __init__(self, nside, lmax, cl, noise_vars, masks=None, beams=None, opts: Options | None = None):
+        self.nside, self.lmax = nside, lmax
+        self._cl = np.ascontiguousarray(cl, dtype=np.float64)
+        self._nv = np.ascontiguousarray(np.stack(noise_vars), dtype=np.float64)
+        self.ndet = self._nv.shape[0]
+        self._mask = None if masks is None else np.ascontiguousarray(np.stack(masks), dtype=np.uint8)
+        self._beams = None if beams is None else np.ascontiguousarray(np.stack(beams), dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(load().wf_multi_create(nside, lmax, self.ndet, _host_ptr(self._cl), _host_ptr(self._beams),
+                                      _host_ptr(self._nv), _host_ptr(self._mask),
+                                      ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def nalm(self):
+        return (self.lmax + 1) * (self.lmax + 2) // 2
+
+    def solve(self, ds, history=0):
+        """ds: [ndet][Npix] host maps. Returns (alm, stats, status, records)."""
+        dh = np.ascontiguousarray(np.stack(ds), dtype=np.float64)
+        out = np.empty(self.nalm, dtype=np.complex128)
+        st = Stats()
+        recs = (IterRecord * max(1, history))()
+        n = ctypes.c_int()
+        status = load().wf_multi_solve(self.handle, _host_ptr(dh), 0, out.ctypes.data_as(ctypes.c_void_p), 0,
+                                       ctypes.byref(st), recs, history, ctypes.byref(n))
+        _check(status, ok=(WF_OK, WF_ENOTCONVERGED))
+        return out, st.as_dict(), status, [recs[i].as_dict() for i in range(n.value)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().wf_multi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
