@@ -43,7 +43,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched-mixed and serving measurements")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-mixed, constrained-realisation, Planck-shaped and serving measurements")
+    ap.add_argument("--no-planck", action="store_true", help="skip the Planck-shaped (Nside 2048) measurement")
+    ap.add_argument("--serving-only", action="store_true", help="run only the config-5 serving measurement")
+    ap.add_argument("--planck-only", action="store_true", help="run only the Planck-shaped measurement")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp64-form", choices=["table", "recurrence", "native"], default="table",
                     help="form of the FP64 solve: double-float kernels reading the precomputed lambda table "
@@ -61,6 +65,20 @@ def parse():
 
 
 FP64_FORMS = {"table": {}, "recurrence": {"legendre_table_bytes": 0}, "native": {"precision": 2}}
+
+
+class progress:
+    """Start / end of a bench section on stderr, with its wall time."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        self.t0 = time.perf_counter()
+        print(f"[bench] {self.name} ...", file=sys.stderr, flush=True)
+
+    def __exit__(self, *exc):
+        print(f"[bench] {self.name} done in {time.perf_counter() - self.t0:.1f} s", file=sys.stderr, flush=True)
 
 
 def job_rate(local_seconds, steps, dist=None, device=None):
@@ -318,8 +336,9 @@ def run_ours(args):
                                  "fp64 (double-float Legendre and ring FFTs, double updates and reductions)"
                                  + ("; Legendre stage reads a precomputed double-float lambda table" if held else "")),
                    "iterations_per_solve": iters, "parallelism": f"replicas{world}",
-                   "stop_rule": "relative increment ||s_k - s_(k-1)|| / ||s_k|| <= 1e-6 at lambda = 1 (the "
-                                "distance to the converged solution is in final.accuracy)",
+                   "stop_rule": "relative increment ||s_k - s_(k-1)|| / ||s_k|| <= 1e-6 at lambda = 1; the "
+                                "relative residual of Eq. 2 at the stop is final.rel_posterior_grad, the distance "
+                                "to the converged solution final.accuracy",
                    "l2": "flushed (512 MiB write) between timed solves", "seed": args.seed},
         "sht_pair_ms": round(sht_pair_ms, 4),
         "roofline": roofline,
@@ -330,11 +349,24 @@ def run_ours(args):
                   "rel_posterior_grad": st["rel_posterior_grad"],
                   "levels": st["levels"], "status": status, "accuracy": accuracy},
     }
+    levels = schedule_levels(P, dmap.cpu().numpy()) if rank == 0 and world == 1 else None
     if rank == 0 and world == 1 and not args.no_extras:
-        result["mixed_batched"] = mixed_batched(prob, dmap, P, out, flush, nrhs=64)
-        result["serving"] = serving_run(seconds=8.0, rate=4.0)
+        with progress("mixed_batched"):
+            result["mixed_batched"] = mixed_batched(prob, dmap, P, out, flush, nrhs=64)
+        with progress("mixed_batched.roofline"):
+            result["mixed_batched"]["roofline"] = batched_roofline(prob)
+        with progress("constrained_realisations"):
+            result["constrained_realisations"] = constrained_realisations_run(prob, dmap)
+        P.close()
+        torch.cuda.empty_cache()
+        if not args.no_planck:
+            with progress("planck"):
+                result["planck"] = planck_run()
+            torch.cuda.empty_cache()
+        with progress("serving"):
+            result["serving"] = serving_run(weights=SERVING_BENCH_WEIGHTS)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(prob, dmap.cpu().numpy(), P, budget_s=25.0)
+        result["cpu_baseline"] = cpu_baseline(prob, dmap.cpu().numpy(), levels=levels, budget_s=25.0)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist:
@@ -389,62 +421,221 @@ def mixed_batched(prob, dmap, P64, out64, flush, nrhs=64):
             "timing": "host wall clock around wf_solve_batch with device-resident inputs"}
 
 
-def serving_run(seconds=8.0, rate=4.0, seed=3):
-    """Config 5 in small: a Poisson stream (rate req/s for `seconds`) of requests
-    with Nside in {128, 256, 512}, lmax = 2 Nside, C_l amplitude x U[0.5, 2],
-    per-request hit map and mask (10-30 % cut plus 0-1000 discs), tol 1e-5
-    (mixed) or 1e-8 (FP64) at random; reports p50 / p99 latency and solves/s."""
+def serving_requests(n, rng, shapes, weights=None):
+    """n requests of config 5: Nside uniform over `shapes`, lmax = 2 Nside, C_l amplitude x U[0.5, 2],
+    per-request hit map and mask (10-30 % band cut plus 0-1000 discs of 0.5 deg), tol 1e-5 (mixed) or
+    1e-8 (FP64) with equal odds. Pixel noise keeps the Nside 512 map's power per steradian."""
     from paper_1211_0585_gb300 import inputs as I
-    from paper_1211_0585_gb300 import wf
-    rng = np.random.default_rng(seed)
-    shapes = [(128, 256), (256, 512), (512, 1024)]
-    reqs = []
-    t_gen = time.perf_counter()
-    n_req = max(1, int(rng.poisson(rate * seconds)))
-    for i in range(n_req):
-        ns, lm = shapes[rng.integers(len(shapes))]
+    geo = {}
+    for ns, _ in shapes:
         z, phi = I.pixel_centres(ns)
+        geo[ns] = (z, phi, np.abs(I.sin_ecliptic_latitude(z, phi)))
+    out = []
+    for _ in range(n):
+        ns, lm = shapes[rng.choice(len(shapes), p=weights)]
+        z, phi, sb = geo[ns]
         cut = rng.uniform(0.1, 0.3)
         mask = I.mask_discs(z, phi, I.mask_band(z, cut), int(rng.integers(0, 1001)), 0.5, rng)
-        h = 1.0 + 7.0 * np.abs(I.sin_ecliptic_latitude(z, phi)) * rng.uniform(0.5, 1.5)
-        var = 2200.0 ** 2 / h * (512.0 / ns) ** 2
+        h = 1.0 + 7.0 * sb * rng.uniform(0.5, 1.5)
+        var = 2200.0 ** 2 / h * (ns / 512.0) ** 2   # pixel area ~ 1 / Nside^2: same noise power per sr
         cl = I.cl_lcdm_like(lm, 13.0 * 512 / ns) * rng.uniform(0.5, 2.0)
         d = rng.standard_normal(len(z)) * np.sqrt(var) + rng.standard_normal(len(z)) * np.sqrt(cl[2:40].sum())
-        reqs.append((ns, lm, cl, var, mask, d, 1e-8 if rng.random() < 0.5 else 1e-5))
-    gaps = rng.exponential(1.0 / rate, n_req)
+        out.append((ns, lm, cl, var, mask, d, 1e-8 if rng.random() < 0.5 else 1e-5))
+    return out
+
+
+SERVING_SHAPES = [(128, 256), (256, 512), (512, 1024), (1024, 2048)]
+# the bench line's stream: Nside 1024 at a low share (its FP64 solves take ~16 s of a worker each, so at the
+# uniform mix a 200-request window would take many minutes); --serving-only runs the uniform mix
+SERVING_BENCH_WEIGHTS = [0.3, 0.3, 0.3, 0.1]
+
+
+def serving_run(n_burst=24, n_stream=200, load=0.8, seed=3, max_batch=16, weights=None):
+    """Config 5: requests of four shapes (Nside 128 / 256 / 512 / 1024, lmax = 2 Nside; drawn with
+    `weights`, uniform when None) and two tolerances through wf_server. Capacity: a burst of n_burst
+    requests submitted at once, completed solves / time (the throughput of the saturated server). Then a
+    Poisson stream at `load` x that capacity for n_stream requests: p50 / p99 latency (submit to result on
+    the host), solves/s, per shape and path."""
+    from paper_1211_0585_gb300 import wf
+    rng = np.random.default_rng(seed)
+    shapes = SERVING_SHAPES
+    t_gen = time.perf_counter()
+    burst = serving_requests(n_burst, rng, shapes, weights)
     t_gen = time.perf_counter() - t_gen
-    S = wf.Server(hbm_budget_bytes=0, max_batch=16)
+    S = wf.Server(hbm_budget_bytes=0, max_batch=max_batch)
     t_warm = time.perf_counter()
-    for ns, lm in shapes:  # the shapes are made resident before the stream, as a server loads its models
+    for ns, lm in shapes:  # the shapes are made resident before the requests, as a server loads its models
         S.warm(ns, lm, wf.WF_PREC_MIXED)
         S.warm(ns, lm, wf.WF_PREC_FP64)
     t_warm = time.perf_counter() - t_warm
+
+    def collect(tickets):
+        rows = []
+        for t, ns, tol in tickets:
+            res = S.poll(t)
+            rows.append((ns, "fp64" if tol <= 1e-7 else "mixed", res[1]["ms_latency"], res[2]))
+        return rows
+
     t0 = time.perf_counter()
-    tickets = []
-    for (ns, lm, cl, var, mask, d, tol), g in zip(reqs, gaps):
-        tickets.append((S.submit(ns, lm, cl, var, mask, d, tol), tol, ns))
+    tk = [(S.submit(ns, lm, cl, var, mask, d, tol), ns, tol) for ns, lm, cl, var, mask, d, tol in burst]
+    t1 = time.perf_counter()
+    stream = serving_requests(n_stream, rng, shapes, weights)   # generated on the host while the burst is served
+    t_gen += time.perf_counter() - t1
+    print(f"[bench] serving: burst of {n_burst} submitted; stream inputs generated", file=sys.stderr, flush=True)
+    S.drain(3600000)
+    # all submitted at t0: the last completion (its latency) closes the burst, however long the host took
+    # to generate the stream meanwhile
+    t_burst = max(r[2] for r in collect(tk)) / 1e3 + (t1 - t0)
+    capacity = n_burst / t_burst
+    rate = load * capacity
+    print(f"[bench] serving: capacity {capacity:.3f} / s, stream of {n_stream} at {rate:.3f} / s",
+          file=sys.stderr, flush=True)
+    gaps = rng.exponential(1.0 / rate, n_stream)
+    t0 = time.perf_counter()
+    tk = []
+    for (ns, lm, cl, var, mask, d, tol), g in zip(stream, gaps):
+        tk.append((S.submit(ns, lm, cl, var, mask, d, tol), ns, tol))
         time.sleep(g)
-    S.drain(900000)
+    t_sub = time.perf_counter() - t0
+    S.drain(3600000)
     wall = time.perf_counter() - t0
-    st = S.stats()
-    lat = {"fp64": [], "mixed": []}
-    for t, tol, ns in tickets:  # each request's latency (submit -> result on the host)
-        res = S.poll(t)
-        lat["fp64" if tol <= 1e-7 else "mixed"].append(res[1]["ms_latency"])
+    rows = collect(tk)
     S.close()
-    by_path = {k: {"n": len(v), "p50_ms": round(float(np.percentile(v, 50)), 1),
-                   "max_ms": round(float(np.max(v)), 1)} for k, v in lat.items() if v}
-    return {"requests": n_req, "rate_per_s": rate, "wall_s": round(wall, 2), "solves_per_s": round(n_req / wall, 3),
-            "p50_ms": round(st["p50_ms"], 1), "p99_ms": round(st["p99_ms"], 1), "by_path": by_path, "max_batch": 16,
-            "shapes": "Nside 128/256/512, lmax 2 Nside", "tol_mix": "1e-5 mixed / 1e-8 FP64, half each",
-            "warm_s": round(t_warm, 2),
-            "note": "inputs generated (%.1f s) and the three shapes made resident (wf_server_warm, mixed engine and "
-                    "one FP64 plan each) before the stream starts" % t_gen}
+    lat = np.array([r[2] for r in rows])
+
+    def summary(sel):
+        v = lat[sel]
+        return {"n": int(v.size), "p50_ms": round(float(np.percentile(v, 50)), 1),
+                "p99_ms": round(float(np.percentile(v, 99)), 1)} if v.size else {"n": 0}
+
+    per_shape = {f"nside{ns}": summary(np.array([r[0] == ns for r in rows])) for ns, _ in shapes}
+    per_path = {k: summary(np.array([r[1] == k for r in rows])) for k in ("fp64", "mixed")}
+    return {"saturation_rate_per_s": round(capacity, 3),
+            "saturation": f"{n_burst} requests submitted at once, solves / time to drain ({t_burst:.1f} s)",
+            "rate_per_s": round(rate, 3), "load_vs_saturation": load, "requests": n_stream,
+            "arrival_s": round(t_sub, 1), "wall_s": round(wall, 1), "solves_per_s": round(n_stream / wall, 3),
+            "p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "statuses_ok": int(sum(r[3] == 0 for r in rows)), "per_shape": per_shape, "per_path": per_path,
+            "max_batch": max_batch, "shapes": "Nside 128/256/512/1024, lmax = 2 Nside, drawn with weights "
+                                              + ("uniform" if weights is None else str(weights)),
+            "tol_mix": "1e-5 (mixed engine) / 1e-8 (FP64 pool), equal odds", "warm_s": round(t_warm, 1),
+            "config5_rate_50_per_s": f"{50.0 / capacity:.1f} x the measured capacity: above saturation, the "
+                                     "queue would grow without bound, so the stream runs at `load` x capacity",
+            "note": f"inputs generated on the host ({t_gen:.0f} s; the stream's while the burst is served); the "
+                    "four shapes made resident (wf_server_warm: mixed engine and one FP64 plan each) before "
+                    "any request"}
 
 
-def rel_l2_alm(a, b):
-    """Relative L2 distance of two lmax = LMAX a_lm vectors, m > 0 weighted x2."""
-    m = np.concatenate([np.full(LMAX + 1 - mm, mm) for mm in range(LMAX + 1)])
+def batched_roofline(prob, nrhs=64, iters=12):
+    """Full-band iterations of the 64-slot mixed engine (cooling off, lambda = 1): ms per iteration and
+    its HBM roofline, the algorithmic bytes of one batched iteration being the FP32 Legendre tables read
+    by the two GEMMs, the Fourier arrays written and read by the ring stage, the GEMM operands, and each
+    slot's data and inverse noise."""
+    import torch
+    from paper_1211_0585_gb300 import wf
+    Pm = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask,
+                 wf.options(tol=0.0, max_iter=iters, cooling=0, precision=wf.WF_PREC_MIXED, batch_slots=nrhs))
+    D = torch.from_numpy(np.stack([prob.noise] * nrhs)).cuda()
+    out = torch.empty((nrhs, 2 * Pm.nalm), dtype=torch.float64, device="cuda")
+    Pm.solve_batch(D.data_ptr(), on_device=True, alm_out=out.data_ptr(), nrhs=nrhs)   # engine, autotune
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Pm.solve_batch(D.data_ptr(), on_device=True, alm_out=out.data_ptr(), nrhs=nrhs)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0) / iters
+    Pm.close()
+    rp, npix = 2 * NSIDE, 12 * NSIDE * NSIDE
+    nalm = (LMAX + 1) * (LMAX + 2) // 2
+    rows = sum((LMAX - m + 2) // 2 for m in range(LMAX + 1))
+    table = 2 * rows * 2 * rp * 4                       # two FP32 tables, rows of one parity, both parities
+    fourier = 4 * (LMAX + 1) * rp * 16 * nrhs           # FS read + FT written (ring stage), XT, FS (GEMMs)
+    data = npix * 8 * nrhs                              # (d, w) FP32 per slot
+    state = 2 * nalm * 16 * nrhs                        # double-float state read and written
+    nbytes = table + fourier + data + state
+    peak, src = hbm_peak_gbs()
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "batched mixed engine, one full-band iteration (ring stage, XT, "
+                                      "analysis and synthesis tcgen05 GEMMs, controller)",
+            "ms_per_iteration": round(ms, 3), "nrhs": nrhs, "algorithmic_bytes_per_iteration": nbytes,
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "peak_source": src, "timing": f"host wall clock over {iters} full-band iterations of all slots"}
+
+
+def planck_run(iters=8, slots=8, seed=1):
+    """Config 3 (Planck-shaped, Nside 2048 / lmax 4096): the same data map through the FP64 path (double-
+    float recurrence form: the lambda table would take 275 GB) and the mixed engine with one slot and with
+    `slots` slots, `iters` fixed iterations at lambda = 1 (cooling off); ms per iteration per right-hand
+    side and the mixed result's relative a_lm distance to the FP64 one."""
+    import torch
+    from paper_1211_0585_gb300 import inputs as I
+    from paper_1211_0585_gb300 import wf
+    ns, lm = 2048, 4096
+    t_gen = time.perf_counter()
+    prob = I.planck_problem(seed=seed, nside=ns, lmax=lm)
+    t_gen = time.perf_counter() - t_gen
+    o = dict(tol=0.0, max_iter=iters, cooling=0, posterior_grad=0)
+    P = wf.Plan(ns, lm, prob.cl, prob.noise_var, prob.mask, wf.options(**o))
+    a = torch.from_numpy(prob.alm_true.view(np.float64).copy()).cuda()
+    d = torch.empty(prob.npix, dtype=torch.float64, device="cuda")
+    P.alm2map(lm, a.data_ptr(), d.data_ptr())
+    torch.cuda.synchronize()
+    d += torch.from_numpy(prob.noise).cuda()
+    del a
+    ref = torch.empty(2 * P.nalm, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st, _, _ = P.solve(d.data_ptr(), ref.data_ptr(), on_device=True)
+    torch.cuda.synchronize()
+    fp64_ms = 1e3 * (time.perf_counter() - t0) / iters
+    P.close()
+    out = {"workload": "Planck-shaped, Nside 2048 (50,331,648 px), lmax 4096, 5' beam, lognormal hits, 25 % cut",
+           "iterations": iters, "fp64_ms_per_iteration": round(fp64_ms, 2)}
+    for b in (1, slots):
+        Pm = wf.Plan(ns, lm, prob.cl, prob.noise_var, prob.mask,
+                     wf.options(precision=wf.WF_PREC_MIXED, batch_slots=b, **o))
+        D = d.repeat(b)
+        res = torch.empty(b * 2 * P.nalm, dtype=torch.float64, device="cuda")
+        Pm.solve_batch(D.data_ptr(), on_device=True, alm_out=res.data_ptr(), nrhs=b)   # engine and tables
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Pm.solve_batch(D.data_ptr(), on_device=True, alm_out=res.data_ptr(), nrhs=b)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0) / iters
+        err = rel_l2_alm(res[:2 * P.nalm].cpu().numpy().view(np.complex128), ref.cpu().numpy().view(np.complex128),
+                         lm)
+        out[f"mixed_{b}slot_ms_per_iteration"] = round(ms, 2)
+        out[f"mixed_{b}slot_ms_per_rhs_iteration"] = round(ms / b, 2)
+        out[f"mixed_{b}slot_rel_l2_vs_fp64"] = err
+        Pm.close()
+        del D, res
+        torch.cuda.empty_cache()
+    out["note"] = f"host generation of the inputs {t_gen:.0f} s; timing: host wall clock around solves of " \
+                  f"{iters} iterations (FP64: one map; mixed: the same map in every slot)"
+    return out
+
+
+def constrained_realisations_run(prob, dmap, nreal=63):
+    """Config 4's constrained realisations through wf_constrained_realisations on the mixed plan: nreal
+    realisations and the Wiener filter of d in one 64-slot batch."""
+    from paper_1211_0585_gb300 import wf
+    Pm = wf.Plan(NSIDE, LMAX, prob.cl, prob.noise_var, prob.mask,
+                 wf.options(precision=wf.WF_PREC_MIXED, tol=TOL, max_iter=20000, batch_slots=nreal + 1))
+    d = dmap.cpu().numpy()
+    Pm.constrained_realisations(d, nreal, seed=7)           # engine and tables
+    t0 = time.perf_counter()
+    cr, wfd, stats, status = Pm.constrained_realisations(d, nreal, seed=8)
+    dt = time.perf_counter() - t0
+    Pm.close()
+    return {"realisations_per_s": round(nreal / dt, 3), "nreal": nreal, "seconds": round(dt, 3),
+            "status": status, "iterations_mean": round(float(np.mean([s["iters"] for s in stats])), 1),
+            "timing": "host wall clock around wf_constrained_realisations (host data in, host results out; "
+                      "draws, syntheses and the 64 Wiener filters on the device)"}
+
+
+def rel_l2_alm(a, b, lmax=None):
+    """Relative L2 distance of two a_lm vectors (lmax = LMAX by default), m > 0 weighted x2."""
+    lmax = LMAX if lmax is None else lmax
+    m = np.concatenate([np.full(lmax + 1 - mm, mm) for mm in range(lmax + 1)])
     wgt = np.where(m == 0, 1.0, 2.0)
     return float(np.sqrt(np.sum(wgt * np.abs(a - b) ** 2) / np.sum(wgt * np.abs(b) ** 2)))
 
@@ -665,6 +856,11 @@ def main():
         return
     if args.profile_fp64:
         profile_fp64(*args.profile_fp64, args.seed, args.fp64_form)
+        return
+    if args.serving_only or args.planck_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(serving_run() if args.serving_only else planck_run()), flush=True)
         return
     if args.profile_batch:
         profile_batch(args.profile_batch[0], args.profile_batch[1], args.seed, args.profile_shape)

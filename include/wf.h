@@ -320,6 +320,45 @@ wf_status wf_multi_solve(wf_multi_t multi, const double *d, int d_on_device, dou
 
 wf_status wf_multi_destroy(wf_multi_t multi);
 
+/* Temperature and polarisation (Sect. 4, Conclusion: the filter on T and P maps
+ * together; the power-spectra figure's TT, EE and TE). Pixels carry (T, Q, U)
+ * with a 3 x 3 noise covariance N_p (T independent of the Q-U block) and
+ * separate temperature and polarisation masks (N^-1 = 0 on masked components);
+ * the signal covariance per (l, m) is [[C_TT, C_TE, 0], [C_TE, C_EE, 0],
+ * [0, 0, C_BB]] on (a^T, a^E, a^B). The messenger covariance is T = tau 1 on all
+ * three components, tau = the smallest eigenvalue of N_p over the observed
+ * components; Eq. 3 becomes a 3 x 3 solve per pixel,
+ *     t_p = s_p + A_p (d_p - s_p),  A_p = lambda tau (N_p + (lambda - 1) tau 1)^-1,
+ * Eq. 4 the 2 x 2 (T, E) block and B per mode, s = S_l (S_l + lambda tau Omega)^-1 t,
+ * with the basis change applied to t - s. (Q, U) <-> (E, B) by spin-2 harmonics,
+ * Q +- iU = - sum_lm (a^E_lm +- i a^B_lm) _{+-2}Y_lm, _{+-2}Y from the spin-raising
+ * operator on Y_lm (Condon-Shortley phase). Cooling takes lambda from
+ * C_TT / (tau Omega) at l_iter (Sect. 3); the band limit stays at lmax.
+ *   cls       : host [4][lmax+1] = C_TT, C_EE, C_BB, C_TE (beams folded in; C_TE^2 <= C_TT C_EE)
+ *   noise     : host [Npix][4] = (TT, QQ, QU, UU) noise (co)variances per pixel
+ *   mask_t, mask_p : host [Npix] (1 = observed) or NULL (all observed)
+ *   opt       : WF_PREC_FP64 or WF_PREC_FP64_NATIVE for the T channel and the ring
+ *               FFTs (WF_EINVAL for WF_PREC_MIXED); the spin-2 Legendre stage runs in
+ *               FP64 from a table of (F+, F-) per (l, m, ring pair) (16 bytes each,
+ *               64 GiB at most: Nside <= 1024 at lmax = 2 Nside)
+ * a_lm of the three fields are stored one after the other: [3][2*nalm] (T, E, B);
+ * maps likewise [3][Npix] (T, Q, U). */
+typedef struct wf_pol_s *wf_pol_t;
+wf_status wf_pol_create(int nside, int lmax, const double *cls, const double *noise, const uint8_t *mask_t,
+                        const uint8_t *mask_p, const wf_options *opt, wf_pol_t *out);
+
+/* Joint (T, Q, U) solve: d [3][Npix] host or device, alm_out [3][2*nalm] host or
+ * device; stats, records as wf_multi_solve. */
+wf_status wf_pol_solve(wf_pol_t pol, const double *d, int d_on_device, double *alm_out, int alm_on_device,
+                       wf_stats *stats, wf_iter_record *records, int max_records, int *n_records);
+
+/* The transform pair of the polarised fields (device pointers, full band, on the
+ * plan's stream, no sync): maps = Y alm and alm = Y^dagger maps = (4 pi / Npix) Y^T maps. */
+wf_status wf_pol_alm2map(wf_pol_t pol, const double *alm_dev, double *map_dev);
+wf_status wf_pol_map2alm(wf_pol_t pol, const double *map_dev, double *alm_dev);
+
+wf_status wf_pol_destroy(wf_pol_t pol);
+
 /* Serving: continuous batching of solve requests of any (nside, lmax, C_l,
  * noise, mask) under a device-memory budget.
  *   hbm_budget_bytes : admission limit for plans + per-request buffers (0 = 90 % of free memory)

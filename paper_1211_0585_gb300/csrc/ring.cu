@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kRingThreads) ring_kernel(const RingArgs A) {
 
   int L = A.lsht;
   double lam = 1.0;
+  if (MODE != RING_ITER && A.gate && A.gate->done) return;
   if (MODE == RING_ITER) {
     if (A.ctl->done) return;
     L = A.ctl->lsht;

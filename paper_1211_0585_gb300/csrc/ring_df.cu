@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(kRingDfThreads, 3) ring_df_kernel(const RingAr
 
   int L = A.lsht;
   double lam = 1.0;
+  if (MODE != RING_ITER && A.gate && A.gate->done) return;
   if (MODE == RING_ITER) {
     if (A.ctl->done) return;
     L = A.ctl->lsht;

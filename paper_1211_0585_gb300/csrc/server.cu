@@ -177,11 +177,22 @@ Ctl request_ctl(const Plan *shape, const Request &r) {
   return c;
 }
 
-// an FP64 plan: the shape's tables and state, plus the precomputed lambda table
-// when it is within the default limit
-size_t fp64_bytes(int nside, int lmax) {
+// Options of the pool's FP64 plans: the defaults, with the precomputed lambda
+// table allowed up to a fifth of the budget (at most 48 GiB, at least the
+// default 8 GiB), so that on a large GPU the Nside 1024 plans (34 GB table)
+// read the table instead of running the recurrence.
+wf_options fp64_plan_options(size_t budget) {
   wf_options o;
   wf_options_default(&o);
+  const size_t cap = size_t(48) << 30, fifth = budget / 5;
+  o.legendre_table_bytes = std::max(o.legendre_table_bytes, std::min(cap, fifth));
+  return o;
+}
+
+// an FP64 plan: the shape's tables and state, plus the precomputed lambda table
+// when it is within the pool's limit
+size_t fp64_bytes(size_t budget, int nside, int lmax) {
+  const wf_options o = fp64_plan_options(budget);
   const size_t tab = lam_table_rows(lmax) * (size_t)((2 * nside + 31) / 32 * 32) * 16;
   const size_t npix = 12 * (size_t)nside * nside, nalm = (size_t)(lmax + 1) * (lmax + 2) / 2;
   const size_t posterior = 2 * npix * sizeof(double) + 2 * nalm * 16;  // rel_posterior_grad buffers
@@ -394,7 +405,7 @@ void fp64_loop(wf_server_s *S) {
         bytes = idle.back().bytes;
         idle.pop_back();
       } else {
-        bytes = fp64_bytes(r->nside, r->lmax);
+        bytes = fp64_bytes(S->budget, r->nside, r->lmax);
         while (S->fp64_bytes_in_use + bytes > S->budget)
           if (Plan *v = evict_idle_fp64(S)) victims.push_back(v);
           else break;
@@ -411,8 +422,7 @@ void fp64_loop(wf_server_s *S) {
       ++S->fp64_busy;
     }
     for (Plan *v : victims) wf_plan_destroy(v);
-    wf_options o;
-    wf_options_default(&o);
+    wf_options o = fp64_plan_options(S->budget);
     o.tol = r->tol;
     wf_status st = WF_OK;
     if (plan) {
@@ -507,7 +517,7 @@ wf_status wf_submit(wf_server_t S, int nside, int lmax, const double *cl, const 
   if (r->n_obs == 0) { set_error("wf_submit: no observed pixel"); return WF_EINVAL; }
   r->tau = tau;
   // a request no path of which fits the whole budget could never be admitted
-  const bool fp64_fits = fp64_bytes(nside, lmax) <= S->budget;
+  const bool fp64_fits = fp64_bytes(S->budget, nside, lmax) <= S->budget;
   const bool engine_fits = engine_bytes(nside, lmax, S->max_batch) <= S->budget;
   const bool to_fp64 = tol <= kFp64Tol || !engine_fits;
   if (to_fp64 && !fp64_fits) {
@@ -587,7 +597,7 @@ wf_status wf_server_warm(wf_server_t S, int nside, int lmax, int precision) {
     return w->status;
   }
   if (precision != WF_PREC_FP64) { set_error("wf_server_warm: precision must be WF_PREC_MIXED or WF_PREC_FP64"); return WF_EINVAL; }
-  const size_t bytes = fp64_bytes(nside, lmax);
+  const size_t bytes = fp64_bytes(S->budget, nside, lmax);
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->fp64_bytes_in_use + bytes > S->budget) {
@@ -598,7 +608,8 @@ wf_status wf_server_warm(wf_server_t S, int nside, int lmax, int precision) {
   }
   std::vector<double> unit(12LL * nside * nside, 1.0), cl(lmax + 1, 1.0);
   wf_plan_t p = nullptr;
-  const wf_status st = wf_plan_create(nside, lmax, cl.data(), unit.data(), nullptr, nullptr, &p);
+  const wf_options o = fp64_plan_options(S->budget);
+  const wf_status st = wf_plan_create(nside, lmax, cl.data(), unit.data(), nullptr, &o, &p);
   std::lock_guard<std::mutex> lk(S->mu);
   if (st != WF_OK) {
     S->fp64_bytes_in_use -= bytes;

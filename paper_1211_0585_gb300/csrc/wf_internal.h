@@ -107,6 +107,7 @@ struct RingArgs {
   double omega, tau;
   double *gain;           // [npix] cached w / (1 + (lambda - 1) tau w) (double-float ring kernel)
   double *gainlam;        // [R] lambda the cached gains of each ring belong to (-1: none)
+  const Ctl *gate;        // RING_SYNTH / RING_ANALYSIS inside a controlled iteration: skip once gate->done
 };
 
 struct LegArgs {

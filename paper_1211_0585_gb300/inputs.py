@@ -132,25 +132,58 @@ def mask_band(z: np.ndarray, sin_b: float) -> np.ndarray:
     return (np.abs(z) >= sin_b).astype(np.uint8)
 
 
+def _rings_of(z):
+    """Start index of each HEALPix ring in a RING-ordered z array (z is constant along a ring)."""
+    starts = np.flatnonzero(np.diff(z) != 0.0) + 1
+    return np.concatenate([[0], starts, [z.size]])
+
+
 def mask_discs(z, phi, mask, ndisc: int, radius_deg: float, rng) -> np.ndarray:
-    """Zero `ndisc` discs of radius `radius_deg` at uniform random positions."""
+    """Zero `ndisc` discs of radius `radius_deg` at uniform random positions
+    (every pixel whose centre is within the radius)."""
     out = mask.copy()
     if ndisc <= 0:
         return out
-    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
-    x, y = s * np.cos(phi), s * np.sin(phi)
     cz = rng.uniform(-1.0, 1.0, ndisc)
     cphi = rng.uniform(0.0, 2.0 * math.pi, ndisc)
     cs = np.sqrt(1.0 - cz * cz)
     cosr = math.cos(math.radians(radius_deg))
-    # discs are small: pre-select pixels by a z window, then test the angle
+    sinr = math.sin(math.radians(radius_deg))
+    rb = _rings_of(z)
+    zr = z[rb[:-1]]                      # ring z, decreasing
+    nzr = -zr
     for k in range(ndisc):
-        cx, cy = cs[k] * math.cos(cphi[k]), cs[k] * math.sin(cphi[k])
-        lo = np.searchsorted(-z, -(min(1.0, cz[k] + 0.01745 * radius_deg * 1.01)), side="left")
-        hi = np.searchsorted(-z, -(max(-1.0, cz[k] - 0.01745 * radius_deg * 1.01)), side="right")
-        sl = slice(lo, hi)
-        inside = x[sl] * cx + y[sl] * cy + z[sl] * cz[k] >= cosr
-        out[sl][inside] = 0
+        # rings within the disc's z range, and on each the pixels within its phi range (candidates),
+        # then the exact angle test on the candidates
+        r0 = np.searchsorted(nzr, -min(1.0, cz[k] + sinr) - 1e-12, side="left")
+        r1 = np.searchsorted(nzr, -max(-1.0, cz[k] - sinr) + 1e-12, side="right")
+        for r in range(r0, r1):
+            a, b = rb[r], rb[r + 1]
+            n = b - a
+            sr = math.sqrt(max(0.0, 1.0 - zr[r] * zr[r]))
+            den = sr * cs[k]
+            num = cosr - zr[r] * cz[k]
+            if den <= 0.0:
+                cand = np.arange(a, b) if num <= 0.0 else np.arange(0)
+            else:
+                c = num / den
+                if c > 1.0:
+                    continue
+                if c <= -1.0:
+                    cand = np.arange(a, b)
+                else:
+                    dphi = math.acos(c)
+                    step = 2.0 * math.pi / n
+                    j0 = int(math.floor((cphi[k] - dphi - phi[a]) / step)) - 1
+                    j1 = int(math.ceil((cphi[k] + dphi - phi[a]) / step)) + 1
+                    if j1 - j0 + 1 >= n:
+                        cand = np.arange(a, b)
+                    else:
+                        cand = a + np.mod(np.arange(j0, j1 + 1), n)
+            if cand.size:
+                dot = sr * np.cos(phi[cand]) * cs[k] * math.cos(cphi[k]) + \
+                    sr * np.sin(phi[cand]) * cs[k] * math.sin(cphi[k]) + zr[r] * cz[k]
+                out[cand[dot >= cosr]] = 0
     return out
 
 

@@ -27,6 +27,7 @@ EXPORTED = ["wf_options_default", "wf_plan_create", "wf_plan_destroy", "wf_plan_
             "wf_alm2map", "wf_map2alm", "wf_map2alm_noalloc", "wf_iterate", "wf_profile_iterations", "wf_solve",
             "wf_solve_history", "wf_solve_batch", "wf_constrained_realisations",
             "wf_multi_create", "wf_multi_solve", "wf_multi_destroy",
+            "wf_pol_create", "wf_pol_solve", "wf_pol_alm2map", "wf_pol_map2alm", "wf_pol_destroy",
             "wf_server_create", "wf_submit", "wf_poll", "wf_cancel", "wf_server_warm", "wf_server_drain", "wf_server_stats",
             "wf_server_destroy", "wf_last_error"]
 
@@ -107,6 +108,12 @@ def load(path: str = LIB_PATH):
         "wf_multi_solve": [_vp, _vp, _i, _vp, _i, ctypes.POINTER(Stats), ctypes.POINTER(IterRecord), _i,
                            ctypes.POINTER(_i)],
         "wf_multi_destroy": [_vp],
+        "wf_pol_create": [_i, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(Options), ctypes.POINTER(_vp)],
+        "wf_pol_solve": [_vp, _vp, _i, _vp, _i, ctypes.POINTER(Stats), ctypes.POINTER(IterRecord), _i,
+                         ctypes.POINTER(_i)],
+        "wf_pol_alm2map": [_vp, _vp, _vp],
+        "wf_pol_map2alm": [_vp, _vp, _vp],
+        "wf_pol_destroy": [_vp],
         "wf_server_create": [ctypes.c_size_t, _i, ctypes.POINTER(_vp)],
         "wf_submit": [_vp, _i, _i, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(ctypes.c_uint64)],
         "wf_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(_i), _vp, ctypes.POINTER(Stats)],
@@ -333,6 +340,55 @@ class Multi:
     def close(self):
         if getattr(self, "handle", None):
             load().wf_multi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pol:
+    """Owns a wf_pol_t: the joint Wiener filter of (T, Q, U) maps."""
+
+    def __init__(self, nside, lmax, cls, noise, mask_t=None, mask_p=None, opts: Options | None = None):
+        self.nside, self.lmax = nside, lmax
+        self._cls = np.ascontiguousarray(np.stack(cls), dtype=np.float64)
+        self._noise = np.ascontiguousarray(noise, dtype=np.float64)
+        self._mt = None if mask_t is None else np.ascontiguousarray(mask_t, dtype=np.uint8)
+        self._mp = None if mask_p is None else np.ascontiguousarray(mask_p, dtype=np.uint8)
+        h = ctypes.c_void_p()
+        _check(load().wf_pol_create(nside, lmax, _host_ptr(self._cls), _host_ptr(self._noise), _host_ptr(self._mt),
+                                    _host_ptr(self._mp), ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def nalm(self):
+        return (self.lmax + 1) * (self.lmax + 2) // 2
+
+    def alm2map(self, alm_dev: int, map_dev: int):
+        _check(load().wf_pol_alm2map(self.handle, ctypes.c_void_p(alm_dev), ctypes.c_void_p(map_dev)))
+
+    def map2alm(self, map_dev: int, alm_dev: int):
+        _check(load().wf_pol_map2alm(self.handle, ctypes.c_void_p(map_dev), ctypes.c_void_p(alm_dev)))
+
+    def solve(self, d, history=0):
+        """d: [3][Npix] host (T, Q, U). Returns (alm [3][nalm], stats, status, records)."""
+        dh = np.ascontiguousarray(d, dtype=np.float64)
+        out = np.empty((3, self.nalm), dtype=np.complex128)
+        st = Stats()
+        recs = (IterRecord * max(1, history))()
+        n = ctypes.c_int()
+        status = load().wf_pol_solve(self.handle, _host_ptr(dh), 0, out.ctypes.data_as(ctypes.c_void_p), 0,
+                                     ctypes.byref(st), recs, history, ctypes.byref(n))
+        _check(status, ok=(WF_OK, WF_ENOTCONVERGED))
+        return out, st.as_dict(), status, [recs[i].as_dict() for i in range(n.value)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().wf_pol_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -223,3 +223,32 @@ def test_paper_stop_rule_stops_on_oracle_iteration(prec):
     assert st["iters"] == ores.iters
     assert [(r["lam"], r["lsht"]) for r in recs] == [(h["lam"], h["lsht"]) for h in ores.history]
     assert O.rel_l2(alm, ores.alm, lmax) < TOL
+
+
+def test_table_form_first_iteration_nside1024():
+    """The lambda-table form at Nside 1024 / lmax 2048 (34 GB table, ring pairs in two analysis chunks of
+    1024), as the serving pool runs it on a large GPU: the first iteration from s = 0 on sampled modes
+    against the oracle, one by one."""
+    import torch
+    from paper_1211_0585_gb300 import inputs as I
+    nside, lmax = 1024, 2048
+    p = I.wmap_problem(seed=2, nside=nside, lmax=lmax, ndisc=50, noise_scale=4.0)
+    rng = np.random.default_rng(8)
+    d = rng.standard_normal(p.npix) * np.sqrt(p.noise_var) + 30.0 * np.sin(5 * np.arange(p.npix) / p.npix)
+    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(legendre_table_bytes=48 << 30))
+    held, _ = P.legendre_table(lmax)
+    assert held > 30e9
+    lam = 3.0
+    s = torch.zeros(2 * P.nalm, dtype=torch.float64, device="cuda")
+    P.iterate(dev(d).data_ptr(), s.data_ptr(), lam, lmax, 1, reset=True)
+    got = host_alm(s)
+    tau = O.messenger_tau(p.noise_var, p.mask)
+    w = O.inverse_noise(p.noise_var, p.mask)
+    u = O.pixel_gain(lam, tau, w) * d
+    f = O.harmonic_filter(lam, tau, 4 * math.pi / p.npix, p.cl)
+    ls = np.array([2, 17, 300, 1024, 2048, 1500, 1100, 2000, 64, 1030])
+    ms = np.array([0, 3, 299, 0, 2047, 1490, 1, 1999, 64, 1025])
+    ref = f[ls] * O.map2alm_modes(nside, lmax, u, ls, ms)
+    scale = np.sqrt(np.mean(np.abs(got) ** 2))
+    assert np.max(np.abs(got[O.alm_index(lmax, ls, ms)] - ref)) <= 1e-10 * scale
+    P.close()
