@@ -359,6 +359,11 @@ def run_ours(args):
             result["constrained_realisations"] = constrained_realisations_run(prob, dmap)
         P.close()
         torch.cuda.empty_cache()
+        with progress("multi"):
+            result["multi"] = multi_run(prob)
+        with progress("polarisation"):
+            result["polarisation"] = polarisation_run()
+        torch.cuda.empty_cache()
         if not args.no_planck:
             with progress("planck"):
                 result["planck"] = planck_run()
@@ -612,6 +617,69 @@ def planck_run(iters=8, slots=8, seed=1):
     out["note"] = f"host generation of the inputs {t_gen:.0f} s; timing: host wall clock around solves of " \
                   f"{iters} iterations (FP64: one map; mixed: the same map in every slot)"
     return out
+
+
+def polarisation_run(iters=10, seed=1):
+    """Temperature and polarisation at the bench size (WMAP-shaped T + P, Nside 512 / lmax 1024): ms per
+    full-band iteration of wf_pol_solve (fixed iterations, lambda = 1) and of its transform pair."""
+    import torch
+    from paper_1211_0585_gb300 import inputs as I
+    from paper_1211_0585_gb300 import wf
+    pp = I.pol_wmap_problem(seed=seed, nside=NSIDE, lmax=LMAX)
+    Q = wf.Pol(NSIDE, LMAX, pp.cls, pp.noise_cov, pp.mask_t, pp.mask_p,
+               wf.options(tol=0.0, max_iter=iters, cooling=0))
+    a = torch.from_numpy(pp.alm_true.view(np.float64).copy().reshape(-1)).cuda()
+    m = torch.empty(3 * 12 * NSIDE * NSIDE, dtype=torch.float64, device="cuda")
+    Q.alm2map(a.data_ptr(), m.data_ptr())
+    torch.cuda.synchronize()
+    d = m.cpu().numpy().reshape(3, -1) + pp.noise
+    Q.solve(d)                                   # graph capture
+    t0 = time.perf_counter()
+    _, st, _, _ = Q.solve(d)
+    ms_it = 1e3 * (time.perf_counter() - t0) / iters
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2 = torch.empty_like(a)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        Q.alm2map(a.data_ptr(), m.data_ptr())
+        Q.map2alm(m.data_ptr(), a2.data_ptr())
+    e1.record()
+    e1.synchronize()
+    pair = e0.elapsed_time(e1) / 3
+    Q.close()
+    return {"workload": "WMAP-shaped T + P, Nside 512 / lmax 1024, 3x3 pixel noise, T and P masks",
+            "ms_per_iteration": round(ms_it, 2), "iterations": iters, "transform_pair_ms": round(pair, 2),
+            "chi2_per_dof_after": st["chi2_per_dof"],
+            "timing": "host wall clock around wf_pol_solve of fixed full-band iterations; CUDA events around "
+                      "wf_pol_alm2map + wf_pol_map2alm (default stream)"}
+
+
+def multi_run(prob, iters=10):
+    """Several messenger fields at the bench size: two maps of the WMAP-shaped sky (13' and 30' beams, the
+    second with twice the noise and its own mask), ms per full-band iteration of wf_multi_solve."""
+    import torch
+    from paper_1211_0585_gb300 import inputs as I
+    from paper_1211_0585_gb300 import wf
+    ell = np.arange(LMAX + 1)
+    beams = [np.ones(LMAX + 1), np.exp(-0.5 * ell * (ell + 1) * (math.radians(30.0 / 60) / math.sqrt(8 * math.log(2))) ** 2)]
+    cl = prob.cl
+    z, phi = I.pixel_centres(NSIDE)
+    mask2 = I.mask_band(z, 0.3)
+    var2 = 2.0 * prob.noise_var
+    rng = np.random.default_rng(9)
+    M = wf.Multi(NSIDE, LMAX, cl, [prob.noise_var, var2], [prob.mask, mask2], beams,
+                 wf.options(tol=0.0, max_iter=iters, cooling=0))
+    d1 = prob.data(np.zeros(prob.npix))
+    d2 = rng.standard_normal(prob.npix) * np.sqrt(var2)
+    M.solve([d1, d2])                           # graph capture
+    t0 = time.perf_counter()
+    M.solve([d1, d2])
+    ms_it = 1e3 * (time.perf_counter() - t0) / iters
+    M.close()
+    return {"workload": "two maps of the WMAP-shaped sky, Nside 512 / lmax 1024 (13' and 30' beams)",
+            "ms_per_iteration": round(ms_it, 2), "iterations": iters,
+            "timing": "host wall clock around wf_multi_solve of fixed full-band iterations"}
 
 
 def constrained_realisations_run(prob, dmap, nreal=63):

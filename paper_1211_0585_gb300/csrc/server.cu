@@ -9,7 +9,8 @@
 //     of an engine by a block of iterations; finished slots are harvested and
 //     refilled before the next step, so a request that arrives while others
 //     iterate joins at the next step with its own lambda schedule.
-//   - tol <= 1e-7 (FP64 path): on kFp64Workers worker threads, each solve on
+//   - tol <= 1e-7 (FP64 path): on kFp64Workers worker threads (shortest job
+//     first, by Nside, unless a request has waited kFp64MaxWait), each solve on
 //     a plan of its shape taken from a pool (created on first use within the
 //     budget, re-pointed at the request's C_l, noise and mask by plan_rebind,
 //     returned afterwards), so that geometry, Legendre and lambda tables stay
@@ -51,6 +52,7 @@ namespace {
 
 constexpr double kFp64Tol = 1e-7;
 constexpr int kFp64Workers = 3;
+constexpr auto kFp64MaxWait = std::chrono::seconds(20);
 
 struct Request {
   uint64_t ticket = 0;
@@ -87,6 +89,8 @@ struct ShapeRunner {
   std::unique_ptr<Engine> engine;
   std::vector<std::shared_ptr<Request>> slot;  // request in each slot (or null)
   size_t bytes = 0;
+  bool in_flight = false;             // a step launched and not yet harvested
+  bool dirty = false;                 // slots changed since the live band limit was computed
   Clock::time_point last_used;
   ~ShapeRunner() {
     engine.reset();
@@ -237,7 +241,7 @@ ShapeRunner *runner_for(wf_server_s *S, int nside, int lmax) {
     // evict the least recently used idle runner
     auto victim = S->runners.end();
     for (auto jt = S->runners.begin(); jt != S->runners.end(); ++jt)
-      if (jt->second->live() == 0 &&
+      if (jt->second->live() == 0 && !jt->second->in_flight &&
           (victim == S->runners.end() || jt->second->last_used < victim->second->last_used))
         victim = jt;
     if (victim == S->runners.end()) {
@@ -261,7 +265,9 @@ ShapeRunner *runner_for(wf_server_s *S, int nside, int lmax) {
   R->shape = static_cast<Plan *>(p);
   R->engine = std::make_unique<Engine>();
   if (R->engine->create(R->shape, S->max_batch, R->shape->stream) != WF_OK) return nullptr;
-  R->engine->graph_iters = 8;
+  // iterations per engine step by shape, so that a step of any shape takes a few ms and a large shape's
+  // step does not hold back the harvest of a small one (one iteration at Nside 1024 is ~30 ms)
+  R->engine->graph_iters = nside <= 128 ? 32 : nside <= 256 ? 16 : nside <= 512 ? 4 : 1;
   R->slot.assign(S->max_batch, nullptr);
   R->bytes = need;
   R->last_used = Clock::now();
@@ -278,7 +284,7 @@ void worker_loop(wf_server_s *S) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
       bool busy = false;
-      for (auto &kv : S->runners) busy |= kv.second->live() > 0;
+      for (auto &kv : S->runners) busy |= kv.second->live() > 0 || kv.second->in_flight;
       if (!busy)
         S->cv.wait_for(lk, std::chrono::milliseconds(20),
                        [&] { return S->stop || !S->pending.empty() || !S->warm_queue.empty(); });
@@ -296,7 +302,6 @@ void worker_loop(wf_server_s *S) {
       S->cv_done.notify_all();
     }
     std::vector<std::shared_ptr<Request>> keep;
-    std::map<ShapeRunner *, bool> changed;
     for (auto &r : take) {
       if (r->cancel.load()) {
         r->status = WF_ECANCELLED;
@@ -315,6 +320,9 @@ void worker_loop(wf_server_s *S) {
         }
       }
       ShapeRunner *R = runner_for(S, r->nside, r->lmax);
+      // a stepping engine is not loaded: its pending copy of the controllers to the host would
+      // overwrite the new slot's host controller before that is copied to the device
+      if (R && R->in_flight) { keep.push_back(r); continue; }
       int b = -1;
       if (R)
         for (int i = 0; i < (int)R->slot.size(); ++i)
@@ -328,21 +336,33 @@ void worker_loop(wf_server_s *S) {
       }
       R->slot[b] = r;
       r->t_slot = Clock::now();
-      changed[R] = true;
+      R->dirty = true;
     }
     if (!keep.empty()) {
       std::lock_guard<std::mutex> lk(S->mu);
       S->pending.insert(S->pending.begin(), keep.begin(), keep.end());
     }
-    // one step of every engine with live slots (their streams overlap on the device)
+    // launch a step of every engine with live slots that is not already stepping (their streams
+    // overlap on the device), then harvest the engines whose step has finished; an engine still
+    // stepping is left running, so small shapes are served while a large one works
+    for (auto &kv : S->runners) {
+      ShapeRunner *R = kv.second.get();
+      if (R->live() == 0 || R->in_flight) continue;
+      if (R->dirty) { R->engine->refresh_state(); R->dirty = false; }
+      if (R->engine->step() == WF_OK) R->in_flight = true;
+    }
     std::vector<ShapeRunner *> stepped;
     for (auto &kv : S->runners) {
       ShapeRunner *R = kv.second.get();
-      if (R->live() == 0) continue;
-      if (changed.count(R)) R->engine->refresh_state();
-      if (R->engine->step() == WF_OK) stepped.push_back(R);
+      if (R->in_flight && cudaStreamQuery(R->engine->stream) != cudaErrorNotReady) stepped.push_back(R);
+    }
+    if (stepped.empty()) {
+      bool any = false;
+      for (auto &kv : S->runners) any |= kv.second->in_flight;
+      if (any) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     for (ShapeRunner *R : stepped) {
+      R->in_flight = false;
       R->engine->sync_host();
       R->last_used = Clock::now();
       bool any = false;
@@ -382,7 +402,7 @@ void worker_loop(wf_server_s *S) {
         r.reset();
         any = true;
       }
-      if (any) R->engine->refresh_state();
+      if (any) R->dirty = true;
     }
   }
 }
@@ -398,7 +418,16 @@ void fp64_loop(wf_server_s *S) {
       S->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return S->stop || !S->fp64_queue.empty(); });
       if (S->stop) return;
       if (S->fp64_queue.empty()) continue;
-      r = S->fp64_queue.front();
+      // shortest job first (smallest Nside, then arrival), except that a request queued for more than
+      // kFp64MaxWait goes first: small requests are not held behind minutes of large solves, and a
+      // large one is not starved
+      auto pick = S->fp64_queue.begin();
+      const auto now = Clock::now();
+      for (auto it = S->fp64_queue.begin(); it != S->fp64_queue.end(); ++it) {
+        if (now - (*it)->t_submit > kFp64MaxWait) { pick = it; break; }
+        if ((*it)->nside < (*pick)->nside) pick = it;
+      }
+      r = *pick;
       auto &idle = S->fp64_idle[std::make_pair(r->nside, r->lmax)];
       if (!idle.empty()) {  // a resident plan of the shape
         plan = idle.back().plan;
@@ -418,7 +447,7 @@ void fp64_loop(wf_server_s *S) {
         }
         S->fp64_bytes_in_use += bytes;
       }
-      S->fp64_queue.pop_front();
+      S->fp64_queue.erase(std::find(S->fp64_queue.begin(), S->fp64_queue.end(), r));
       ++S->fp64_busy;
     }
     for (Plan *v : victims) wf_plan_destroy(v);

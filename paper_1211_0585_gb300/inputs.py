@@ -249,6 +249,54 @@ def planck_problem(seed: int = 1, nside: int = 2048, lmax: int = 4096) -> Proble
     return Problem(nside, lmax, cl, var, mask, alm, noise, name=f"planck_ns{nside}_l{lmax}_s{seed}")
 
 
+@dataclass
+class PolProblem:
+    """A temperature-polarisation problem: spectra (TT, EE, BB, TE), per-pixel noise (TT, QQ, QU, UU),
+    temperature and polarisation masks, the true (T, E, B) a_lm and a noise realisation [3][Npix]."""
+    nside: int
+    lmax: int
+    cls: tuple
+    noise_cov: np.ndarray
+    mask_t: np.ndarray
+    mask_p: np.ndarray
+    alm_true: np.ndarray
+    noise: np.ndarray
+
+
+def pol_wmap_problem(seed: int = 1, nside: int = 512, lmax: int = 1024, ndisc: int = 500,
+                     fwhm_arcmin: float = 13.0) -> PolProblem:
+    """WMAP-shaped T + P: C_TT as wmap_problem, C_EE = C_TT / 30, C_BB = C_TT / 1000, C_TE = 0.3 sqrt(TT EE);
+    noise sigma_T^2 = 2200^2 / h, Q and U twice that with a Q-U correlation of up to 0.2; temperature mask as
+    wmap_problem, polarisation mask a 30 % band cut plus the same discs."""
+    rng = np.random.default_rng(seed)
+    tt = cl_lcdm_like(lmax, fwhm_arcmin)
+    ee, bb = tt / 30.0, tt / 1000.0
+    te = 0.3 * np.sqrt(tt * ee)
+    z, phi = pixel_centres(nside)
+    npix = z.size
+    h = 1.0 + 7.0 * np.abs(sin_ecliptic_latitude(z, phi))
+    cov = np.zeros((npix, 4))
+    cov[:, 0] = 2200.0 ** 2 / h
+    cov[:, 1] = 2.0 * cov[:, 0]
+    cov[:, 3] = 2.0 * cov[:, 0]
+    cov[:, 2] = 0.2 * cov[:, 1] * rng.uniform(-1.0, 1.0, npix)
+    mt = mask_discs(z, phi, mask_band(z, 0.2), ndisc, 0.5, rng)
+    mp = mt & mask_band(z, 0.3)
+    g1, g2, g3 = draw_alm(np.ones(lmax + 1), rng), draw_alm(np.ones(lmax + 1), rng), draw_alm(np.ones(lmax + 1), rng)
+    ls, _ = alm_lm_arrays(lmax)
+    safe = np.where(tt[ls] > 0, tt[ls], 1.0)
+    a_t = np.sqrt(tt[ls]) * g1
+    a_e = np.where(tt[ls] > 0, te[ls] / np.sqrt(safe), 0.0) * g1 + \
+        np.sqrt(np.maximum(ee[ls] - np.where(tt[ls] > 0, te[ls] ** 2 / safe, 0.0), 0.0)) * g2
+    a_b = np.sqrt(bb[ls]) * g3
+    e1, e2, e3 = rng.standard_normal(npix), rng.standard_normal(npix), rng.standard_normal(npix)
+    l11 = np.sqrt(cov[:, 1])
+    l21 = cov[:, 2] / l11
+    l22 = np.sqrt(cov[:, 3] - l21 ** 2)
+    noise = np.array([np.sqrt(cov[:, 0]) * e1, l11 * e2, l21 * e2 + l22 * e3])
+    return PolProblem(nside, lmax, (tt, ee, bb, te), cov, mt, mp, np.array([a_t, a_e, a_b]), noise)
+
+
 def fluctuation_draws(prob: Problem, nrhs: int, seed0: int = 1):
     """Per-RHS signal and noise fluctuations for constrained-realisation style
     batches: a_i ~ N(0, C_l), n_i ~ N(0, sigma^2), seeds seed0 .. seed0+nrhs-1."""
