@@ -475,12 +475,5 @@ extern "C" wf_status wf_solve_batch(wf_plan_t plan, int nrhs, const double *d, i
   Plan *P = static_cast<Plan *>(plan);
   if (P->opt.precision == WF_PREC_MIXED)
     return solve_mixed(P, nrhs, d, d_on_device, alm_out, alm_on_device, stats);
-  wf_status worst = WF_OK;
-  for (int i = 0; i < nrhs; ++i) {
-    const wf_status st = wf_solve(plan, d + (size_t)i * P->npix, d_on_device, alm_out + (size_t)i * 2 * P->nalm,
-                                  alm_on_device, nullptr, stats ? stats + i : nullptr);
-    if (st != WF_OK && st != WF_ENOTCONVERGED) return st;
-    if (st != WF_OK) worst = st;
-  }
-  return worst;
+  return solve_fp64_batch(P, nrhs, d, d_on_device, alm_out, alm_on_device, stats);
 }

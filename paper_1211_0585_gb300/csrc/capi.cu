@@ -54,6 +54,7 @@ wf_status Plan::dalloc(void **p, size_t bytes) {
 
 Plan::~Plan() {
   delete engine;
+  destroy_f64_batch(f64batch);
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
   for (void *p : allocs) cudaFree(p);
   if (h_ctl) cudaFreeHost(h_ctl);
@@ -793,6 +794,8 @@ static wf_status solve_impl(Plan *P, const double *d, int d_on_device, double *a
 }  // extern "C"
 
 namespace wfk {
+
+wf_status posterior_grad_plan(Plan *P, cudaStream_t s, double *rel) { return posterior_grad(P, s, rel); }
 
 wf_status refine_fp64(Plan *P, const double *d, int d_on_device, const double *alm_dev, double *alm_out,
                       int alm_on_device, wf_stats *stats) {

@@ -138,6 +138,24 @@ struct LegDfArgs {
   const long long *poff;  // [lmax+1] first table row of each m
 };
 
+// Per-map buffers of the batched FP64 Legendre stage (legendre_batch.cu): up to
+// kLegBatchMax maps of one shape, each with its own Fourier arrays, state, C_l,
+// tau, partial sums and controller.
+constexpr int kLegBatchMax = 2;
+constexpr int kSynRowsB = 4;      // batched synthesis: table rows per load batch
+struct LegBatchMaps {
+  int n;                          // maps in use (the rest are skipped)
+  const double4_32a *FT[kLegBatchMax];
+  double4_32a *FS[kLegBatchMax];
+  double2 *alm[kLegBatchMax];
+  double *m_part[kLegBatchMax];
+  const Ctl *ctl[kLegBatchMax];
+  const double *cl[kLegBatchMax];
+  double tau[kLegBatchMax];
+};
+size_t leg_batch_smem(int nb, int lmax, int RP);
+void launch_legendre_batch(const LegArgs &a, const LegDfArgs &d, const LegBatchMaps &bm, int nb, cudaStream_t s);
+
 // Double-float copies of the ring-stage tables (ring_df.cu): float4 =
 // (re hi, re lo, im hi, im lo).
 struct RingDfArgs {

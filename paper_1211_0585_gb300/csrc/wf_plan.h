@@ -15,9 +15,12 @@ struct wf_plan_s {
 namespace wfk {
 
 struct Engine;
+struct F64Batch;
+void destroy_f64_batch(F64Batch *b);
 
 struct Plan : wf_plan_s {
   Engine *engine = nullptr;  // batched engine of this shape (mixed precision), built on first use
+  F64Batch *f64batch = nullptr;  // batched FP64 solves (batch_fp64.cu): per-map buffers, built on first use
   int nside = 0, lmax = 0, R = 0, RP = 0;
   long long npix = 0, nalm = 0, n_obs = 0;
   double tau = 0.0, omega = 0.0;
@@ -117,6 +120,14 @@ wf_status plan_rebind(Plan *P, const double *cl, const double *w, double tau, lo
 // refined figures replace those of stats (iterations and time are added).
 wf_status refine_fp64(Plan *P, const double *d, int d_on_device, const double *alm_dev, double *alm_out,
                       int alm_on_device, wf_stats *stats);
+
+// rel_posterior_grad of the plan's state d_s against its data d_d (capi.cu).
+wf_status posterior_grad_plan(Plan *P, cudaStream_t s, double *rel);
+
+// FP64 solves of nrhs right-hand sides in groups that share the Legendre stage (batch_fp64.cu);
+// plans without a lambda table solve them one by one.
+wf_status solve_fp64_batch(Plan *P, int nrhs, const double *d, int d_on_device, double *alm_out, int alm_on_device,
+                           wf_stats *stats);
 
 // Mixed-precision solves through the plan's batched engine (batch.cu).
 wf_status solve_mixed(Plan *P, int nrhs, const double *d, int d_on_device, double *alm_out, int alm_on_device,

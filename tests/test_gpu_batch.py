@@ -181,3 +181,30 @@ def test_batch64_engine_matches_oracle_and_alone(nside, lmax):
     assert max(errs) <= MIXED_TOL, f"worst right-hand side vs oracle {max(errs):.3e} (#{int(np.argmax(errs))})"
     assert max(alone_errs) <= 1.0, f"worst batched vs alone {max(alone_errs):.3f} of its bar"
     assert sum(s == 0 for s in shifts) >= len(shifts) // 2   # most stop on the oracle's own iteration
+
+
+@pytest.mark.parametrize("nrhs", [2, 5])
+def test_batched_fp64_equals_single_solves_and_oracle(nrhs):
+    """wf_solve_batch on an FP64 plan (lambda table): groups of right-hand sides
+    share one Legendre launch per iteration (each table row read once for the
+    group), and each map's result is its single solve's bit for bit (the same
+    arithmetic in the same order) and the oracle's within the FP64 bar; a
+    ragged last group (5 = 2 + 2 + 1) leaves its empty map stopped."""
+    nside, lmax = 32, 64
+    p, _ = problem("wmap-cooled", seed=31, nside=nside, lmax=lmax)
+    D = rhs_set(p, nrhs, seed0=201)
+    opts = dict(tol=1e-8, max_iter=4000)
+    P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(**opts))
+    assert P.legendre_table(lmax)[0] > 0
+    out, stats, status = P.solve_batch(D)
+    assert status == wf.WF_OK
+    Q = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask, wf.options(**opts))
+    for i in range(nrhs):
+        alone, st1, _, _ = Q.solve(D[i])
+        assert stats[i]["iters"] == st1["iters"] and stats[i]["converged"] == 1
+        assert np.array_equal(out[i], alone), i
+        assert stats[i]["chi2"] == st1["chi2"]
+        assert abs(stats[i]["rel_posterior_grad"] - st1["rel_posterior_grad"]) <= 1e-6 * st1["rel_posterior_grad"]
+    refs = oracle_solves([(nside, lmax, p.cl, p.noise_var, p.mask, D[i], opts, 0) for i in range(nrhs)])
+    for i in range(nrhs):
+        assert O.rel_l2(out[i], refs[i][1][refs[i][0]], lmax) < 1e-10
