@@ -107,8 +107,11 @@ typedef struct {
   double refine_tol;     /* stop rule of the refinement (0 = run all refine_iters) (0) */
   int synthesis_table;   /* batched engine: 1 keeps the synthesis-ordered FP32 Legendre table resident;
                             0 rebuilds it band by band of m from the analysis table every iteration (half
-                            the table memory, one transpose pass more); -1 chooses 1 when the engine fits
-                            the free device memory with it (-1) */
+                            the table memory, one transpose pass more); 2 keeps both tables resident and
+                            split into their two tf32 parts (twice the table memory; the GEMMs then make
+                            no split of their own, same results bit for bit); -1 chooses the largest of
+                            2, 1, 0 with which the engine fits the free device memory (-1; the server's
+                            engines choose between 1 and 0) */
   void *stream;          /* cudaStream_t to run on; NULL = the plan's own stream */
 } wf_options;
 

@@ -46,7 +46,7 @@ static void make_tc_lists(int lmax, int RPp, std::vector<int4> &ana, std::vector
 
 static int round_up(int v, int q) { return (v + q - 1) / q * q; }
 
-size_t Engine::bytes_needed(int nside, int lmax, int nslots) {
+size_t Engine::bytes_needed(int nside, int lmax, int nslots, int mode) {
   const size_t RP = 2 * (size_t)nside, R = 4 * (size_t)nside - 1, npix = 12 * (size_t)nside * nside;
   const size_t RPp = (size_t)round_up((int)RP, 32);
   const size_t nalm = nalm_of(lmax), nF = (size_t)(lmax + 1) * RP;
@@ -57,9 +57,9 @@ size_t Engine::bytes_needed(int nside, int lmax, int nslots) {
       nchunks += (size_t)(n_par(m, p, lmax) + 31) / 32;
     }
   const size_t B = (size_t)round_up(nslots, 8), L1 = (size_t)lmax + 1, Nc = 2 * B;
-  const size_t tables = (nalm + 32 * nchunks) * RPp * sizeof(float)                            // lamA, lamT
+  const size_t tables = (nalm + 32 * nchunks) * RPp * sizeof(float) * (mode == 2 ? 2 : 1)     // lamA, lamT
                         + sizeof(float2) * (8 * (size_t)nside + 16 * (size_t)nside * nside);  // FP32 FFT tables
-  const size_t operands = (L1 * 2 * RPp + 32 * nchunks) * Nc * sizeof(float);                 // XT, SPT
+  const size_t operands = 3 * (L1 * 2 * RPp + 32 * nchunks) * Nc * sizeof(float);             // XT, SPT (3 parts)
   const size_t per_slot = 2 * nF * sizeof(float4)                                             // FS, FT
                           + nalm * (sizeof(double2) + sizeof(float4))                          // s, sdf
                           + npix * 2 * sizeof(float)                                           // (d, w) in FP32
@@ -123,11 +123,14 @@ TcArgs Engine::tc_args() const {
   t.chunk_info = chunk_info;
   t.lamA = lamA;
   t.lamTs = lamTs;
+  t.pre = pre ? 1 : 0;
+  t.loA = pre ? (int)geo->nalm : 0;                    // rows of lamA's map
+  t.loT = pre ? nchunks * RPp : 0;                     // rows of lamT's map
   return t;
 }
 
 
-wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
+wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_, int max_mode) {
   geo = shape_plan;
   stream = s_;
   if (nslots < 1 || nslots > kBatchMax) { set_error("batched engine: slots must be in [1, 64]"); return WF_EINVAL; }
@@ -142,16 +145,23 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   make_tc_lists(lmax, RPp, ana, syn, off, nchunks);
   natiles = (int)ana.size();
   ntstiles = (int)syn.size();
-  const size_t nXT = (size_t)(lmax + 1) * 2 * RPp * Nc, nSPT = (size_t)nchunks * 32 * Nc;
+  // operands in three tf32 parts (part-major within each 32-wide chunk)
+  const size_t nXT = 3 * (size_t)(lmax + 1) * 2 * RPp * Nc, nSPT = 3 * (size_t)nchunks * 32 * Nc;
   wf_status st;
   // the synthesis-ordered table: resident, or rebuilt band by band of m from the
-  // analysis table each iteration (half the table memory; Nside 2048 needs it)
+  // analysis table each iteration (half the table memory; Nside 2048 needs it);
+  // mode 2 holds both tables split into their tf32 parts (twice the memory, no
+  // split in the GEMMs). Auto: the largest mode up to max_mode that fits.
   int mode = geo->opt.synthesis_table;
   if (mode < 0) {
     size_t fr = 0, tot = 0;
     ENG_CUDA(cudaMemGetInfo(&fr, &tot));
-    mode = bytes_needed(geo->nside, lmax, nslots) + ((size_t)1 << 30) <= fr ? 1 : 0;
+    mode = 0;
+    for (int md = std::min(max_mode, 2); md >= 1 && mode == 0; --md)
+      if (bytes_needed(geo->nside, lmax, nslots, md) + ((size_t)1 << 30) <= fr) mode = md;
   }
+  pre = mode == 2;
+  const size_t tsplit = pre ? 2 : 1;
   std::vector<int4> cinfo;
   size_t band_chunks = 0;
   bands.clear();
@@ -179,8 +189,8 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
       m = m1;
     }
   }
-  if ((st = dalloc((void **)&lamA, sizeof(float) * nalm * RPp)) ||
-      (mode == 1 && (st = dalloc((void **)&lamT, sizeof(float) * (size_t)nchunks * 32 * RPp))) ||
+  if ((st = dalloc((void **)&lamA, sizeof(float) * tsplit * nalm * RPp)) ||
+      (mode >= 1 && (st = dalloc((void **)&lamT, sizeof(float) * tsplit * (size_t)nchunks * 32 * RPp))) ||
       (mode == 0 && (st = dalloc((void **)&lamTs, sizeof(float) * band_chunks * 32 * RPp))) ||
       (mode == 0 && (st = dalloc((void **)&chunk_info, sizeof(int4) * cinfo.size()))) ||
       (st = dalloc((void **)&XT, sizeof(float) * nXT)) || (st = dalloc((void **)&SPT, sizeof(float) * nSPT)) ||
@@ -202,9 +212,10 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
       (st = dalloc((void **)&m_part, sizeof(double) * 3 * (size_t)natiles * B)) ||
       (st = dalloc((void **)&bstate, sizeof(int) * 2)) || (st = dalloc((void **)&last, sizeof(wf_iter_record) * B)))
     return st;
-  if (!make_tc_map(&maps.A, lamA, RPp, nalm, 128) || !make_tc_map(&maps.X, XT, 32, nXT / 32, (unsigned)Nc) ||
-      !make_tc_map(&maps.T, mode == 1 ? lamT : lamTs, 32, (mode == 1 ? (size_t)nchunks : band_chunks) * RPp, 128) ||
-      !make_tc_map(&maps.S, SPT, 32, (size_t)nchunks * Nc, (unsigned)Nc)) {
+  if (!make_tc_map(&maps.A, lamA, RPp, tsplit * nalm, 128) || !make_tc_map(&maps.X, XT, 32, nXT / 32, (unsigned)Nc) ||
+      !make_tc_map(&maps.T, mode >= 1 ? lamT : lamTs, 32,
+                   (mode >= 1 ? tsplit * (size_t)nchunks : band_chunks) * RPp, 128) ||
+      !make_tc_map(&maps.S, SPT, 32, nSPT / 32, (unsigned)Nc)) {
     set_error("batched engine: cuTensorMapEncodeTiled failed");
     return WF_ECUDA;
   }
@@ -243,7 +254,8 @@ wf_status Engine::create(Plan *shape_plan, int nslots, cudaStream_t s_) {
   ENG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl) * B, stream));
   ENG_CUDA(cudaMemsetAsync(active, 0, sizeof(int) * B, stream));
   ENG_CUDA(cudaMemsetAsync(last, 0, sizeof(wf_iter_record) * B, stream));
-  launch_lam_tc_tables(geo->d_x, geo->legdf_args(), lmax, RP, RPp, offTc, lamA, mode == 1 ? lamT : nullptr, stream);
+  launch_lam_tc_tables(geo->d_x, geo->legdf_args(), lmax, RP, RPp, offTc, lamA, mode >= 1 ? lamT : nullptr, pre,
+                       nalm * RPp, (size_t)nchunks * 32 * RPp, stream);
   launch_batch_state(args(), bstate, stream);
   ENG_CUDA(cudaGetLastError());
   ENG_CUDA(cudaStreamSynchronize(stream));

@@ -48,6 +48,7 @@ struct Engine {
   int *alm_of_row = nullptr;
   int *err = nullptr, *h_err = nullptr;
   int natiles = 0, ntstiles = 0, nchunks = 0, RPp = 0;
+  bool pre = false;   // tables held split into their tf32 parts (synthesis_table mode 2)
   TcMaps maps{};
   std::vector<int> ring_groups;   // slots per ring-stage CTA of each ring class (autotuned)
   float4 *FS = nullptr, *FT = nullptr;
@@ -69,7 +70,8 @@ struct Engine {
   cudaGraphExec_t graph = nullptr;
 
   ~Engine();
-  wf_status create(Plan *shape_plan, int nslots, cudaStream_t s);
+  // max_mode: the largest synthesis_table mode an automatic choice may take (2: split tables)
+  wf_status create(Plan *shape_plan, int nslots, cudaStream_t s, int max_mode = 2);
   BatchArgs args() const;
   TcArgs tc_args() const;
   wf_status dalloc(void **p, size_t bytes);
@@ -89,7 +91,8 @@ struct Engine {
   wf_status release_slot(int b);
   // Write slot b's double-float state as double a_lm into s + b nalm (stream-ordered).
   wf_status export_slot(int b);
-  static size_t bytes_needed(int nside, int lmax, int nslots);
+  // device bytes of an engine whose synthesis table is in `mode` (0 and 1 are sized as 1)
+  static size_t bytes_needed(int nside, int lmax, int nslots, int mode = 1);
 };
 
 }  // namespace wfk

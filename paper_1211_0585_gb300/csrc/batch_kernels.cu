@@ -31,6 +31,9 @@ __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 f2conj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.x, v.z); }  // hi parts of a df complex
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
+}
 
 }  // namespace
 
@@ -89,6 +92,19 @@ __global__ void __launch_bounds__(kBringThreads, 3) bring_kernel(const BatchArgs
   int Lmax = -1;
 #pragma unroll
   for (int g = 0; g < G; ++g) Lmax = max(Lmax, Lg[g]);
+  // Every global line this CTA reads goes to L2 first, all requests at once:
+  // the Fourier coefficients of the G slots (one run of G float4 per m) and
+  // the slots' (d, w) on the ring. The fold's and the pixel pass's loads then
+  // wait on L2, not on HBM, one after another.
+  for (int m = threadIdx.x; m <= Lmax; m += blockDim.x) prefetch_l2(A.FS + ((size_t)m * A.RP + k) * B + b0);
+  {
+    constexpr int kLine = 128 / sizeof(float2);   // pixels per line
+    const int nl = (n + kLine - 1) / kLine + 1;     // the ring's run may straddle one more line
+    for (int e = threadIdx.x; e < G * nl; e += blockDim.x) {
+      const int g = e / nl, li = e % nl;
+      if (on[g]) prefetch_l2(A.dw32 + (size_t)(b0 + g) * A.npix + rg.off + min(li * kLine, n - 1));
+    }
+  }
 
   // fold F_m onto residues q for the G slots (m-aliasing), packed in pairs;
   // on rings shorter than the block each residue's alias series is split over
@@ -120,7 +136,7 @@ __global__ void __launch_bounds__(kBringThreads, 3) bring_kernel(const BatchArgs
     }
   };
   auto store_residue = [&](int q, const float2 (&acc)[G]) {
-    const float2 h = hi2(hs[q]), cq = rg.blue ? hi2(ch[q]) : make_float2(0.f, 0.f);
+    const float2 h = rg.shifted ? hi2(hs[q]) : make_float2(0.f, 0.f), cq = rg.blue ? hi2(ch[q]) : make_float2(0.f, 0.f);
 #pragma unroll
     for (int pp = 0; pp < P; ++pp) {
       float2 va = acc[2 * pp], vb = acc[2 * pp + 1];
@@ -264,9 +280,7 @@ __global__ void __launch_bounds__(kBringThreads, 3) bring_kernel(const BatchArgs
           V = f2mul(V, hq);
           if (j & 1) { V.x = -V.x; V.y = -V.y; }
         }
-        float *dst = reinterpret_cast<float *>(dst4 + g) + 2 * slot;
-        dst[0] = om * V.x;
-        dst[1] = om * V.y;
+        reinterpret_cast<float2 *>(dst4 + g)[slot] = make_float2(om * V.x, om * V.y);
       }
     }
   }
@@ -317,7 +331,7 @@ __global__ void bstate_kernel(const BatchArgs A, int *bstate) {
 }
 
 // reset slot b: zero its state, its Fourier coefficients and its columns of
-// the synthesis operand (2 b, 2 b + 1 of every 32-wide chunk)
+// the synthesis operand (2 b, 2 b + 1 of every part of every 32-wide chunk)
 __global__ void bzero_slot_kernel(const BatchArgs A, const TcArgs T, long long nchunks, int b) {
   const long long nF = (long long)(A.lmax + 1) * A.RP;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -325,8 +339,8 @@ __global__ void bzero_slot_kernel(const BatchArgs A, const TcArgs T, long long n
     A.FS[i * A.B + b] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nalm; i += stride)
     A.sdf[(size_t)b * A.nalm + i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nchunks * 64; i += stride) {
-    const long long q = i >> 6, e = i & 63;   // chunk, (column 2 b or 2 b + 1, i within the chunk)
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nchunks * 3 * 64; i += stride) {
+    const long long q = i >> 6, e = i & 63;   // (chunk, part), (column 2 b or 2 b + 1, i within the chunk)
     T.SPT[(q * T.Nc + 2 * b + (e >> 5)) * 32 + (e & 31)] = 0.f;
   }
 }
@@ -392,6 +406,7 @@ static size_t bring_smem(int logM, int G) {
   const size_t part = ((size_t)1 << logM) <= 2 * kBringThreads ? (size_t)kBringThreads * G * sizeof(float2) : 0;
   return (size_t)(G / 2) * bring_smem_per_pair(logM) + part;
 }
+
 
 // default slots per ring-stage CTA of a class (before autotuning): 8, 4 or 2
 // (pairs share one FFT), within a third of an SM's shared memory so that three

@@ -18,14 +18,23 @@
 //         multiple of 32): the analysis A operand, one TMA box = 128 rows x 32 k;
 //   lamT  rows (m, p, chunk of 32 i, k), 32 values of i contiguous: the synthesis
 //         A operand, one TMA box = 128 ring pairs x 32 i.
-// Per-iteration operands (written by the engine's own kernels):
-//   XT    rows (m, p, chunk of 32 k, c), 32 values of k contiguous (from FT);
-//   SPT   rows (m, p, chunk of 32 i, c), 32 values of i contiguous (written by the
-//         analysis epilogue for the next synthesis).
+// With split tables (T.pre) each table holds th in its first half of rows and
+// tl in its second, so the GEMMs load both parts; otherwise the 22-bit values
+// are loaded and split in shared memory by four splitting warps.
+// Per-iteration operands (written by the engine's own kernels), each value
+// already split into its three tf32 parts (part-major within a chunk):
+//   XT    rows (m, p, chunk of 32 k, part, c), 32 values of k contiguous (from FT);
+//   SPT   rows (m, p, chunk of 32 i, part, c), 32 values of i contiguous (written
+//         by the analysis epilogue for the next synthesis).
+// A data chunk is split once where it is produced, not once per GEMM tile that
+// reads it (an analysis chunk is read by every tile of i of its (m, p), a
+// synthesis chunk by every tile of ring pairs of its m).
 //
-// Each GEMM CTA is warp-specialised: warp 0 issues the TMA loads of a 3-stage
-// pipeline, warp 1 owns the tensor memory and issues the MMAs, warps 2-5 split
-// each landed tile into its tf32 parts and then run the epilogue.
+// Each GEMM CTA is warp-specialised: warp 0 issues the table's TMA loads into a
+// 4-stage ring, warp 2 the data operand's into a 2-stage ring (its chunks come
+// mostly from L2), warp 1 owns the tensor memory and issues the MMAs, warps 3-6
+// split the table tiles (when the table is not split already) and, in the
+// synthesis GEMM, run the epilogue.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -41,17 +50,12 @@ namespace wfk {
 
 namespace {
 
-// Products per k-step: 5 (FP32-level: the data split exactly into three tf32
-// parts) or 3 (data in two parts, ~2^-22 per product).
-constexpr int kProducts = 5;
-constexpr int kDerTiles = kProducts == 5 ? 3 : 2;   // table lo, data (mid,) lo
-constexpr int kDerSets = 2;                          // double-buffered split parts
 constexpr int kTileRows = 128;                       // M of every MMA
-constexpr int kTileBytes = kTileRows * 128;          // 128 rows x 32 fp32
-constexpr int kSmemTiles = 12;                       // 192 KB of operand tiles per CTA
-constexpr int kStages = (kSmemTiles - kDerSets * kDerTiles) / 2;   // raw TMA stages (table, data)
-constexpr int kSynThreads = 320;                     // synthesis: TMA, MMA, 8 splitting warps (2-5: epilogue)
-constexpr int kSynSplitWarps = 8;
+constexpr int kTileBytes = kTileRows * 128;          // 128 rows x 32 fp32 (a data tile: at most 128 columns)
+constexpr int kSmemTiles = 14;                       // 224 KB of operand tiles per CTA
+constexpr int kDAhead = 5;                           // data chunks brought into L2 this far ahead of their load
+constexpr int kSplitWarps = 4;                       // warps 3-6
+constexpr int kSynThreads = 224;                     // synthesis: table TMA, MMA, data TMA, 4 split / epilogue warps
 constexpr uint32_t kWaitLimit = 1u << 22;            // polls of one bounded mbarrier wait
 
 __device__ __forceinline__ size_t aidx(int lmax, int l, int m) { return (size_t)m * (2 * lmax + 1 - m) / 2 + l; }
@@ -59,17 +63,28 @@ __device__ __forceinline__ size_t aidx(int lmax, int l, int m) { return (size_t)
 // number of l in [m, L] with l - m = p (mod 2)
 __host__ __device__ __forceinline__ int n_par(int m, int p, int L) { return L >= m + p ? (L - m - p) / 2 + 1 : 0; }
 
-// Shared memory: kStages raw stages of (table, data) tiles that TMA fills, the
-// tf32 split writing the leading parts in place, and kDerSets sets of the
-// remaining parts (table lo, data mid, data lo). Every tile 1024-byte aligned.
-struct Smem {
-  __device__ static uint8_t *raw(uint8_t *base, int s, int which) {   // which: 0 table, 1 data
-    return base + ((size_t)s * 2 + which) * kTileBytes;
+// Shared memory rings of one GEMM CTA, every tile 1024-byte aligned:
+//   table  TS stages that TMA fills: (th, tl) with split tables, else th alone
+//          (the 22-bit values, split in place by the splitting warps);
+//   tl     (tables not split) LS slots the splitting warps write tl into;
+//   data   DS stages of the operand's (h, m, l) parts.
+// Loads wait about three MMA chunks' time to land, so each ring holds three
+// stages where shared memory allows.
+template <bool PRE>
+struct Ring {
+  static constexpr int TS = PRE ? 2 : 3;
+  static constexpr int LS = PRE ? 0 : 2;
+  static constexpr int DS = 3;
+  static_assert(TS * (PRE ? 2 : 1) + LS + 3 * DS <= kSmemTiles, "rings exceed the operand tiles");
+  __device__ static uint8_t *th(uint8_t *base, int s) { return base + (size_t)s * (PRE ? 2 : 1) * kTileBytes; }
+  __device__ static uint8_t *tl(uint8_t *base, int s, int kc) {
+    return PRE ? base + ((size_t)2 * s + 1) * kTileBytes : base + ((size_t)TS + kc % (LS ? LS : 1)) * kTileBytes;
   }
-  __device__ static uint8_t *der(uint8_t *base, int d, int which) {   // which: 0 table lo, 1 data lo, 2 data mid
-    return base + ((size_t)kStages * 2 + (size_t)d * kDerTiles + which) * kTileBytes;
+  __device__ static uint8_t *dat(uint8_t *base, int s, int part) {
+    return base + ((size_t)TS * (PRE ? 2 : 1) + LS + (size_t)s * 3 + part) * kTileBytes;
   }
 };
+constexpr int kRingMax = 3;   // barrier array sizes
 
 // v rounded to 11 significant bits (a tf32 number; ties away from zero) by
 // integer arithmetic on its bits; v - hi is then exact. Rounding to nearest
@@ -79,19 +94,29 @@ __device__ __forceinline__ float tf32_rn(float v) {
 }
 
 // table tile (22-bit values): th = v rounded to 11 bits in place, tl = v - th
-// (exact, and a tf32 number)
-__device__ __forceinline__ void split_table(uint8_t *hi, uint8_t *lo, int nbytes, int t, int nt) {
+// (exact, and a tf32 number). Each thread loads kSplitU float4 before it
+// splits and stores any of them, so that their shared-memory loads overlap.
+constexpr int kSplitU = 4;
+__device__ __forceinline__ void split_table(uint8_t *hi, uint8_t *lo, int t, int nt) {
   float4 *h4 = reinterpret_cast<float4 *>(hi);
   float4 *l4 = reinterpret_cast<float4 *>(lo);
-  for (int e = t; e < nbytes / 16; e += nt) {
-    const float4 v = h4[e];
-    float4 h, l;
-    h.x = tf32_rn(v.x); l.x = v.x - h.x;
-    h.y = tf32_rn(v.y); l.y = v.y - h.y;
-    h.z = tf32_rn(v.z); l.z = v.z - h.z;
-    h.w = tf32_rn(v.w); l.w = v.w - h.w;
-    h4[e] = h;
-    l4[e] = l;
+  constexpr int n = kTileBytes / 16;
+  for (int e0 = t; e0 < n; e0 += kSplitU * nt) {
+    float4 v[kSplitU];
+#pragma unroll
+    for (int u = 0; u < kSplitU; ++u)
+      if (e0 + u * nt < n) v[u] = h4[e0 + u * nt];
+#pragma unroll
+    for (int u = 0; u < kSplitU; ++u) {
+      if (e0 + u * nt >= n) break;
+      float4 h, l;
+      h.x = tf32_rn(v[u].x); l.x = v[u].x - h.x;
+      h.y = tf32_rn(v[u].y); l.y = v[u].y - h.y;
+      h.z = tf32_rn(v[u].z); l.z = v[u].z - h.z;
+      h.w = tf32_rn(v[u].w); l.w = v[u].w - h.w;
+      h4[e0 + u * nt] = h;
+      l4[e0 + u * nt] = l;
+    }
   }
 }
 
@@ -103,56 +128,41 @@ __device__ __forceinline__ void split3(float v, float &h, float &m, float &l) {
   l = r - m;               // exact: the last bits
 }
 
-// data tile (FP32): ah in place, then am, al (ah + am + al = v exactly) or,
-// with three products, al = v - ah rounded to 11 bits
-__device__ __forceinline__ void split_data(uint8_t *hi, uint8_t *lo, uint8_t *mid, int nbytes, int t, int nt) {
-  float4 *h4 = reinterpret_cast<float4 *>(hi);
-  float4 *m4 = reinterpret_cast<float4 *>(mid);
-  float4 *l4 = reinterpret_cast<float4 *>(lo);
-  for (int e = t; e < nbytes / 16; e += nt) {
-    const float4 v = h4[e];
-    float4 h, m, l;
-    if (kProducts == 5) {
-      split3(v.x, h.x, m.x, l.x);
-      split3(v.y, h.y, m.y, l.y);
-      split3(v.z, h.z, m.z, l.z);
-      split3(v.w, h.w, m.w, l.w);
-      m4[e] = m;
-    } else {
-      h.x = tf32_rn(v.x); l.x = tf32_rn(v.x - h.x);
-      h.y = tf32_rn(v.y); l.y = tf32_rn(v.y - h.y);
-      h.z = tf32_rn(v.z); l.z = tf32_rn(v.z - h.z);
-      h.w = tf32_rn(v.w); l.w = tf32_rn(v.w - h.w);
-    }
-    h4[e] = h;
-    l4[e] = l;
-  }
+// h + l += v with the rounding error of the leading sum kept (two-sum)
+__device__ __forceinline__ void two_sum_acc(float &h, float &l, float v) {
+  const float s = h + v, bv = s - h;
+  l += (h - (s - bv)) + (v - bv);
+  h = s;
 }
 
-// 4 k-steps of 8 over one 32-wide chunk. The leading product th ah
-// accumulates alone in `dmain`; the correction products (2^-11 and less of
-// it) accumulate in `dcorr`, so the rounding of the tensor-core accumulation
-// stays relative to each sum's own size. REV runs the k-steps from the end of
-// the chunk to its start.
+// (h, l) += (h2, l2), renormalised; the result does not depend on the order of
+// the two operands, so a butterfly leaves the same sum on every lane
+__device__ __forceinline__ void df_pair_add(float &h, float &l, float h2, float l2) {
+  const float s = h + h2, bv = s - h;
+  const float e = (h - (s - bv)) + (h2 - bv) + (l + l2);
+  h = s + e;
+  l = e - (h - s);
+}
+
+// 4 k-steps of 8 over one 32-wide chunk: table parts th, tl; data parts h, m,
+// l. The leading product th h accumulates alone in `dmain`; the correction
+// products (2^-11 and less of it) accumulate in `dcorr`, so the rounding of
+// the tensor-core accumulation stays relative to each sum's own size. REV runs
+// the k-steps from the end of the chunk to its start.
 template <bool REV = false>
-__device__ __forceinline__ void mma_chunk(uint32_t dmain, uint32_t dcorr, uint8_t *raw, uint8_t *der, uint32_t idesc,
-                                          bool acc_main, bool acc_corr) {
+__device__ __forceinline__ void mma_chunk(uint32_t dmain, uint32_t dcorr, uint8_t *th, uint8_t *tl, uint8_t *dh,
+                                          uint8_t *dm, uint8_t *dl, uint32_t idesc, bool acc_main, bool acc_corr) {
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     const int ks = REV ? 3 - kk : kk;
     const uint64_t off = (uint64_t)((ks * 32) >> 4);   // 32 bytes along K inside the swizzle atom
-    const uint64_t th = tc::sw128_desc(raw) + off;
-    const uint64_t ah = tc::sw128_desc(raw + kTileBytes) + off;
-    const uint64_t tl = tc::sw128_desc(der) + off;
-    const uint64_t al = tc::sw128_desc(der + kTileBytes) + off;
-    tc::mma_tf32(dmain, th, ah, idesc, acc_main || kk > 0);
-    tc::mma_tf32(dcorr, th, al, idesc, acc_corr || kk > 0);
-    tc::mma_tf32(dcorr, tl, ah, idesc, true);
-    if (kProducts == 5) {
-      const uint64_t am = tc::sw128_desc(der + 2 * kTileBytes) + off;
-      tc::mma_tf32(dcorr, th, am, idesc, true);
-      tc::mma_tf32(dcorr, tl, am, idesc, true);
-    }
+    const uint64_t a_h = tc::sw128_desc(th) + off, a_l = tc::sw128_desc(tl) + off;
+    const uint64_t b_h = tc::sw128_desc(dh) + off, b_m = tc::sw128_desc(dm) + off, b_l = tc::sw128_desc(dl) + off;
+    tc::mma_tf32(dmain, a_h, b_h, idesc, acc_main || kk > 0);
+    tc::mma_tf32(dcorr, a_h, b_l, idesc, acc_corr || kk > 0);
+    tc::mma_tf32(dcorr, a_l, b_h, idesc, true);
+    tc::mma_tf32(dcorr, a_h, b_m, idesc, true);
+    tc::mma_tf32(dcorr, a_l, b_m, idesc, true);
   }
 }
 
@@ -163,9 +173,12 @@ __device__ __forceinline__ void mma_chunk(uint32_t dmain, uint32_t dcorr, uint8_
 // writes lambda_lm(x_k) (rounded to 22 bits, 0 below l_start) into both table
 // layouts (only the analysis layout when lamT is nullptr: the synthesis rows are
 // then rebuilt per band, lamt_band_kernel); rows of the transposed layout are
-// written 32 values at a time from registers.
+// written 32 values at a time from registers. With `split`, each layout holds
+// th = tf32_rn(v) in its first half of rows and tl = v - th in its second (the
+// split the GEMMs otherwise make in shared memory, value for value).
 __global__ void lam_tc_tables_kernel(const double *xk, const LegDfArgs D, int lmax, int RP, int RPp,
-                                     const int *offTc, float *lamA, float *lamT) {
+                                     const int *offTc, float *lamA, float *lamT, int split, size_t loA,
+                                     size_t loT) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long long)(lmax + 1) * RPp) return;
   const int m = (int)(id / RPp), k = (int)(id % RPp);
@@ -173,12 +186,15 @@ __global__ void lam_tc_tables_kernel(const double *xk, const LegDfArgs D, int lm
   const int n0 = n_par(m, 0, lmax);
   float buf[2][32];
   if (k >= RP) {   // padding ring pairs: zeros
-    for (int p = 0; p < 2; ++p) {
-      const int np = n_par(m, p, lmax);
-      for (int i = 0; i < np; ++i) lamA[(base + (p ? n0 + i : i)) * (size_t)RPp + k] = 0.f;
-      for (int ic = 0; lamT && ic < (np + 31) / 32; ++ic) {
-        float4 *dst = reinterpret_cast<float4 *>(lamT + ((size_t)(offTc[2 * m + p] + ic) * RPp + k) * 32);
-        for (int j = 0; j < 8; ++j) dst[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int h = 0; h <= split; ++h) {
+      float *tA = lamA + (h ? loA : 0), *tT = lamT ? lamT + (h ? loT : 0) : nullptr;
+      for (int p = 0; p < 2; ++p) {
+        const int np = n_par(m, p, lmax);
+        for (int i = 0; i < np; ++i) tA[(base + (p ? n0 + i : i)) * (size_t)RPp + k] = 0.f;
+        for (int ic = 0; tT && ic < (np + 31) / 32; ++ic) {
+          float4 *dst = reinterpret_cast<float4 *>(tT + ((size_t)(offTc[2 * m + p] + ic) * RPp + k) * 32);
+          for (int j = 0; j < 8; ++j) dst[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
     }
     return;
@@ -206,14 +222,34 @@ __global__ void lam_tc_tables_kernel(const double *xk, const LegDfArgs D, int lm
       v = h + tc::to_tf32((float)(lam - (double)h));
     }
     const int p = (l - m) & 1, i = (l - m) >> 1;
-    lamA[(base + (p ? n0 + i : i)) * (size_t)RPp + k] = v;
+    const size_t ra = (base + (p ? n0 + i : i)) * (size_t)RPp + k;
+    if (split) {
+      const float th = tf32_rn(v);
+      lamA[ra] = th;
+      lamA[loA + ra] = v - th;
+    } else {
+      lamA[ra] = v;
+    }
     buf[p][i & 31] = v;
     const int np = n_par(m, p, lmax);
     if (lamT && ((i & 31) == 31 || i == np - 1)) {   // a chunk of 32 values of i is complete: write its row
       for (int j = (i & 31) + 1; j < 32; ++j) buf[p][j] = 0.f;
-      float4 *dst = reinterpret_cast<float4 *>(lamT + ((size_t)(offTc[2 * m + p] + (i >> 5)) * RPp + k) * 32);
+      const size_t rt = ((size_t)(offTc[2 * m + p] + (i >> 5)) * RPp + k) * 32;
+      float4 *dst = reinterpret_cast<float4 *>(lamT + rt);
+      if (split) {
+        float4 *dlo = reinterpret_cast<float4 *>(lamT + loT + rt);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) dst[j] = make_float4(buf[p][4 * j], buf[p][4 * j + 1], buf[p][4 * j + 2], buf[p][4 * j + 3]);
+        for (int j = 0; j < 8; ++j) {
+          const float4 v4 = make_float4(buf[p][4 * j], buf[p][4 * j + 1], buf[p][4 * j + 2], buf[p][4 * j + 3]);
+          const float4 h4 = make_float4(tf32_rn(v4.x), tf32_rn(v4.y), tf32_rn(v4.z), tf32_rn(v4.w));
+          dst[j] = h4;
+          dlo[j] = make_float4(v4.x - h4.x, v4.y - h4.y, v4.z - h4.z, v4.w - h4.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          dst[j] = make_float4(buf[p][4 * j], buf[p][4 * j + 1], buf[p][4 * j + 2], buf[p][4 * j + 3]);
+      }
     }
   }
 }
@@ -240,7 +276,8 @@ __global__ void __launch_bounds__(256) lamt_band_kernel(const TcArgs T, int q0, 
 // ---------------------------------------------------------------- FT -> XT
 // One CTA per (m, chunk of 32 ring pairs): the Fourier coefficients of every
 // slot, (N re, N im, S re, S im), become the analysis B operand of both
-// parities, X_0 = N + S and X_1 = N - S, with ring pairs contiguous.
+// parities, X_0 = N + S and X_1 = N - S, with ring pairs contiguous, each
+// value written as its three tf32 parts.
 __global__ void __launch_bounds__(256) xt_kernel(const BatchArgs A, const TcArgs T) {
   __shared__ float4 sF[32][kBatchMax + 1];
   const int m = blockIdx.y, kc = blockIdx.x;
@@ -252,6 +289,7 @@ __global__ void __launch_bounds__(256) xt_kernel(const BatchArgs A, const TcArgs
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t part = (size_t)T.Nc * 32;
   for (int row = warp; row < 2 * T.Nc; row += blockDim.x / 32) {
     const int p = row / T.Nc, c = row % T.Nc, b = c >> 1;
     float v = 0.f;
@@ -260,7 +298,12 @@ __global__ void __launch_bounds__(256) xt_kernel(const BatchArgs A, const TcArgs
       const float n = (c & 1) ? f.y : f.x, s = (c & 1) ? f.w : f.z;
       v = p ? n - s : n + s;
     }
-    T.XT[((((size_t)m * 2 + p) * T.nkc + kc) * T.Nc + c) * 32 + lane] = v;
+    float h, mid, l;
+    split3(v, h, mid, l);
+    float *dst = T.XT + ((((size_t)m * 2 + p) * T.nkc + kc) * 3 * T.Nc + c) * 32 + lane;
+    dst[0] = h;
+    dst[part] = mid;
+    dst[2 * part] = l;
   }
 }
 
@@ -274,22 +317,26 @@ __global__ void __launch_bounds__(256) xt_kernel(const BatchArgs A, const TcArgs
 // finished chunk into a double-float accumulator: hi in tensor memory, lo in
 // the folding threads' registers, as the FP32 path folded its chunk sums. The
 // correction products accumulate over all chunks in a third block. Warps: 0
-// TMA, 1 MMA (and tensor memory), 2-5 tf32 split, 6-13 folding and the
-// epilogue (warp w: TMEM lanes 32 (w % 4) .., columns 64 ((w - 6) / 4) ..).
-// Tiles wholly above the live band limit hold zero state (band limits only
-// grow within a solve and new slots start from zero): they only report zero
-// partials.
-constexpr int kAnaThreads = 448;
+// table TMA, 1 MMA (and tensor memory), 2 data TMA, 3-6 table split (when the
+// table is not split already), 7-14 folding and the epilogue (warp w: TMEM
+// lanes 32 (w % 4) .., columns 64 ((w - 7) / 4) ..). Tiles wholly above the
+// live band limit hold zero state (band limits only grow within a solve and
+// new slots start from zero): they only report zero partials.
+constexpr int kAnaThreads = 512;
+constexpr int kFoldWarp0 = 8;
 constexpr int kFoldThreads = 256;
 constexpr int kFoldChunks = 1;   // chunks of 32 ring pairs per folded segment
 constexpr uint32_t kColSeg0 = 0, kColSeg1 = 128, kColCorr = 256, kColHi = 384;
 
+template <bool PRE>
 __global__ void __launch_bounds__(kAnaThreads, 1)
     bana_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX,
                    const BatchArgs A, const TcArgs T) {
   extern __shared__ __align__(1024) uint8_t tsm_raw[];
   uint8_t *tsm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], dfree[kDerSets], segf[2], segfree[2];
+  using R = Ring<PRE>;
+  __shared__ uint64_t tfull[kRingMax], tready[kRingMax], tempty[kRingMax], dfull[kRingMax], dempty[kRingMax];
+  __shared__ uint64_t lfree[2], segf[2], segfree[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ unsigned long long live_slots;   // bit b: slot b iterates
@@ -306,22 +353,27 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
   }
   const int nkc = T.nkc;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&conv[s], 4);   // one arrival per splitting warp
-      tc::mbar_init(&empty[s], 1);
+    for (int s = 0; s < R::TS; ++s) {
+      tc::mbar_init(&tfull[s], 1);
+      tc::mbar_init(&tready[s], kSplitWarps);   // one arrival per splitting warp
+      tc::mbar_init(&tempty[s], 1);
     }
-    for (int d = 0; d < kDerSets; ++d) tc::mbar_init(&dfree[d], 1);
+    for (int s = 0; s < R::DS; ++s) {
+      tc::mbar_init(&dfull[s], 1);
+      tc::mbar_init(&dempty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) tc::mbar_init(&lfree[s], 1);
     for (int j = 0; j < 2; ++j) {
       tc::mbar_init(&segf[j], 1);
       tc::mbar_init(&segfree[j], kFoldThreads / 32);   // one arrival per folding warp
     }
     tc::fence_mbar_init();
     abort_flag = 0;
-    unsigned long long mask = 0;
-    for (int b = 0; b < B; ++b)
-      if (A.active[b] && !A.ctl[b].done) mask |= 1ull << b;
-    live_slots = mask;
+  }
+  if (warp < 2) {   // live slots: one slot per thread of warps 0-1, gathered by ballots
+    const int b = threadIdx.x;
+    const unsigned bits = __ballot_sync(0xffffffffu, b < B && A.active[b] && !A.ctl[b].done);
+    if (lane == 0) reinterpret_cast<unsigned *>(&live_slots)[warp] = bits;
   }
   if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
   tc::tc_fence_before();
@@ -330,66 +382,107 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = tc::tf32_idesc(kTileRows, Nc);
   const uint32_t bbytes = (uint32_t)Nc * 128;
-  int issued = 0;   // TMA stages issued by the producer (for the drain on abort)
+  int issued = 0;   // TMA stages issued by this thread's ring (for the drain on abort)
 
-  if (warp == 0 && lane == 0) {
-    tc::prefetch_tensormap(&mapA);
-    tc::prefetch_tensormap(&mapX);
-    for (int kc = 0; kc < nkc; ++kc) {
-      const int s = kc % kStages;
-      if (kc >= kStages && !tc::mbar_wait(&empty[s], ((kc / kStages) - 1) & 1, kWaitLimit)) {
-        atomicExch(&abort_flag, 1);
-        break;
+  // Each role branch is taken by a whole warp (lane 0 does the work) and ends in
+  // __syncwarp, so that every warp reaches the block barriers below converged.
+  if (warp == 0) {   // table ring
+    if (lane == 0) {
+      tc::prefetch_tensormap(&mapA);
+      for (int kc = 0; kc < nkc; ++kc) {
+        const int s = kc % R::TS;
+        if (kc >= R::TS && !tc::mbar_wait(&tempty[s], ((kc / R::TS) - 1) & 1, kWaitLimit)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int *)&abort_flag) break;
+        tc::mbar_arrive_expect_tx(&tfull[s], PRE ? 2 * kTileBytes : kTileBytes);
+        tc::tma_load_2d(R::th(tsm, s), &mapA, 32 * kc, rowA + i0, &tfull[s]);
+        if (PRE) tc::tma_load_2d(R::tl(tsm, s, kc), &mapA, 32 * kc, T.loA + rowA + i0, &tfull[s]);
+        issued = kc + 1;
       }
-      if (*(volatile int *)&abort_flag) break;
-      tc::mbar_arrive_expect_tx(&full[s], kTileBytes + bbytes);
-      tc::tma_load_2d(Smem::raw(tsm, s, 0), &mapA, 32 * kc, rowA + i0, &full[s]);
-      tc::tma_load_2d(Smem::raw(tsm, s, 1), &mapX, 0, (int)((((size_t)m * 2 + p) * T.nkc + kc) * Nc), &full[s]);
-      issued = kc + 1;
     }
-  } else if (warp == 1 && lane == 0) {
-    for (int kc = 0; kc < nkc; ++kc) {
-      const int s = kc % kStages, j = kc / kFoldChunks;
-      const uint32_t seg = tmem + ((j & 1) ? kColSeg1 : kColSeg0);
-      // a segment block is reused once the folding warps have read it
-      if (kc % kFoldChunks == 0 && j >= 2 &&
-          (*(volatile int *)&abort_flag || !tc::mbar_wait(&segfree[j & 1], ((j - 2) >> 1) & 1, kWaitLimit))) {
-        atomicExch(&abort_flag, 1);
-        break;
+    __syncwarp();
+  } else if (warp == 2) {   // data ring: the three parts of X_p's chunk, brought into L2 kDAhead chunks early
+    if (lane == 0) {
+      tc::prefetch_tensormap(&mapX);
+      const int y0 = (int)(((size_t)m * 2 + p) * T.nkc * 3 * Nc);
+      for (int kc = R::DS; kc < kDAhead && kc < nkc; ++kc)
+        for (int part = 0; part < 3; ++part) tc::tma_prefetch_2d(&mapX, 0, y0 + (kc * 3 + part) * Nc);
+      for (int kc = 0; kc < nkc; ++kc) {
+        const int s = kc % R::DS;
+        if (kc >= R::DS && !tc::mbar_wait(&dempty[s], ((kc / R::DS) - 1) & 1, kWaitLimit)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int *)&abort_flag) break;
+        tc::mbar_arrive_expect_tx(&dfull[s], 3 * bbytes);
+        const int y = y0 + kc * 3 * Nc;
+#pragma unroll
+        for (int part = 0; part < 3; ++part)
+          tc::tma_load_2d(R::dat(tsm, s, part), &mapX, 0, y + part * Nc, &dfull[s]);
+        if (kc + kDAhead < nkc)
+          for (int part = 0; part < 3; ++part) tc::tma_prefetch_2d(&mapX, 0, y + (kDAhead * 3 + part) * Nc);
+        issued = kc + 1;
       }
-      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&conv[s], (kc / kStages) & 1, kWaitLimit)) {
-        atomicExch(&abort_flag, 1);
-        break;
-      }
-      tc::tc_fence_after();
-      mma_chunk(seg, tmem + kColCorr, Smem::raw(tsm, s, 0), Smem::der(tsm, kc % kDerSets, 0), idesc,
-                kc % kFoldChunks != 0, kc > 0);
-      tc::mma_commit(&empty[s]);
-      tc::mma_commit(&dfree[kc % kDerSets]);
-      if (kc % kFoldChunks == kFoldChunks - 1 || kc == nkc - 1) tc::mma_commit(&segf[j & 1]);
     }
-  } else if (warp >= 2 && warp < 6) {
-    const int t = threadIdx.x - 64;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int kc = 0; kc < nkc; ++kc) {
+        const int s = kc % R::TS, sd = kc % R::DS, j = kc / kFoldChunks;
+        const uint32_t seg = tmem + ((j & 1) ? kColSeg1 : kColSeg0);
+        // a segment block is reused once the folding warps have read it
+        if (kc % kFoldChunks == 0 && j >= 2 &&
+            (*(volatile int *)&abort_flag || !tc::mbar_wait(&segfree[j & 1], ((j - 2) >> 1) & 1, kWaitLimit))) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int *)&abort_flag ||
+            !tc::mbar_wait(PRE ? &tfull[s] : &tready[s], (kc / R::TS) & 1, kWaitLimit) ||
+            !tc::mbar_wait(&dfull[sd], (kc / R::DS) & 1, kWaitLimit)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        tc::tc_fence_after();
+        mma_chunk(seg, tmem + kColCorr, R::th(tsm, s), R::tl(tsm, s, kc), R::dat(tsm, sd, 0), R::dat(tsm, sd, 1),
+                  R::dat(tsm, sd, 2), idesc, kc % kFoldChunks != 0, kc > 0);
+        tc::mma_commit(&tempty[s]);
+        tc::mma_commit(&dempty[sd]);
+        if (!PRE) tc::mma_commit(&lfree[kc % 2]);
+        if (kc % kFoldChunks == kFoldChunks - 1 || kc == nkc - 1) tc::mma_commit(&segf[j & 1]);
+      }
+    }
+    __syncwarp();
+  } else if (!PRE && warp >= 3 && warp < 3 + kSplitWarps) {
+    const int t = threadIdx.x - 96;
     for (int kc = 0; kc < nkc; ++kc) {
-      const int s = kc % kStages, dset = kc % kDerSets;
-      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&full[s], (kc / kStages) & 1, kWaitLimit) ||
-          (kc >= kDerSets && !tc::mbar_wait_warp(&dfree[dset], ((kc / kDerSets) - 1) & 1, kWaitLimit))) {
+      const int s = kc % R::TS;
+      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&tfull[s], (kc / R::TS) & 1, kWaitLimit) ||
+          (kc >= 2 && !tc::mbar_wait_warp(&lfree[kc % 2], ((kc / 2) - 1) & 1, kWaitLimit))) {
         atomicExch(&abort_flag, 1);
         break;
       }
-      split_table(Smem::raw(tsm, s, 0), Smem::der(tsm, dset, 0), kTileBytes, t, 128);
-      split_data(Smem::raw(tsm, s, 1), Smem::der(tsm, dset, 1), Smem::der(tsm, dset, 2), (int)bbytes, t, 128);
+      split_table(R::th(tsm, s), R::tl(tsm, s, kc), t, 32 * kSplitWarps);
       tc::fence_proxy_async_smem();
-      tc::mbar_arrive_warp(&conv[s]);
+      tc::mbar_arrive_warp(&tready[s]);
     }
   }
   // folding warps: chunk sums into (hi in TMEM, lo in registers)
-  const int fq = warp & 3, fh = (warp - 6) >> 2;      // lane quadrant, column half
+  const int fq = warp & 3, fh = (warp - kFoldWarp0) >> 2;      // lane quadrant, column half
   const uint32_t flanes = (uint32_t)(32 * fq) << 16;
   float lo[64];
 #pragma unroll
   for (int e = 0; e < 64; ++e) lo[e] = 0.f;
-  if (warp >= 6) {
+  if (warp >= kFoldWarp0) {
+    {   // the epilogue's state rows into L2 while the GEMM runs
+      const int i = i0 + 32 * fq + lane;
+      if (i < n_par(m, p, lmax)) {
+        const unsigned long long mine = live_slots >> (32 * fh);
+        for (int jb = 0; jb < 32; ++jb)
+          if ((mine >> jb) & 1ull) tc::prefetch_l2(A.sdf + (size_t)(32 * fh + jb) * A.nalm + rowA + i);
+      }
+    }
     const int nseg = (nkc + kFoldChunks - 1) / kFoldChunks;
     for (int kc = 0; kc < nseg; ++kc) {   // segment index
       if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&segf[kc & 1], (kc >> 1) & 1, kWaitLimit)) {
@@ -444,13 +537,15 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
     tc::tc_fence_before();
   }
 
-  // ---- epilogue (warps 6-13)
+  // ---- epilogue (all 16 warps: warp w takes TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..)
   __syncthreads();   // every chunk is folded, the stage buffers are free, abort_flag is final
   tc::tc_fence_after();
   const bool ok_acc = abort_flag == 0;   // uniform over the CTA
   float *red = reinterpret_cast<float *>(tsm);    // [3][Bp][129] partials (row stride 129: no bank conflicts)
-  if (warp >= 6) {
-    const int r = 32 * fq + lane;
+  {
+    const int eq = warp & 3, ec = warp >> 2;
+    const uint32_t elanes = (uint32_t)(32 * eq) << 16;
+    const int r = 32 * eq + lane;
     const int i = i0 + r;
     const int np = n_par(m, p, lmax);
     const bool row_ok = i < np;
@@ -458,15 +553,15 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
     const size_t idx = (size_t)rowA + (row_ok ? i : 0);   // state row (the analysis table's row order)
     const float wgt = (m == 0) ? 1.f : 2.f;
 #pragma unroll
-    for (int bb = 0; bb < 4; ++bb) {
-      const int cb = 4 * fh + bb;
+    for (int bb = 0; bb < 2; ++bb) {
+      const int cb = 2 * ec + bb;
       if (16 * cb >= Nc) break;
       float th[16], tl[16];
       if (ok_acc) {   // t = hi + (lo + corrections)
         uint32_t hr[16], cr[16], lr[16];
-        tc::tmem_ld16_issue(tmem + flanes + kColHi + 16 * cb, hr);
-        tc::tmem_ld16_issue(tmem + flanes + kColCorr + 16 * cb, cr);
-        tc::tmem_ld16_issue(tmem + flanes + kColSeg0 + 16 * cb, lr);
+        tc::tmem_ld16_issue(tmem + elanes + kColHi + 16 * cb, hr);
+        tc::tmem_ld16_issue(tmem + elanes + kColCorr + 16 * cb, cr);
+        tc::tmem_ld16_issue(tmem + elanes + kColSeg0 + 16 * cb, lr);
         tc::tmem_ld_wait(hr);
         tc::tmem_ld_wait(cr);
         tc::tmem_ld_wait(lr);
@@ -493,7 +588,9 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
         iv[0] = c4[0];
         iv[1] = c4[1];
       }
-      float *spt = T.SPT + (((size_t)T.offTc[2 * m + p] + (i >> 5)) * Nc + 16 * cb) * 32 + (i & 31);
+      // the next synthesis operand, split into its tf32 parts (part-major within the chunk)
+      float *spt = T.SPT + (((size_t)T.offTc[2 * m + p] + (i >> 5)) * 3 * Nc + 16 * cb) * 32 + (i & 31);
+      const size_t spart = (size_t)Nc * 32;
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
         const int b = 8 * cb + jj;
@@ -512,8 +609,15 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
           inc = wgt * (dx * dx + dy * dy);
           nrm = wgt * (sn.x * sn.x + sn.z * sn.z);
           A.sdf[(size_t)b * A.nalm + idx] = sn;
-          spt[(2 * jj) * 32] = sn.x;
-          spt[(2 * jj + 1) * 32] = sn.z;
+          float h, mid, lw;
+          split3(sn.x, h, mid, lw);
+          spt[(2 * jj) * 32] = h;
+          spt[spart + (2 * jj) * 32] = mid;
+          spt[2 * spart + (2 * jj) * 32] = lw;
+          split3(sn.z, h, mid, lw);
+          spt[(2 * jj + 1) * 32] = h;
+          spt[spart + (2 * jj + 1) * 32] = mid;
+          spt[2 * spart + (2 * jj + 1) * 32] = lw;
         }
         red[(0 * B + b) * 129 + r] = c2;
         red[(1 * B + b) * 129 + r] = inc;
@@ -522,17 +626,29 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
     }
   }
   __syncthreads();
-  // fixed-order sums over the 128 rows, one (quantity, slot) per thread
-  for (int qb = threadIdx.x; qb < 3 * B; qb += blockDim.x) {
-    const int qq = qb / B, b = qb % B;
-    double sum = 0.0;
-    for (int rr = 0; rr < 128; ++rr) sum += (double)red[qb * 129 + rr];
-    A.m_part[((size_t)b * A.ntiles + blockIdx.x) * 3 + qq] = sum;
+  // sums over the 128 rows, one (quantity, slot) per warp: each lane adds its
+  // four rows, then a butterfly of double-float pairs (the same order on every
+  // lane and in every run: the sums are reproducible)
+  for (int qb = warp; qb < 3 * B; qb += kAnaThreads / 32) {
+    const float *rw = red + qb * 129;
+    float h = rw[lane], l = 0.f;
+#pragma unroll
+    for (int e = 1; e < 4; ++e) two_sum_acc(h, l, rw[lane + 32 * e]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+      df_pair_add(h, l, h2, l2);
+    }
+    if (lane == 0) A.m_part[((size_t)(qb % B) * A.ntiles + blockIdx.x) * 3 + qb / B] = (double)h + (double)l;
   }
   // drain: every TMA this CTA issued has landed before its shared memory is released
-  if (warp == 0 && lane == 0 && *(volatile int *)&abort_flag) {
-    for (int kc = std::max(0, issued - kStages); kc < issued; ++kc)
-      tc::mbar_wait(&full[kc % kStages], (kc / kStages) & 1, kWaitLimit);
+  if (warp == 0 || warp == 2) {
+    if (lane == 0 && *(volatile int *)&abort_flag) {
+      const int ns = warp == 0 ? R::TS : R::DS;
+      uint64_t *bar = warp == 0 ? tfull : dfull;
+      for (int kc = max(0, issued - ns); kc < issued; ++kc) tc::mbar_wait(&bar[kc % ns], (kc / ns) & 1, kWaitLimit);
+    }
+    __syncwarp();
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -546,13 +662,18 @@ __global__ void __launch_bounds__(kAnaThreads, 1)
 // ---------------------------------------------------------------- synthesis GEMM
 // One CTA per (m, 128 ring pairs): E and O accumulate in two tensor-memory
 // blocks over the chunks of 32 values of i of each parity up to the live band
-// limit; the epilogue writes FS = (E + O, E - O) for every slot.
+// limit; the epilogue writes FS = (E + O, E - O) for every slot. Warps: 0 table
+// TMA, 1 MMA, 2 data TMA, 3-6 table split (when the table is not split already)
+// and the epilogue.
+template <bool PRE>
 __global__ void __launch_bounds__(kSynThreads, 1)
     bsyn_tc_kernel(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapS,
                    const BatchArgs A, const TcArgs T) {
   extern __shared__ __align__(1024) uint8_t tsm_raw[];
   uint8_t *tsm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[kStages], conv[kStages], empty[kStages], dfree[kDerSets], accf;
+  using R = Ring<PRE>;
+  __shared__ uint64_t tfull[kRingMax], tready[kRingMax], tempty[kRingMax], dfull[kRingMax], dempty[kRingMax];
+  __shared__ uint64_t lfree[2], accf;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -564,12 +685,16 @@ __global__ void __launch_bounds__(kSynThreads, 1)
   const int nc0 = (n_par(m, 0, Lact) + 31) / 32, nc1 = (n_par(m, 1, Lact) + 31) / 32;
   const int nq = nc0 + nc1;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&conv[s], kSynSplitWarps);   // one arrival per splitting warp
-      tc::mbar_init(&empty[s], 1);
+    for (int s = 0; s < R::TS; ++s) {
+      tc::mbar_init(&tfull[s], 1);
+      tc::mbar_init(&tready[s], kSplitWarps);   // one arrival per splitting warp
+      tc::mbar_init(&tempty[s], 1);
     }
-    for (int d = 0; d < kDerSets; ++d) tc::mbar_init(&dfree[d], 1);
+    for (int s = 0; s < R::DS; ++s) {
+      tc::mbar_init(&dfull[s], 1);
+      tc::mbar_init(&dempty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) tc::mbar_init(&lfree[s], 1);
     tc::mbar_init(&accf, 1);
     tc::fence_mbar_init();
     abort_flag = 0;
@@ -582,66 +707,101 @@ __global__ void __launch_bounds__(kSynThreads, 1)
   const uint32_t idesc = tc::tf32_idesc(kTileRows, Nc);
   const uint32_t bbytes = (uint32_t)Nc * 128;
   int issued = 0;
+  // within a parity the chunks run from high l to low l: the large low-l
+  // terms enter the fp32 accumulator last
+  auto chunk_of = [&](int qi) {
+    const int p = qi < nc0 ? 0 : 1, ic = p ? nc0 + nc1 - 1 - qi : nc0 - 1 - qi;
+    return (long long)T.offTc[2 * m + p] + ic;
+  };
 
-  if (warp == 0 && lane == 0) {
-    if (nq > 0) {
-      tc::prefetch_tensormap(&mapT);
-      tc::prefetch_tensormap(&mapS);
+  // Each role branch is taken by a whole warp (lane 0 does the work) and ends in
+  // __syncwarp, so that every warp reaches the block barriers below converged.
+  if (warp == 0) {   // table ring
+    if (lane == 0) {
+      if (nq > 0) tc::prefetch_tensormap(&mapT);
+      for (int qi = 0; qi < nq; ++qi) {
+        const int s = qi % R::TS;
+        if (qi >= R::TS && !tc::mbar_wait(&tempty[s], ((qi / R::TS) - 1) & 1, kWaitLimit)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int *)&abort_flag) break;
+        const int y = (int)((chunk_of(qi) - T.qbase) * T.RPp + k0);
+        tc::mbar_arrive_expect_tx(&tfull[s], PRE ? 2 * kTileBytes : kTileBytes);
+        tc::tma_load_2d(R::th(tsm, s), &mapT, 0, y, &tfull[s]);
+        if (PRE) tc::tma_load_2d(R::tl(tsm, s, qi), &mapT, 0, T.loT + y, &tfull[s]);
+        issued = qi + 1;
+      }
     }
+    __syncwarp();
+  } else if (warp == 2) {   // data ring: the three parts of the state chunk, brought into L2 kDAhead chunks early
+    if (lane == 0) {
+      if (nq > 0) tc::prefetch_tensormap(&mapS);
+      for (int qi = R::DS; qi < kDAhead && qi < nq; ++qi)
+        for (int part = 0; part < 3; ++part) tc::tma_prefetch_2d(&mapS, 0, (int)((chunk_of(qi) * 3 + part) * Nc));
+      for (int qi = 0; qi < nq; ++qi) {
+        const int s = qi % R::DS;
+        if (qi >= R::DS && !tc::mbar_wait(&dempty[s], ((qi / R::DS) - 1) & 1, kWaitLimit)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int *)&abort_flag) break;
+        const int y = (int)(chunk_of(qi) * 3 * Nc);
+        tc::mbar_arrive_expect_tx(&dfull[s], 3 * bbytes);
+#pragma unroll
+        for (int part = 0; part < 3; ++part)
+          tc::tma_load_2d(R::dat(tsm, s, part), &mapS, 0, y + part * Nc, &dfull[s]);
+        if (qi + kDAhead < nq)
+          for (int part = 0; part < 3; ++part)
+            tc::tma_prefetch_2d(&mapS, 0, (int)((chunk_of(qi + kDAhead) * 3 + part) * Nc));
+        issued = qi + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int qi = 0; qi < nq; ++qi) {
+        const int s = qi % R::TS, sd = qi % R::DS;
+        if (*(volatile int *)&abort_flag ||
+            !tc::mbar_wait(PRE ? &tfull[s] : &tready[s], (qi / R::TS) & 1, kWaitLimit) ||
+            !tc::mbar_wait(&dfull[sd], (qi / R::DS) & 1, kWaitLimit)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        tc::tc_fence_after();
+        const int p = qi < nc0 ? 0 : 1, first = p ? qi == nc0 : qi == 0;
+        // leading products of parity p in columns 128 p, corrections in 256 + 128 p
+        mma_chunk<true>(tmem + (uint32_t)(128 * p), tmem + (uint32_t)(256 + 128 * p), R::th(tsm, s),
+                        R::tl(tsm, s, qi), R::dat(tsm, sd, 0), R::dat(tsm, sd, 1), R::dat(tsm, sd, 2), idesc, !first,
+                        !first);
+        tc::mma_commit(&tempty[s]);
+        tc::mma_commit(&dempty[sd]);
+        if (!PRE) tc::mma_commit(&lfree[qi % 2]);
+      }
+      if (nq > 0) tc::mma_commit(&accf);
+    }
+    __syncwarp();
+  } else if (!PRE && warp >= 3) {
+    const int t = threadIdx.x - 96;
     for (int qi = 0; qi < nq; ++qi) {
-      const int s = qi % kStages;
-      if (qi >= kStages && !tc::mbar_wait(&empty[s], ((qi / kStages) - 1) & 1, kWaitLimit)) {
+      const int s = qi % R::TS;
+      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&tfull[s], (qi / R::TS) & 1, kWaitLimit) ||
+          (qi >= 2 && !tc::mbar_wait_warp(&lfree[qi % 2], ((qi / 2) - 1) & 1, kWaitLimit))) {
         atomicExch(&abort_flag, 1);
         break;
       }
-      if (*(volatile int *)&abort_flag) break;
-      // within a parity the chunks run from high l to low l: the large low-l
-      // terms enter the fp32 accumulator last
-      const int p = qi < nc0 ? 0 : 1, ic = p ? nc0 + nc1 - 1 - qi : nc0 - 1 - qi;
-      const long long q = (long long)T.offTc[2 * m + p] + ic;
-      tc::mbar_arrive_expect_tx(&full[s], kTileBytes + bbytes);
-      tc::tma_load_2d(Smem::raw(tsm, s, 0), &mapT, 0, (int)((q - T.qbase) * T.RPp + k0), &full[s]);
-      tc::tma_load_2d(Smem::raw(tsm, s, 1), &mapS, 0, (int)(q * Nc), &full[s]);
-      issued = qi + 1;
-    }
-  } else if (warp == 1 && lane == 0) {
-    for (int qi = 0; qi < nq; ++qi) {
-      const int s = qi % kStages;
-      if (*(volatile int *)&abort_flag || !tc::mbar_wait(&conv[s], (qi / kStages) & 1, kWaitLimit)) {
-        atomicExch(&abort_flag, 1);
-        break;
-      }
-      tc::tc_fence_after();
-      const int p = qi < nc0 ? 0 : 1, first = p ? qi == nc0 : qi == 0;
-      // leading products of parity p in columns 128 p, corrections in 256 + 128 p
-      mma_chunk<true>(tmem + (uint32_t)(128 * p), tmem + (uint32_t)(256 + 128 * p), Smem::raw(tsm, s, 0),
-                      Smem::der(tsm, qi % kDerSets, 0), idesc, !first, !first);
-      tc::mma_commit(&empty[s]);
-      tc::mma_commit(&dfree[qi % kDerSets]);
-    }
-    if (nq > 0) tc::mma_commit(&accf);
-  } else if (warp >= 2) {
-    const int t = threadIdx.x - 64, nt = 32 * kSynSplitWarps;
-    for (int qi = 0; qi < nq; ++qi) {
-      const int s = qi % kStages, dset = qi % kDerSets;
-      if (tc::warp_flag(&abort_flag) || !tc::mbar_wait_warp(&full[s], (qi / kStages) & 1, kWaitLimit) ||
-          (qi >= kDerSets && !tc::mbar_wait_warp(&dfree[dset], ((qi / kDerSets) - 1) & 1, kWaitLimit))) {
-        atomicExch(&abort_flag, 1);
-        break;
-      }
-      split_table(Smem::raw(tsm, s, 0), Smem::der(tsm, dset, 0), kTileBytes, t, nt);
-      split_data(Smem::raw(tsm, s, 1), Smem::der(tsm, dset, 1), Smem::der(tsm, dset, 2), (int)bbytes, t, nt);
+      split_table(R::th(tsm, s), R::tl(tsm, s, qi), t, 32 * kSplitWarps);
       tc::fence_proxy_async_smem();
-      tc::mbar_arrive_warp(&conv[s]);
+      tc::mbar_arrive_warp(&tready[s]);
     }
   }
-  // ---- epilogue (warps 2-5): row k0 + r of E (columns 0 .. Nc) and O (Nc .. 2 Nc)
-  if (warp >= 2 && warp < 6 && nq > 0 && !tc::warp_flag(&abort_flag) && !tc::mbar_wait_warp(&accf, 0, kWaitLimit))
+  // ---- epilogue (warps 3-6): row k0 + r of E (columns 0 .. Nc) and O (Nc .. 2 Nc)
+  if (warp >= 3 && nq > 0 && !tc::warp_flag(&abort_flag) && !tc::mbar_wait_warp(&accf, 0, kWaitLimit))
     atomicExch(&abort_flag, 1);
   __syncthreads();   // abort_flag is final from here on
   tc::tc_fence_after();
   const bool have = nq > 0 && abort_flag == 0;   // uniform over the CTA
-  if (warp >= 2 && warp < 6) {
+  if (warp >= 3) {
     const int qd = warp & 3;
     const int k = k0 + 32 * qd + lane;
     const uint32_t lanes = (uint32_t)(32 * qd) << 16;
@@ -685,9 +845,13 @@ __global__ void __launch_bounds__(kSynThreads, 1)
       }
     }
   }
-  if (warp == 0 && lane == 0 && *(volatile int *)&abort_flag) {
-    for (int qi = std::max(0, issued - kStages); qi < issued; ++qi)
-      tc::mbar_wait(&full[qi % kStages], (qi / kStages) & 1, kWaitLimit);
+  if (warp == 0 || warp == 2) {
+    if (lane == 0 && *(volatile int *)&abort_flag) {
+      const int ns = warp == 0 ? R::TS : R::DS;
+      uint64_t *bar = warp == 0 ? tfull : dfull;
+      for (int qi = max(0, issued - ns); qi < issued; ++qi) tc::mbar_wait(&bar[qi % ns], (qi / ns) & 1, kWaitLimit);
+    }
+    __syncwarp();
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -730,20 +894,23 @@ bool make_tc_map(CUtensorMap *map, const float *base, unsigned long long inner, 
 }
 
 void launch_lam_tc_tables(const double *x, const LegDfArgs &D, int lmax, int RP, int RPp, const int *offTc,
-                          float *lamA, float *lamT, cudaStream_t s) {  // lamT nullptr: analysis table only
+                          float *lamA, float *lamT, bool split, size_t loA, size_t loT, cudaStream_t s) {
+  // lamT nullptr: analysis table only
   const long long n = (long long)(lmax + 1) * RPp;
-  lam_tc_tables_kernel<<<(int)((n + 127) / 128), 128, 0, s>>>(x, D, lmax, RP, RPp, offTc, lamA, lamT);
+  lam_tc_tables_kernel<<<(int)((n + 127) / 128), 128, 0, s>>>(x, D, lmax, RP, RPp, offTc, lamA, lamT, split ? 1 : 0,
+                                                               loA, loT);
 }
 
-void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which,
-                           const SynBand *bands, int nbands) {
-  raise_smem_cap(reinterpret_cast<const void *>(bana_tc_kernel));
-  raise_smem_cap(reinterpret_cast<const void *>(bsyn_tc_kernel));
+template <bool PRE>
+static void launch_gemms(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which,
+                         const SynBand *bands, int nbands) {
+  raise_smem_cap(reinterpret_cast<const void *>(bana_tc_kernel<PRE>));
+  raise_smem_cap(reinterpret_cast<const void *>(bsyn_tc_kernel<PRE>));
   if (which == 0) {
     xt_kernel<<<dim3(t.nkc, a.lmax + 1), 256, 0, s>>>(a, t);
-    bana_tc_kernel<<<t.natiles, kAnaThreads, gemm_smem(), s>>>(maps.A, maps.X, a, t);
+    bana_tc_kernel<PRE><<<t.natiles, kAnaThreads, gemm_smem(), s>>>(maps.A, maps.X, a, t);
   } else if (!t.lamTs) {
-    bsyn_tc_kernel<<<t.nstiles, kSynThreads, gemm_smem(), s>>>(maps.T, maps.S, a, t);
+    bsyn_tc_kernel<PRE><<<t.nstiles, kSynThreads, gemm_smem(), s>>>(maps.T, maps.S, a, t);
   } else {
     // band by band: rebuild the band's synthesis-ordered rows, then its GEMM tiles
     for (int i = 0; i < nbands; ++i) {
@@ -752,9 +919,15 @@ void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &ma
       tb.qbase = b.q0;
       tb.tile0 = b.tile0;
       lamt_band_kernel<<<dim3(b.q1 - b.q0, t.nkc), 256, 0, s>>>(tb, b.q0, a.bstate);
-      bsyn_tc_kernel<<<b.tile1 - b.tile0, kSynThreads, gemm_smem(), s>>>(maps.T, maps.S, a, tb);
+      bsyn_tc_kernel<PRE><<<b.tile1 - b.tile0, kSynThreads, gemm_smem(), s>>>(maps.T, maps.S, a, tb);
     }
   }
+}
+
+void launch_batch_gemms_tc(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, cudaStream_t s, int which,
+                           const SynBand *bands, int nbands) {
+  if (t.pre) launch_gemms<true>(a, t, maps, s, which, bands, nbands);
+  else launch_gemms<false>(a, t, maps, s, which, bands, nbands);
 }
 
 }  // namespace wfk

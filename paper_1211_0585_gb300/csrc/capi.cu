@@ -473,7 +473,7 @@ static wf_status check_options(const wf_options *o) {
       o->max_level_iters < 1 || o->graph_iters < 1 || o->graph_iters > 1024 || o->batch_slots < 1 ||
       o->batch_slots > kBatchMax || !(o->plateau_eps >= 0.0) ||
       !(o->final_dchi2 >= 0.0) || o->refine_iters < 0 || !(o->refine_tol >= 0.0) || o->synthesis_table < -1 ||
-      o->synthesis_table > 1 || (o->posterior_grad != 0 && o->posterior_grad != 1)) {
+      o->synthesis_table > 2 || (o->posterior_grad != 0 && o->posterior_grad != 1)) {
     set_error("wf_options: value out of range");
     return WF_EINVAL;
   }

@@ -193,14 +193,18 @@ wf_options fp64_plan_options(size_t budget) {
   return o;
 }
 
-// an FP64 plan: the shape's tables and state, plus the precomputed lambda table
-// when it is within the pool's limit
+// an FP64 plan: its Fourier arrays (two 32-byte double-float complexes per (m,
+// ring pair)), recurrence tables (40 bytes per (m, ring pair), 48 per a_lm), the
+// per-pixel buffers and ring FFT tables (about 176 bytes per pixel in all), the
+// posterior-gradient buffers, plus the precomputed lambda table when it is
+// within the pool's limit
 size_t fp64_bytes(size_t budget, int nside, int lmax) {
   const wf_options o = fp64_plan_options(budget);
   const size_t tab = lam_table_rows(lmax) * (size_t)((2 * nside + 31) / 32 * 32) * 16;
   const size_t npix = 12 * (size_t)nside * nside, nalm = (size_t)(lmax + 1) * (lmax + 2) / 2;
+  const size_t nmk = (size_t)(lmax + 1) * 2 * nside;
   const size_t posterior = 2 * npix * sizeof(double) + 2 * nalm * 16;  // rel_posterior_grad buffers
-  return engine_bytes(nside, lmax, 1) + posterior + (tab <= o.legendre_table_bytes ? tab : 0);
+  return nmk * (64 + 40) + nalm * 48 + npix * 176 + posterior + (tab <= o.legendre_table_bytes ? tab : 0);
 }
 
 size_t bytes_in_use(wf_server_s *S) {
@@ -264,7 +268,8 @@ ShapeRunner *runner_for(wf_server_s *S, int nside, int lmax) {
   if (wf_plan_create(nside, lmax, cl.data(), unit.data(), nullptr, nullptr, &p) != WF_OK) return nullptr;
   R->shape = static_cast<Plan *>(p);
   R->engine = std::make_unique<Engine>();
-  if (R->engine->create(R->shape, S->max_batch, R->shape->stream) != WF_OK) return nullptr;
+  // tables kept unsplit (synthesis_table 1, or 0 when free memory is short): the budget counts them so
+  if (R->engine->create(R->shape, S->max_batch, R->shape->stream, 1) != WF_OK) return nullptr;
   // iterations per engine step by shape, so that a step of any shape takes a few ms and a large shape's
   // step does not hold back the harvest of a small one (one iteration at Nside 1024 is ~30 ms)
   R->engine->graph_iters = nside <= 128 ? 32 : nside <= 256 ? 16 : nside <= 512 ? 4 : 1;

@@ -215,6 +215,9 @@ struct TcArgs {
   const int4 *chunk_info;    // [nchunks] (first lamA row of the chunk, rows in it, m, 0)
   const float *lamA;
   float *lamTs;              // scratch of the streamed synthesis table (nullptr: resident lamT)
+  // split tables: lamA and lamT hold th in their first rows and tl from row loA / loT
+  int pre;
+  int loA, loT;
 };
 
 // A band of m whose synthesis table is rebuilt and used in one step: chunks
@@ -224,7 +227,7 @@ struct SynBand {
 };
 
 void launch_lam_tc_tables(const double *x, const LegDfArgs &D, int lmax, int RP, int RPp, const int *offTc,
-                          float *lamA, float *lamT, cudaStream_t s);
+                          float *lamA, float *lamT, bool split, size_t loA, size_t loT, cudaStream_t s);
 struct TcMaps;
 // groups: slots per ring-stage CTA for each class (0 or nullptr: the default rule)
 void launch_batch_iteration(const BatchArgs &a, const TcArgs &t, const TcMaps &maps, const RingClass *cls, int ncls,

@@ -96,18 +96,21 @@ def test_batch_on_device_buffers():
 def test_streamed_synthesis_table(nside, lmax):
     """With the synthesis-ordered Legendre table rebuilt band by band of m from
     the analysis table (synthesis_table = 0, the form that lets Nside 2048 fit),
-    the batched solve is bitwise the one with the table resident: the GEMM sees
-    the same operand values in the same order."""
+    and with both tables held split into their tf32 parts (synthesis_table = 2,
+    no split in the GEMMs), the batched solve is bitwise the one with the table
+    resident and split in shared memory: the GEMMs see the same operand values
+    in the same order."""
     p, _ = problem("wmap", seed=11, nside=nside, lmax=lmax)
     D = rhs_set(p, 3)
     out = []
-    for mode in (1, 0):
+    for mode in (1, 0, 2):
         P = wf.Plan(nside, lmax, p.cl, p.noise_var, p.mask,
                     wf.options(precision=wf.WF_PREC_MIXED, tol=1e-6, synthesis_table=mode))
         alm, stats, status = P.solve_batch(D)
         assert status == wf.WF_OK
         out.append(alm)
     assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2])
 
 
 def test_fp64_refinement_of_mixed_solves():

@@ -122,7 +122,7 @@ def test_server_fp64_pool_evicts_idle_plans_for_other_shapes():
     """With a budget that holds one FP64 plan of these shapes, a request of a
     second shape evicts the idle plan of the first; both results are right."""
     reqs = [make_request(501, 16, 32), make_request(502, 32, 64), make_request(503, 16, 32)]
-    S = wf.Server(hbm_budget_bytes=7_600_000, max_batch=1)  # FP64 plans: about 1.6 MB and 6.9 MB
+    S = wf.Server(hbm_budget_bytes=4_800_000, max_batch=1)  # FP64 plans: about 0.9 MB and 4.1 MB
     for r in reqs:
         t = S.submit(r["nside"], r["lmax"], r["cl"], r["noise"], r["mask"], r["d"], 1e-8)
         S.drain(300000)
