@@ -24,9 +24,12 @@
 // parity (-1)^{l-m} of lambda_lm and F- the opposite.
 //
 // The T channel, the azimuthal transforms of all three maps and the
-// controller are the scalar plan's kernels (its precision); the spin-2
-// Legendre stage reads a precomputed FP64 table of (F+, F-) per (l, m, ring
-// pair) on the FP64 pipe.
+// controller are the scalar plan's kernels (its precision). The spin-2
+// Legendre stage reads a precomputed table of (F+, F-) per (l, m, ring pair):
+// in double-float with compensated dot products on the FP32 pipe for
+// WF_PREC_FP64 plans (GB300's FP64 pipe runs at 1/63 of it), in FP64 for
+// WF_PREC_FP64_NATIVE plans. Rows below the first l at which lambda_lm(x_k)
+// reaches 2^-100 hold zeros and are not read.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +38,7 @@
 #include <string>
 #include <vector>
 
+#include "df.cuh"
 #include "wf_internal.h"
 #include "wf_plan.h"
 
@@ -54,7 +58,7 @@ __device__ __forceinline__ size_t idx_lm(int lmax, int l, int m) { return (size_
 // (F+, F-) of every (l, m) at the north ring of pair k: one thread per (m, k), the FP64 recurrence
 // from the scalar plan's start values (first l with |lambda| >= 2^-100 and the two values there)
 __global__ void spin2_table_kernel(const double *xk, const double2 *rec, const int *ls, const double2 *sv, int lmax,
-                                   int RP, double2 *tab) {
+                                   int RP, double2 *tab, int df) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long long)(lmax + 1) * RP) return;
   const int m = (int)(id / RP), k = (int)(id % RP);
@@ -82,7 +86,12 @@ __global__ void spin2_table_kernel(const double *xk, const double2 *rec, const i
       fp = nl * ((2.0 * ((double)m * m - dl) / s2 - dl * (dl - 1.0)) * lam + 2.0 * x * c * lm1 / s2);
       fm = nl * (2.0 * m / s2) * (c * lm1 - (dl - 1.0) * x * lam);
     }
-    tab[(base + (l - m)) * RP + k] = make_double2(fp, fm);
+    if (df) {   // (F+ hi, F+ lo, F- hi, F- lo)
+      const dfl a = df_from(fp), b = df_from(fm);
+      reinterpret_cast<float4 *>(tab)[(base + (l - m)) * RP + k] = make_float4(a.h, a.l, b.h, b.l);
+    } else {
+      tab[(base + (l - m)) * RP + k] = make_double2(fp, fm);
+    }
     p2 = p1;
     p1 = lam;
   }
@@ -165,6 +174,128 @@ __global__ void __launch_bounds__(kPolThreads) spin2_synthesis_kernel(const Ctl 
       unr -= aur; uni -= aui;
       usr -= p * bur; usi -= p * bui;
     }
+    FSQ[(size_t)m * RP + k] = make_double4_32a(qnr, qni, qsr, qsi);
+    FSU[(size_t)m * RP + k] = make_double4_32a(unr, uni, usr, usi);
+  }
+}
+
+// ---- double-float spin-2 Legendre stage
+__device__ __forceinline__ float4 cdf(double re, double im) {   // complex double-float (re hi, re lo, im hi, im lo)
+  const dfl a = df_from(re), b = df_from(im);
+  return make_float4(a.h, a.l, b.h, b.l);
+}
+__device__ __forceinline__ dfl dneg(dfl a) { return dfl{-a.h, -a.l}; }
+
+// spin-2 analysis in double-float: one CTA per m, a warp per l, lanes over
+// ring pairs. Shared memory holds, per ring pair, Q_N + Q_S, Q_N - Q_S, U_N + U_S,
+// U_N - U_S (the two parities' combinations of the rings' coefficients).
+__global__ void __launch_bounds__(kPolThreads) spin2_analysis_df_kernel(const Ctl *gate, const float4 *tab,
+                                                                         const int *ls, const double4_32a *FTQ,
+                                                                         const double4_32a *FTU, int lmax, int RP,
+                                                                         double2 *aE, double2 *aB) {
+  if (gate && gate->done) return;
+  extern __shared__ float4 pol_dsm[];   // [RP][4]
+  const int m = blockIdx.x;
+  for (int k = threadIdx.x; k < RP; k += blockDim.x) {
+    const double4_32a Qv = FTQ[(size_t)m * RP + k], Uv = FTU[(size_t)m * RP + k];
+    pol_dsm[4 * k + 0] = cdf(Qv.x + Qv.z, Qv.y + Qv.w);
+    pol_dsm[4 * k + 1] = cdf(Qv.x - Qv.z, Qv.y - Qv.w);
+    pol_dsm[4 * k + 2] = cdf(Uv.x + Uv.z, Uv.y + Uv.w);
+    pol_dsm[4 * k + 3] = cdf(Uv.x - Uv.z, Uv.y - Uv.w);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const size_t base = idx_lm(lmax, m, m);
+  for (int l = m + warp; l <= lmax; l += nw) {
+    const int even = ((l - m) & 1) == 0;
+    // F+ sees Q_N + p Q_S, U_N + p U_S; F- sees Q_N - p Q_S, U_N - p U_S (p = (-1)^(l-m))
+    const int iqp = even ? 0 : 1, iqm = even ? 1 : 0, iup = even ? 2 : 3, ium = even ? 3 : 2;
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+    const float4 *row = tab + (base + (l - m)) * RP;
+    for (int k = lane; k < RP; k += 32) {
+      if (l < ls[(size_t)m * RP + k]) continue;   // F+- = 0 below the ring pair's first l
+      const float4 f = row[k];
+      const dfl fp = {f.x, f.y}, fm = {f.z, f.w};
+      const float4 qp = pol_dsm[4 * k + iqp], qm = pol_dsm[4 * k + iqm];
+      const float4 up = pol_dsm[4 * k + iup], um = pol_dsm[4 * k + ium];
+      // a^E = -(F+ Q+ + i F- U-),  a^B = -(F+ U+ - i F- Q-)
+      dot2_acc(S[0], C[0], fp, dneg(dfl{qp.x, qp.y}));
+      dot2_acc(S[0], C[0], fm, dfl{um.z, um.w});
+      dot2_acc(S[1], C[1], fp, dneg(dfl{qp.z, qp.w}));
+      dot2_acc(S[1], C[1], fm, dneg(dfl{um.x, um.y}));
+      dot2_acc(S[2], C[2], fp, dneg(dfl{up.x, up.y}));
+      dot2_acc(S[2], C[2], fm, dneg(dfl{qm.z, qm.w}));
+      dot2_acc(S[3], C[3], fp, dneg(dfl{up.z, up.w}));
+      dot2_acc(S[3], C[3], fm, dfl{qm.x, qm.y});
+    }
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = (double)S[j] + (double)C[j];
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    if (lane == 0) {
+      aE[base + (l - m)] = l >= 2 ? make_double2(v[0], v[1]) : make_double2(0.0, 0.0);
+      aB[base + (l - m)] = l >= 2 ? make_double2(v[2], v[3]) : make_double2(0.0, 0.0);
+    }
+  }
+}
+
+// spin-2 synthesis in double-float: one CTA per m, a thread per ring pair.
+// The eight products F+ E.re, F- B.im, F+ E.im, F- B.re, F+ B.re, F- E.im,
+// F+ B.im, F- E.re are summed separately over even (S0) and odd (S1) l - m;
+// the north ring takes even + odd, the south ring (parity (-1)^(l-m) for F+,
+// the opposite for F-) even - odd.
+__global__ void __launch_bounds__(kPolThreads) spin2_synthesis_df_kernel(const Ctl *gate, const float4 *tab,
+                                                                          const int *ls, const double2 *aE,
+                                                                          const double2 *aB, int lmax, int RP,
+                                                                          double4_32a *FSQ, double4_32a *FSU) {
+  if (gate && gate->done) return;
+  extern __shared__ float4 pol_dsa[];   // [Lm][2]: E, B as complex double-float
+  const int m = blockIdx.x;
+  const int Lm = lmax - m + 1;
+  const size_t base = idx_lm(lmax, m, m);
+  for (int i = threadIdx.x; i < Lm; i += blockDim.x) {
+    pol_dsa[2 * i] = cdf(aE[base + i].x, aE[base + i].y);
+    pol_dsa[2 * i + 1] = cdf(aB[base + i].x, aB[base + i].y);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < RP; k += blockDim.x) {
+    float S0[8], C0[8], S1[8], C1[8];   // compile-time indices: the sums stay in registers
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { S0[j] = 0.f; C0[j] = 0.f; S1[j] = 0.f; C1[j] = 0.f; }
+    auto accum = [&](int i, float(&Sa)[8], float(&Ca)[8]) {
+      const float4 f = tab[(base + i) * RP + k];
+      const dfl fp = {f.x, f.y}, fm = {f.z, f.w};
+      const float4 E = pol_dsa[2 * i], Bv = pol_dsa[2 * i + 1];
+      const dfl er = {E.x, E.y}, ei = {E.z, E.w}, br = {Bv.x, Bv.y}, bi = {Bv.z, Bv.w};
+      dot2_acc(Sa[0], Ca[0], fp, er);
+      dot2_acc(Sa[1], Ca[1], fm, bi);
+      dot2_acc(Sa[2], Ca[2], fp, ei);
+      dot2_acc(Sa[3], Ca[3], fm, br);
+      dot2_acc(Sa[4], Ca[4], fp, br);
+      dot2_acc(Sa[5], Ca[5], fm, ei);
+      dot2_acc(Sa[6], Ca[6], fp, bi);
+      dot2_acc(Sa[7], Ca[7], fm, er);
+    };
+    int i = max(m < 2 ? 2 - m : 0, ls[(size_t)m * RP + k] - m);
+    if (i < Lm && (i & 1)) accum(i++, S1, C1);
+    for (; i + 1 < Lm; i += 2) {
+      accum(i, S0, C0);
+      accum(i + 1, S1, C1);
+    }
+    if (i < Lm) accum(i, S0, C0);
+    double e[8], o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      e[j] = (double)S0[j] + (double)C0[j];
+      o[j] = (double)S1[j] + (double)C1[j];
+    }
+    // north: Q = -(F+ E + i F- B), U = -(F+ B - i F- E); south: F+ -> p F+, F- -> -p F-
+    const double qnr = -((e[0] + o[0]) - (e[1] + o[1])), qni = -((e[2] + o[2]) + (e[3] + o[3]));
+    const double qsr = -((e[0] - o[0]) + (e[1] - o[1])), qsi = -((e[2] - o[2]) - (e[3] - o[3]));
+    const double unr = -((e[4] + o[4]) + (e[5] + o[5])), uni = -((e[6] + o[6]) - (e[7] + o[7]));
+    const double usr = -((e[4] - o[4]) - (e[5] - o[5])), usi = -((e[6] - o[6]) + (e[7] - o[7]));
     FSQ[(size_t)m * RP + k] = make_double4_32a(qnr, qni, qsr, qsi);
     FSU[(size_t)m * RP + k] = make_double4_32a(unr, uni, usr, usi);
   }
@@ -274,7 +405,8 @@ struct Pol : wf_pol_s {
   double tau = 0.0, omega = 0.0;
   wf_options opt{};
   std::vector<double> h_tt;
-  double2 *d_tab = nullptr;                       // (F+, F-) [nalm][RP]
+  double2 *d_tab = nullptr;                       // (F+, F-) [nalm][RP]: double2, or float4 double-float when df
+  bool df = false;                                // double-float spin-2 stage (WF_PREC_FP64 plans)
   double *d_cls = nullptr;                        // [4][lmax+1] TT, EE, BB, TE
   double4 *d_w = nullptr;                         // [npix] (w_T, w_QQ, w_QU, w_UU)
   double *d_d = nullptr, *d_map = nullptr, *d_u = nullptr;   // [3][npix]
@@ -315,9 +447,15 @@ void Pol::synth(cudaStream_t s, const double2 *alm, double *map, const Ctl *gate
   la.alm_in = alm;
   la.gate = gate;
   P->launch_leg(la, s, LEG_SYNTH);                                    // T -> the plan's FS
-  raise_smem_cap(reinterpret_cast<const void *>(spin2_synthesis_kernel));
-  spin2_synthesis_kernel<<<lmax + 1, kPolThreads, sizeof(double2) * 2 * (lmax + 1), s>>>(
-      gate, d_tab, alm + nalm, alm + 2 * nalm, lmax, RP, d_FSQ, d_FSU);
+  if (df) {
+    raise_smem_cap(reinterpret_cast<const void *>(spin2_synthesis_df_kernel));
+    spin2_synthesis_df_kernel<<<lmax + 1, kPolThreads, sizeof(float4) * 2 * (lmax + 1), s>>>(
+        gate, reinterpret_cast<const float4 *>(d_tab), P->d_ls, alm + nalm, alm + 2 * nalm, lmax, RP, d_FSQ, d_FSU);
+  } else {
+    raise_smem_cap(reinterpret_cast<const void *>(spin2_synthesis_kernel));
+    spin2_synthesis_kernel<<<lmax + 1, kPolThreads, sizeof(double2) * 2 * (lmax + 1), s>>>(
+        gate, d_tab, alm + nalm, alm + 2 * nalm, lmax, RP, d_FSQ, d_FSU);
+  }
   const double4_32a *fs[3] = {P->d_FS, d_FSQ, d_FSU};
   for (int c = 0; c < 3; ++c) {
     RingArgs ra = P->ring_args();
@@ -344,9 +482,15 @@ void Pol::analysis(cudaStream_t s, const double *map, double2 *alm, const Ctl *g
   la.alm = alm;
   la.gate = gate;
   P->launch_leg(la, s, LEG_ANALYSIS);                                 // T
-  raise_smem_cap(reinterpret_cast<const void *>(spin2_analysis_kernel));
-  spin2_analysis_kernel<<<lmax + 1, kPolThreads, sizeof(double4_32a) * 2 * RP, s>>>(
-      gate, d_tab, d_FTQ, d_FTU, lmax, RP, alm + nalm, alm + 2 * nalm);
+  if (df) {
+    raise_smem_cap(reinterpret_cast<const void *>(spin2_analysis_df_kernel));
+    spin2_analysis_df_kernel<<<lmax + 1, kPolThreads, sizeof(float4) * 4 * RP, s>>>(
+        gate, reinterpret_cast<const float4 *>(d_tab), P->d_ls, d_FTQ, d_FTU, lmax, RP, alm + nalm, alm + 2 * nalm);
+  } else {
+    raise_smem_cap(reinterpret_cast<const void *>(spin2_analysis_kernel));
+    spin2_analysis_kernel<<<lmax + 1, kPolThreads, sizeof(double4_32a) * 2 * RP, s>>>(
+        gate, d_tab, d_FTQ, d_FTU, lmax, RP, alm + nalm, alm + 2 * nalm);
+  }
 }
 
 void Pol::enqueue_iteration(cudaStream_t s) {
@@ -450,6 +594,7 @@ wf_status wf_pol_create(int nside, int lmax, const double *cls, const double *no
   Q->tau = tau;
   Q->omega = Q->P->omega;
   Q->n_obs = n_obs;
+  Q->df = o.precision == WF_PREC_FP64;
   const size_t nF = (size_t)(lmax + 1) * Q->RP;
   if ((st = Q->dalloc((void **)&Q->d_tab, tab_bytes)) || (st = Q->dalloc((void **)&Q->d_cls, sizeof(double) * 4 * (lmax + 1))) ||
       (st = Q->dalloc((void **)&Q->d_w, sizeof(double4) * npix)) ||
@@ -477,7 +622,7 @@ wf_status wf_pol_create(int nside, int lmax, const double *cls, const double *no
   if (e == cudaSuccess) {
     const long long n = (long long)(lmax + 1) * Q->RP;
     spin2_table_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(Q->P->d_x, Q->P->d_rec, Q->P->d_ls, Q->P->d_sv,
-                                                                  lmax, Q->RP, Q->d_tab);
+                                                                  lmax, Q->RP, Q->d_tab, Q->df ? 1 : 0);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMallocHost((void **)&Q->h_ctl, sizeof(Ctl));
