@@ -204,39 +204,67 @@ __global__ void __launch_bounds__(kPolThreads) spin2_analysis_df_kernel(const Ct
     pol_dsm[4 * k + 3] = cdf(Uv.x - Uv.z, Uv.y - Uv.w);
   }
   __syncthreads();
+  // a warp takes l and l + 1 (l - m even, then odd): both read the same four combinations, the even
+  // l as (Q+, Q-, U+, U-) = (N + S, N - S), the odd one with the two swapped
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const size_t base = idx_lm(lmax, m, m);
-  for (int l = m + warp; l <= lmax; l += nw) {
-    const int even = ((l - m) & 1) == 0;
-    // F+ sees Q_N + p Q_S, U_N + p U_S; F- sees Q_N - p Q_S, U_N - p U_S (p = (-1)^(l-m))
-    const int iqp = even ? 0 : 1, iqm = even ? 1 : 0, iup = even ? 2 : 3, ium = even ? 3 : 2;
-    float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
-    const float4 *row = tab + (base + (l - m)) * RP;
-    for (int k = lane; k < RP; k += 32) {
-      if (l < ls[(size_t)m * RP + k]) continue;   // F+- = 0 below the ring pair's first l
-      const float4 f = row[k];
-      const dfl fp = {f.x, f.y}, fm = {f.z, f.w};
-      const float4 qp = pol_dsm[4 * k + iqp], qm = pol_dsm[4 * k + iqm];
-      const float4 up = pol_dsm[4 * k + iup], um = pol_dsm[4 * k + ium];
-      // a^E = -(F+ Q+ + i F- U-),  a^B = -(F+ U+ - i F- Q-)
-      dot2_acc(S[0], C[0], fp, dneg(dfl{qp.x, qp.y}));
-      dot2_acc(S[0], C[0], fm, dfl{um.z, um.w});
-      dot2_acc(S[1], C[1], fp, dneg(dfl{qp.z, qp.w}));
-      dot2_acc(S[1], C[1], fm, dneg(dfl{um.x, um.y}));
-      dot2_acc(S[2], C[2], fp, dneg(dfl{up.x, up.y}));
-      dot2_acc(S[2], C[2], fm, dneg(dfl{qm.z, qm.w}));
-      dot2_acc(S[3], C[3], fp, dneg(dfl{up.z, up.w}));
-      dot2_acc(S[3], C[3], fm, dfl{qm.x, qm.y});
-    }
-    double v[4];
+  for (int l = m + 2 * warp; l <= lmax; l += 2 * nw) {
+    const bool has1 = l + 1 <= lmax;
+    float S[8], C[8];   // [0..3]: l, [4..7]: l + 1
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = (double)S[j] + (double)C[j];
+    for (int j = 0; j < 8; ++j) { S[j] = 0.f; C[j] = 0.f; }
+    const float4 *row0 = tab + (base + (l - m)) * RP, *row1 = row0 + RP;
+    // two ring pairs per step, every global load of both issued before the products
+    auto term = [&](int lsk, float4 f0, float4 f1, int k) {
+      if (l + 1 < lsk) return;   // F+- = 0 below the ring pair's first l
+      const float4 A = pol_dsm[4 * k + 0], Bq = pol_dsm[4 * k + 1];
+      const float4 Cu = pol_dsm[4 * k + 2], Du = pol_dsm[4 * k + 3];
+      // a^E = -(F+ Q+ + i F- U-),  a^B = -(F+ U+ - i F- Q-)
+      if (l >= lsk) {   // l: Q+ = A, Q- = Bq, U+ = Cu, U- = Du
+        const dfl fp = {f0.x, f0.y}, fm = {f0.z, f0.w};
+        dot2_acc(S[0], C[0], fp, dneg(dfl{A.x, A.y}));
+        dot2_acc(S[0], C[0], fm, dfl{Du.z, Du.w});
+        dot2_acc(S[1], C[1], fp, dneg(dfl{A.z, A.w}));
+        dot2_acc(S[1], C[1], fm, dneg(dfl{Du.x, Du.y}));
+        dot2_acc(S[2], C[2], fp, dneg(dfl{Cu.x, Cu.y}));
+        dot2_acc(S[2], C[2], fm, dneg(dfl{Bq.z, Bq.w}));
+        dot2_acc(S[3], C[3], fp, dneg(dfl{Cu.z, Cu.w}));
+        dot2_acc(S[3], C[3], fm, dfl{Bq.x, Bq.y});
+      }
+      if (has1) {   // l + 1: Q+ = Bq, Q- = A, U+ = Du, U- = Cu
+        const dfl fp = {f1.x, f1.y}, fm = {f1.z, f1.w};
+        dot2_acc(S[4], C[4], fp, dneg(dfl{Bq.x, Bq.y}));
+        dot2_acc(S[4], C[4], fm, dfl{Cu.z, Cu.w});
+        dot2_acc(S[5], C[5], fp, dneg(dfl{Bq.z, Bq.w}));
+        dot2_acc(S[5], C[5], fm, dneg(dfl{Cu.x, Cu.y}));
+        dot2_acc(S[6], C[6], fp, dneg(dfl{Du.x, Du.y}));
+        dot2_acc(S[6], C[6], fm, dneg(dfl{A.z, A.w}));
+        dot2_acc(S[7], C[7], fp, dneg(dfl{Du.z, Du.w}));
+        dot2_acc(S[7], C[7], fm, dfl{A.x, A.y});
+      }
+    };
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = lane; k < RP; k += 64) {
+      const int ka = k, kb = k + 32;
+      const int la = ls[(size_t)m * RP + ka], lb = kb < RP ? ls[(size_t)m * RP + kb] : lmax + 2;
+      const float4 fa0 = l >= la ? row0[ka] : z4, fa1 = has1 && l + 1 >= la ? row1[ka] : z4;
+      const float4 fb0 = l >= lb ? row0[kb] : z4, fb1 = has1 && l + 1 >= lb ? row1[kb] : z4;
+      term(la, fa0, fa1, ka);
+      if (kb < RP) term(lb, fb0, fb1, kb);
+    }
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = (double)S[j] + (double)C[j];
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+      for (int j = 0; j < 8; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
     if (lane == 0) {
       aE[base + (l - m)] = l >= 2 ? make_double2(v[0], v[1]) : make_double2(0.0, 0.0);
       aB[base + (l - m)] = l >= 2 ? make_double2(v[2], v[3]) : make_double2(0.0, 0.0);
+      if (has1) {
+        aE[base + (l + 1 - m)] = l + 1 >= 2 ? make_double2(v[4], v[5]) : make_double2(0.0, 0.0);
+        aB[base + (l + 1 - m)] = l + 1 >= 2 ? make_double2(v[6], v[7]) : make_double2(0.0, 0.0);
+      }
     }
   }
 }
@@ -264,8 +292,7 @@ __global__ void __launch_bounds__(kPolThreads) spin2_synthesis_df_kernel(const C
     float S0[8], C0[8], S1[8], C1[8];   // compile-time indices: the sums stay in registers
 #pragma unroll
     for (int j = 0; j < 8; ++j) { S0[j] = 0.f; C0[j] = 0.f; S1[j] = 0.f; C1[j] = 0.f; }
-    auto accum = [&](int i, float(&Sa)[8], float(&Ca)[8]) {
-      const float4 f = tab[(base + i) * RP + k];
+    auto accum4 = [&](int i, float4 f, float(&Sa)[8], float(&Ca)[8]) {
       const dfl fp = {f.x, f.y}, fm = {f.z, f.w};
       const float4 E = pol_dsa[2 * i], Bv = pol_dsa[2 * i + 1];
       const dfl er = {E.x, E.y}, ei = {E.z, E.w}, br = {Bv.x, Bv.y}, bi = {Bv.z, Bv.w};
@@ -278,8 +305,17 @@ __global__ void __launch_bounds__(kPolThreads) spin2_synthesis_df_kernel(const C
       dot2_acc(Sa[6], Ca[6], fp, bi);
       dot2_acc(Sa[7], Ca[7], fm, er);
     };
+    auto accum = [&](int i, float(&Sa)[8], float(&Ca)[8]) { accum4(i, tab[(base + i) * RP + k], Sa, Ca); };
     int i = max(m < 2 ? 2 - m : 0, ls[(size_t)m * RP + k] - m);
     if (i < Lm && (i & 1)) accum(i++, S1, C1);
+    for (; i + 3 < Lm; i += 4) {   // four rows of the table in flight
+      const float4 f0 = tab[(base + i) * RP + k], f1 = tab[(base + i + 1) * RP + k];
+      const float4 f2 = tab[(base + i + 2) * RP + k], f3 = tab[(base + i + 3) * RP + k];
+      accum4(i, f0, S0, C0);
+      accum4(i + 1, f1, S1, C1);
+      accum4(i + 2, f2, S0, C0);
+      accum4(i + 3, f3, S1, C1);
+    }
     for (; i + 1 < Lm; i += 2) {
       accum(i, S0, C0);
       accum(i + 1, S1, C1);
