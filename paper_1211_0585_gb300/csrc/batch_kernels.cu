@@ -45,11 +45,12 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // The G / 2 packed arrays share every twiddle load, the pixel pass updates
 // them in place (the inverse transform's output order is the forward
 // transform's input order), and the G slots read their Fourier coefficients
-// as one contiguous run of G float4. Three CTAs of 256 threads per SM, so that
-// the FFT passes of one CTA overlap the global loads and stores of another.
+// as one contiguous run of G float4. Four CTAs of 256 threads per SM (64
+// registers), so that the FFT passes of one CTA overlap the global loads and
+// stores of the others.
 constexpr int kBringThreads = 256;
 template <int G>
-__global__ void __launch_bounds__(kBringThreads, 3) bring_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kBringThreads, 4) bring_kernel(const BatchArgs A) {
   static_assert(G % 2 == 0, "slots are packed in pairs");
   constexpr int P = G / 2;
   extern __shared__ float2 bsm[];
@@ -409,11 +410,11 @@ static size_t bring_smem(int logM, int G) {
 
 
 // default slots per ring-stage CTA of a class (before autotuning): 8, 4 or 2
-// (pairs share one FFT), within a third of an SM's shared memory so that three
+// (pairs share one FFT), within a quarter of an SM's shared memory so that four
 // CTAs share each SM
 static int batch_ring_group(int logM, int B) {
   int G = 8;
-  while (G > 2 && (bring_smem(logM, G) > 72 * 1024 || G >= 2 * B)) G >>= 1;
+  while (G > 2 && (bring_smem(logM, G) > 54 * 1024 || G >= 2 * B)) G >>= 1;
   return G;
 }
 
