@@ -361,6 +361,8 @@ def run_ours(args):
             result["constrained_realisations"] = constrained_realisations_run(prob, dmap)
         P.close()
         torch.cuda.empty_cache()
+        with progress("small"):
+            result["small"] = small_run()
         with progress("multi"):
             result["multi"] = multi_run(prob)
         with progress("polarisation"):
@@ -678,6 +680,34 @@ def polarisation_run(iters=10, seed=1):
                       "wf_pol_alm2map + wf_pol_map2alm pairs between device synchronizes"}
 
 
+def small_run(iters=200, seed=1, reps=3):
+    """The small configuration (Nside 16 / lmax 32, FP64, lambda = 1, no cooling): microseconds per
+    iteration over a fixed 200-iteration solve, data resident on the device (host clock around
+    wf_solve, the shortest of `reps` solves). At this size an iteration is a few launches of tiny
+    kernels, so the number measures launch and graph overhead, not bandwidth."""
+    import torch
+    from paper_1211_0585_gb300 import inputs as I
+    from paper_1211_0585_gb300 import wf
+    prob = I.small_problem(seed=seed)
+    d = torch.from_numpy(prob.data(np.zeros(prob.npix))).cuda()
+    P = wf.Plan(16, 32, prob.cl, prob.noise_var, prob.mask, wf.options(tol=0.0, max_iter=iters, cooling=0))
+    out = torch.empty(2 * P.nalm, dtype=torch.float64, device="cuda")
+    P.solve(d.data_ptr(), out.data_ptr(), on_device=True)   # graph capture
+    best = float("inf")
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st, _, _ = P.solve(d.data_ptr(), out.data_ptr(), on_device=True)
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    P.close()
+    return {"workload": "Nside 16 (3,072 px), lmax 32, FP64, 200 iterations at lambda = 1",
+            "us_per_iteration": round(1e6 * best / iters, 2), "iterations": st["iters"],
+            "chi2_per_dof": st["chi2_per_dof"],
+            "timing": f"host wall clock around wf_solve (device-resident data), shortest of {reps}; the "
+                      f"posterior gradient after the solve included"}
+
+
 def multi_run(prob, iters=10):
     """Several messenger fields at the bench size: two maps of the WMAP-shaped sky (13' and 30' beams, the
     second with twice the noise and its own mask), ms per full-band iteration of wf_multi_solve."""
@@ -859,7 +889,43 @@ def cpu_baseline(prob, d, P=None, budget_s=25.0, levels=None):
             "sample": f"one oracle iteration at each band limit {sorted(per)} "
                       f"(s per iteration {[round(per[k], 2) for k in sorted(per)]}), projected over the "
                       f"{n_it}-iteration schedule of the GPU solve",
-            "seconds_per_solve_projected": round(t_solve, 2)}
+            "seconds_per_solve_projected": round(t_solve, 2),
+            "one_core": oracle_one_core()}
+
+
+def oracle_one_core(timeout_s=120):
+    """The oracle on one host core (OMP_NUM_THREADS=1, a child process): seconds per iteration of the
+    Nside 512 problem at band limit 120 (the schedule's first level), of the Nside 16 / lmax 32 problem,
+    and the same two on all cores, for the speedup of the threaded oracle."""
+    import subprocess
+    code = ("import json, math, time, numpy as np, bench\n"
+            "from oracle import oracle as O\n"
+            "from paper_1211_0585_gb300 import inputs as I\n"
+            "O.build_oracle()\n"
+            "out = {}\n"
+            "for tag, prob, ns, lm, lsht in (('nside512_lsht120', bench.make_problem(1), 512, 1024, 120),\n"
+            "                                ('nside16_lmax32', I.small_problem(seed=1), 16, 32, 32)):\n"
+            "    d = prob.data(O.alm2map(ns, lm, prob.alm_true))\n"
+            "    tau = O.messenger_tau(prob.noise_var, prob.mask); w = O.inverse_noise(prob.noise_var, prob.mask)\n"
+            "    s = np.zeros(O.nalm_of(lm), dtype=np.complex128); reps = 1 if ns > 16 else 20\n"
+            "    t0 = time.perf_counter()\n"
+            "    for _ in range(reps):\n"
+            "        O.messenger_step(ns, lm, lsht, s, d, w, O.pixel_gain(1.0, tau, w),\n"
+            "                         O.harmonic_filter(1.0, tau, 4 * math.pi / prob.npix, prob.cl), prob.cl, 1.0, tau)\n"
+            "    out[tag] = (time.perf_counter() - t0) / reps\n"
+            "print(json.dumps(out))\n")
+    res = {}
+    for cores in (1, os.cpu_count()):
+        env = dict(os.environ, OMP_NUM_THREADS=str(cores))
+        try:
+            r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                               timeout=timeout_s, cwd=os.path.dirname(os.path.abspath(__file__)))
+            vals = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+        except (subprocess.TimeoutExpired, ValueError, IndexError):
+            vals = None
+        res[f"{cores}_cores"] = {k: round(v, 5) for k, v in vals.items()} if vals else None
+    res["unit"] = "s per oracle iteration (lambda = 1)"
+    return res
 
 
 def run_reference(args):
