@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-planck", action="store_true", help="skip the Planck-shaped (Nside 2048) measurement")
     ap.add_argument("--serving-only", action="store_true", help="run only the config-5 serving measurement")
     ap.add_argument("--planck-only", action="store_true", help="run only the Planck-shaped measurement")
+    ap.add_argument("--polarisation-only", action="store_true",
+                    help="run only the temperature-and-polarisation measurement (also a profiling target)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fp64-form", choices=["table", "recurrence", "native"], default="table",
                     help="form of the FP64 solve: double-float kernels reading the precomputed lambda table "
@@ -1014,10 +1016,11 @@ def main():
     if args.profile_fp64:
         profile_fp64(*args.profile_fp64, args.seed, args.fp64_form)
         return
-    if args.serving_only or args.planck_only:
+    if args.serving_only or args.planck_only or args.polarisation_only:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps(serving_run() if args.serving_only else planck_run()), flush=True)
+        run = serving_run if args.serving_only else planck_run if args.planck_only else polarisation_run
+        print(json.dumps(run()), flush=True)
         return
     if args.profile_batch:
         profile_batch(args.profile_batch[0], args.profile_batch[1], args.seed, args.profile_shape)
