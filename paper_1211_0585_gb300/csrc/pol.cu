@@ -337,22 +337,36 @@ __global__ void __launch_bounds__(kPolThreads) spin2_synthesis_df_kernel(const C
   }
 }
 
-// Eq. 3 per pixel with the 3 x 3 messenger and the chi^2 partials (sum r^T W r and r^T (N + (lambda-1) tau)^-1 r)
+// Eq. 3 per pixel with the 3 x 3 messenger and the chi^2 partials (sum r^T W r and r^T (N + (lambda-1) tau)^-1 r).
+// The gains (N + (lambda - 1) tau)^-1 depend on lambda only: each block keeps those of its pixels (the grid
+// is fixed, so a block always owns the same pixels) with the lambda they belong to, and recomputes them,
+// divisions on the FP64 pipe, only when lambda changes.
 __global__ void __launch_bounds__(kPolThreads) pol_pixel_kernel(const Ctl *ctl, long long npix, double tau,
                                                                  const double *s, const double *d, const double4 *w,
-                                                                 double *u, double *part) {
+                                                                 double4 *gain, double *gainlam, double *u,
+                                                                 double *part) {
   __shared__ double red[2][kPolThreads / 32];
   if (ctl->done) return;
   const double lam = ctl->lambda, c = (lam - 1.0) * tau, lt = lam * tau;
+  const bool fresh = gainlam[blockIdx.x] == lam;   // this block's gains are already at this lambda
   double c2n = 0.0, c2l = 0.0;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
     const double4 W = w[p];   // (w_T, w_QQ, w_QU, w_UU)
     const double rt = d[p] - s[p], rq = d[npix + p] - s[npix + p], ru = d[2 * npix + p] - s[2 * npix + p];
-    const double gt = W.x / (1.0 + c * W.x);
-    const double a11 = 1.0 + c * W.y, a12 = c * W.z, a22 = 1.0 + c * W.w;
-    const double det = a11 * a22 - a12 * a12;
-    const double i11 = a22 / det, i12 = -a12 / det, i22 = a11 / det;
-    const double g11 = W.y * i11 + W.z * i12, g12 = W.y * i12 + W.z * i22, g22 = W.z * i12 + W.w * i22;
+    double gt, g11, g12, g22;
+    if (fresh) {
+      const double4 G = gain[p];
+      gt = G.x; g11 = G.y; g12 = G.z; g22 = G.w;
+    } else {
+      gt = W.x / (1.0 + c * W.x);
+      const double a11 = 1.0 + c * W.y, a12 = c * W.z, a22 = 1.0 + c * W.w;
+      const double det = a11 * a22 - a12 * a12;
+      const double i11 = a22 / det, i12 = -a12 / det, i22 = a11 / det;
+      g11 = W.y * i11 + W.z * i12;
+      g12 = W.y * i12 + W.z * i22;
+      g22 = W.z * i12 + W.w * i22;
+      gain[p] = make_double4(gt, g11, g12, g22);
+    }
     u[p] = lt * gt * rt;
     u[npix + p] = lt * (g11 * rq + g12 * ru);
     u[2 * npix + p] = lt * (g12 * rq + g22 * ru);
@@ -370,6 +384,7 @@ __global__ void __launch_bounds__(kPolThreads) pol_pixel_kernel(const Ctl *ctl, 
     for (int i = 0; i < kPolThreads / 32; ++i) { a += red[0][i]; b += red[1][i]; }
     part[2 * blockIdx.x] = a;
     part[2 * blockIdx.x + 1] = b;
+    if (!fresh) gainlam[blockIdx.x] = lam;   // after the barrier: every gain of the block is written
   }
 }
 
@@ -445,6 +460,8 @@ struct Pol : wf_pol_s {
   bool df = false;                                // double-float spin-2 stage (WF_PREC_FP64 plans)
   double *d_cls = nullptr;                        // [4][lmax+1] TT, EE, BB, TE
   double4 *d_w = nullptr;                         // [npix] (w_T, w_QQ, w_QU, w_UU)
+  double4 *d_gain = nullptr;                      // [npix] cached 3 x 3 gains (g_T, g_QQ, g_QU, g_UU)
+  double *d_gainlam = nullptr;                    // [kPixBlocks] lambda of each block's cached gains
   double *d_d = nullptr, *d_map = nullptr, *d_u = nullptr;   // [3][npix]
   double2 *d_s = nullptr, *d_ta = nullptr;        // [3][nalm]
   double4_32a *d_FSQ = nullptr, *d_FSU = nullptr, *d_FTQ = nullptr, *d_FTU = nullptr;
@@ -531,7 +548,8 @@ void Pol::analysis(cudaStream_t s, const double *map, double2 *alm, const Ctl *g
 
 void Pol::enqueue_iteration(cudaStream_t s) {
   synth(s, d_s, d_map, d_ctl);
-  pol_pixel_kernel<<<kPixBlocks, kPolThreads, 0, s>>>(d_ctl, npix, tau, d_map, d_d, d_w, d_u, d_part);
+  pol_pixel_kernel<<<kPixBlocks, kPolThreads, 0, s>>>(d_ctl, npix, tau, d_map, d_d, d_w, d_gain, d_gainlam, d_u,
+                                                       d_part);
   analysis(s, d_u, d_ta, d_ctl);
   pol_eq4_kernel<<<lmax + 1, 128, 0, s>>>(d_ctl, lmax, nalm, tau, omega, d_cls, d_ta, d_s, d_m_part);
   launch_control(d_ctl, d_part, kPixBlocks, d_m_part, lmax, P->d_cl, d_hist, hist_cap, s);
@@ -634,6 +652,8 @@ wf_status wf_pol_create(int nside, int lmax, const double *cls, const double *no
   const size_t nF = (size_t)(lmax + 1) * Q->RP;
   if ((st = Q->dalloc((void **)&Q->d_tab, tab_bytes)) || (st = Q->dalloc((void **)&Q->d_cls, sizeof(double) * 4 * (lmax + 1))) ||
       (st = Q->dalloc((void **)&Q->d_w, sizeof(double4) * npix)) ||
+      (st = Q->dalloc((void **)&Q->d_gain, sizeof(double4) * npix)) ||
+      (st = Q->dalloc((void **)&Q->d_gainlam, sizeof(double) * kPixBlocks)) ||
       (st = Q->dalloc((void **)&Q->d_d, sizeof(double) * 3 * npix)) ||
       (st = Q->dalloc((void **)&Q->d_map, sizeof(double) * 3 * npix)) ||
       (st = Q->dalloc((void **)&Q->d_u, sizeof(double) * 3 * npix)) ||
@@ -652,6 +672,9 @@ wf_status wf_pol_create(int nside, int lmax, const double *cls, const double *no
   cudaStream_t s = Q->stream();
   cudaError_t e = cudaMemcpyAsync(Q->d_cls, cls, sizeof(double) * 4 * (lmax + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_w, w.data(), sizeof(double4) * npix, cudaMemcpyHostToDevice, s);
+  const std::vector<double> no_gains(kPixBlocks, -1.0);   // no gains cached yet: lambda >= 1 never equals -1
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Q->d_gainlam, no_gains.data(), sizeof(double) * kPixBlocks, cudaMemcpyHostToDevice, s);
   // the ring stage never writes the equator pair's south slot: it must read as zero
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->d_FTQ, 0, sizeof(double4_32a) * nF, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->d_FTU, 0, sizeof(double4_32a) * nF, s);
