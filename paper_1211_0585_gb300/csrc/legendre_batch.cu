@@ -18,6 +18,10 @@
 // partial sums, so a batched map's iterates equal its single solve's bit for
 // bit (the analysis takes its ring pairs in chunks of kBatchChunk, as the
 // single kernel does).
+// MODE LEG_SYNTH and LEG_ANALYSIS are the single kernel's transforms for NB
+// maps (several messenger fields: one synthesis and one analysis per map and
+// iteration, the maps' Eq. 4 joint): the synthesis reads each map's
+// coefficients from Bm.alm, the analysis writes each map's t_l there.
 #include <cuda_runtime.h>
 
 #include "df.cuh"
@@ -41,7 +45,7 @@ __device__ __forceinline__ void xor_sum_b(float &S, float &C, int off) {
   C = C + rC + e;
 }
 
-template <int NB, int kBThreads, int kBatchChunk, int kMinBlocks>
+template <int NB, int kBThreads, int kBatchChunk, int kMinBlocks, int MODE>
 __global__ void __launch_bounds__(kBThreads, kMinBlocks) legendre_batch_kernel(const LegArgs A, const LegDfArgs D,
                                                                                 const LegBatchMaps Bm) {
   constexpr int kBWarps = kBThreads / 32;
@@ -95,8 +99,17 @@ __global__ void __launch_bounds__(kBThreads, kMinBlocks) legendre_batch_kernel(c
   };
   if (m > Lmax) {
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
-      if (on[b]) outside(b);
+    for (int b = 0; b < NB; ++b) {
+      if (!on[b]) continue;
+      if (MODE == LEG_ITER) {
+        outside(b);
+      } else if (MODE == LEG_ANALYSIS) {
+        for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) Bm.alm[b][base + (l - m)] = make_double2(0.0, 0.0);
+      } else {
+        for (int k = threadIdx.x; k < RP; k += blockDim.x)
+          Bm.FS[b][(size_t)m * RP + k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      }
+    }
     return;
   }
   const int L = Lmax;
@@ -114,7 +127,7 @@ __global__ void __launch_bounds__(kBThreads, kMinBlocks) legendre_batch_kernel(c
   __syncthreads();
 
   // ---- analysis
-  {
+  if (MODE != LEG_SYNTH) {
     const int rho = lane >> 3, sig = lane & 7;
     for (int k0 = 0; k0 < RP; k0 += kBatchChunk) {
       const int nk = min(kBatchChunk, RP - k0);
@@ -202,10 +215,42 @@ __global__ void __launch_bounds__(kBThreads, kMinBlocks) legendre_batch_kernel(c
     }
   }
 
-  // ---- Eq. 4, the prior chi^2 / increment / norm partials and the synthesis coefficients, map by map
-  float4 *ss = reg;   // [NB][Lpm]
+  if (MODE == LEG_ANALYSIS) {   // t_l of every map, zero above its band limit
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
+    for (int b = 0; b < NB; ++b) {
+      if (!on[b]) continue;
+      const double2 *tb = tl + (size_t)b * Lpm;
+      for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x)
+        Bm.alm[b][base + (l - m)] = (l <= Lb[b]) ? tb[l - m] : make_double2(0.0, 0.0);
+    }
+    return;
+  }
+
+  // ---- Eq. 4, the prior chi^2 / increment / norm partials and the synthesis coefficients, map by map
+  // (synthesis alone: the coefficients are the maps' a_lm)
+  float4 *ss = reg;   // [NB][Lpm]
+  if (MODE == LEG_SYNTH) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      float4 *sb = ss + (size_t)b * Lpm;
+      const bool use = on[b] && m <= Lb[b];
+      for (int i = threadIdx.x; i < Lm + 2; i += blockDim.x) {
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (use && i < Lm && m + i <= Lb[b]) {
+          const double2 v = Bm.alm[b][base + i];
+          const dfl re = df_from(v.x), im = df_from(v.y);
+          c = make_float4(re.h, re.l, im.h, im.l);
+        }
+        sb[i] = c;
+      }
+      if (on[b] && m > Lb[b])
+        for (int k = threadIdx.x; k < RP; k += blockDim.x)
+          Bm.FS[b][(size_t)m * RP + k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < NB && MODE == LEG_ITER; ++b) {
     float4 *sb = ss + (size_t)b * Lpm;
     if (!on[b] || m > Lb[b]) {
       // the synthesis reads rows up to L: coefficients 0 .. Lm + 1 (Lm + 2 <= Lpm)
@@ -319,10 +364,18 @@ static size_t batch_smem(int nb, int chunk, int lmax, int RP) {
 
 size_t leg_batch_smem(int nb, int lmax, int RP) { return batch_smem(nb, 1024, lmax, RP); }
 
-void launch_legendre_batch(const LegArgs &a, const LegDfArgs &d, const LegBatchMaps &bm, int nb, cudaStream_t s) {
+template <int MODE>
+static void launch_lb(const LegArgs &a, const LegDfArgs &d, const LegBatchMaps &bm, cudaStream_t s) {
+  raise_smem_cap(reinterpret_cast<const void *>(legendre_batch_kernel<2, 256, 1024, 1, MODE>));
+  legendre_batch_kernel<2, 256, 1024, 1, MODE><<<a.lmax + 1, 256, batch_smem(2, 1024, a.lmax, a.RP), s>>>(a, d, bm);
+}
+
+void launch_legendre_batch(const LegArgs &a, const LegDfArgs &d, const LegBatchMaps &bm, int nb, cudaStream_t s,
+                           int mode) {
   (void)nb;   // groups of kLegBatchMax = 2 maps (four were measured no faster per map)
-  raise_smem_cap(reinterpret_cast<const void *>(legendre_batch_kernel<2, 256, 1024, 1>));
-  legendre_batch_kernel<2, 256, 1024, 1><<<a.lmax + 1, 256, batch_smem(2, 1024, a.lmax, a.RP), s>>>(a, d, bm);
+  if (mode == LEG_SYNTH) launch_lb<LEG_SYNTH>(a, d, bm, s);
+  else if (mode == LEG_ANALYSIS) launch_lb<LEG_ANALYSIS>(a, d, bm, s);
+  else launch_lb<LEG_ITER>(a, d, bm, s);
 }
 
 }  // namespace wfk

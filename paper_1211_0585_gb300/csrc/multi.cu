@@ -23,6 +23,8 @@
 // as CUDA graphs on the first plan's stream with the controller on the device.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cmath>
 #include <new>
 #include <vector>
@@ -146,6 +148,37 @@ __global__ void multi_eq4_kernel(const Ctl *ctl, int K, int lmax, long long nalm
 void Multi::enqueue_iteration(cudaStream_t s) {
   Plan *P0 = P[0];
   multi_beam_kernel<<<lmax + 1, 128, 0, s>>>(d_ctl, K, lmax, nalm, d_beam, d_s, d_balm);
+  if (P0->legdf_args().tab) {
+    // table form: the maps' syntheses, and then their analyses, two maps per launch (each table row
+    // read once for both; every map's transform bitwise the single kernel's)
+    for (int k0 = 0; k0 < K; k0 += kLegBatchMax) {
+      const int nb = std::min(kLegBatchMax, K - k0);
+      LegBatchMaps syn{}, ana{};
+      syn.n = ana.n = nb;
+      for (int b = 0; b < nb; ++b) {
+        const int k = k0 + b;
+        syn.FS[b] = P[k]->d_FS;
+        syn.alm[b] = d_balm + (size_t)k * nalm;
+        ana.FT[b] = P[k]->d_FT;
+        ana.alm[b] = d_ta + (size_t)k * nalm;
+        syn.ctl[b] = ana.ctl[b] = d_ctl;
+      }
+      LegArgs la = P0->leg_args();
+      la.lsht = lmax;
+      launch_legendre_batch(la, P0->legdf_args(), syn, nb, s, LEG_SYNTH);
+      for (int b = 0; b < nb; ++b) {
+        const int k = k0 + b;
+        RingArgs ra = P[k]->ring_args();   // map k's data, noise, gains and Fourier buffers
+        ra.ctl = d_ctl;
+        ra.ring_part = d_ring_part + (size_t)k * 2 * R;
+        P[k]->launch_rng(ra, s, RING_ITER);
+      }
+      launch_legendre_batch(la, P0->legdf_args(), ana, nb, s, LEG_ANALYSIS);
+    }
+    multi_eq4_kernel<<<lmax + 1, 128, 0, s>>>(d_ctl, K, lmax, nalm, omega, d_beam, d_tau, d_cl, d_ta, d_s, d_m_part);
+    launch_control(d_ctl, d_ring_part, K * R, d_m_part, lmax, d_lamcl, d_hist, hist_cap, s);
+    return;
+  }
   for (int k = 0; k < K; ++k) {
     LegArgs ls = P0->leg_args();          // the first plan's Legendre tables, map k's buffers
     ls.lsht = lmax;

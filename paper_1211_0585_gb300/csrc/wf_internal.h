@@ -154,7 +154,10 @@ struct LegBatchMaps {
   double tau[kLegBatchMax];
 };
 size_t leg_batch_smem(int nb, int lmax, int RP);
-void launch_legendre_batch(const LegArgs &a, const LegDfArgs &d, const LegBatchMaps &bm, int nb, cudaStream_t s);
+// mode: LEG_ITER (NB independent iterations), LEG_SYNTH or LEG_ANALYSIS (NB maps' transforms, a_lm in / t_l out
+// through Bm.alm); the table form only
+void launch_legendre_batch(const LegArgs &a, const LegDfArgs &d, const LegBatchMaps &bm, int nb, cudaStream_t s,
+                           int mode = LEG_ITER);
 
 // Double-float copies of the ring-stage tables (ring_df.cu): float4 =
 // (re hi, re lo, im hi, im lo).

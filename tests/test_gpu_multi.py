@@ -35,6 +35,32 @@ def test_two_detectors_match_oracle(nside, lmax, l_iter0, prec):
     M.close()
 
 
+def test_three_detectors_match_oracle():
+    """Three maps (on the table form the maps' transforms run two per launch, the
+    third alone): the joint result and the chi^2 records match the oracle's."""
+    nside, lmax = 8, 16
+    cl, beams, var, masks, ds, z, phi = two_detectors(nside, lmax, 17)
+    rng = np.random.default_rng(18)
+    ell = np.arange(lmax + 1)
+    beams = beams + [np.exp(-0.5 * ell * (ell + 1) * 0.05 ** 2)]
+    var = var + [3e-3 * (1 + rng.random(z.size))]
+    masks = masks + [(z < 0.6).astype(np.uint8)]
+    # the third map: the first one's sky (its data minus its noise) through the third beam, plus noise
+    a_sky = O.map2alm(nside, lmax, ds[0])   # a noisy stand-in for the sky: any a_lm makes valid data
+    ds = ds + [O.alm2map(nside, lmax, beams[2][O.l_of_index(lmax)] * a_sky) +
+               rng.standard_normal(z.size) * np.sqrt(var[2])]
+    opts = dict(tol=1e-8, max_iter=4000, l_iter0=4)
+    ores = MU.solve_multi(nside, lmax, cl, beams, var, masks, ds, O.Options(**opts, band_limit=False))
+    assert ores.converged
+    M = wf.Multi(nside, lmax, cl, var, masks, beams, wf.options(**opts))
+    alm, st, status, recs = M.solve(ds, history=opts["max_iter"] + 1)
+    assert status == wf.WF_OK and st["iters"] == ores.iters
+    assert O.rel_l2(alm, ores.alm, lmax) < TOL
+    for r, h in zip(recs, ores.history):
+        assert r["chi2"] == pytest.approx(h["chi2"], rel=TOL)
+    M.close()
+
+
 def test_one_detector_equals_single_plan():
     """One map with a unit beam is the single-field solve (full band)."""
     p, d = problem("wmap-cooled", seed=14, nside=16, lmax=32)
