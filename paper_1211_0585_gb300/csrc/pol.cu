@@ -342,8 +342,8 @@ __global__ void __launch_bounds__(kPolThreads) spin2_synthesis_df_kernel(const C
 // is fixed, so a block always owns the same pixels) with the lambda they belong to, and recomputes them,
 // divisions on the FP64 pipe, only when lambda changes.
 __global__ void __launch_bounds__(kPolThreads) pol_pixel_kernel(const Ctl *ctl, long long npix, double tau,
-                                                                 const double *s, const double *d, const double4 *w,
-                                                                 double4 *gain, double *gainlam, double *u,
+                                                                 const double *s, const double *d, const double4_32a *w,
+                                                                 double4_32a *gain, double *gainlam, double *u,
                                                                  double *part) {
   __shared__ double red[2][kPolThreads / 32];
   if (ctl->done) return;
@@ -351,11 +351,11 @@ __global__ void __launch_bounds__(kPolThreads) pol_pixel_kernel(const Ctl *ctl, 
   const bool fresh = gainlam[blockIdx.x] == lam;   // this block's gains are already at this lambda
   double c2n = 0.0, c2l = 0.0;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
-    const double4 W = w[p];   // (w_T, w_QQ, w_QU, w_UU)
+    const double4_32a W = w[p];   // (w_T, w_QQ, w_QU, w_UU)
     const double rt = d[p] - s[p], rq = d[npix + p] - s[npix + p], ru = d[2 * npix + p] - s[2 * npix + p];
     double gt, g11, g12, g22;
     if (fresh) {
-      const double4 G = gain[p];
+      const double4_32a G = gain[p];
       gt = G.x; g11 = G.y; g12 = G.z; g22 = G.w;
     } else {
       gt = W.x / (1.0 + c * W.x);
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kPolThreads) pol_pixel_kernel(const Ctl *ctl, 
       g11 = W.y * i11 + W.z * i12;
       g12 = W.y * i12 + W.z * i22;
       g22 = W.z * i12 + W.w * i22;
-      gain[p] = make_double4(gt, g11, g12, g22);
+      gain[p] = make_double4_32a(gt, g11, g12, g22);
     }
     u[p] = lt * gt * rt;
     u[npix + p] = lt * (g11 * rq + g12 * ru);
@@ -459,8 +459,8 @@ struct Pol : wf_pol_s {
   double2 *d_tab = nullptr;                       // (F+, F-) [nalm][RP]: double2, or float4 double-float when df
   bool df = false;                                // double-float spin-2 stage (WF_PREC_FP64 plans)
   double *d_cls = nullptr;                        // [4][lmax+1] TT, EE, BB, TE
-  double4 *d_w = nullptr;                         // [npix] (w_T, w_QQ, w_QU, w_UU)
-  double4 *d_gain = nullptr;                      // [npix] cached 3 x 3 gains (g_T, g_QQ, g_QU, g_UU)
+  double4_32a *d_w = nullptr;                         // [npix] (w_T, w_QQ, w_QU, w_UU)
+  double4_32a *d_gain = nullptr;                      // [npix] cached 3 x 3 gains (g_T, g_QQ, g_QU, g_UU)
   double *d_gainlam = nullptr;                    // [kPixBlocks] lambda of each block's cached gains
   double *d_d = nullptr, *d_map = nullptr, *d_u = nullptr;   // [3][npix]
   double2 *d_s = nullptr, *d_ta = nullptr;        // [3][nalm]
@@ -605,12 +605,12 @@ wf_status wf_pol_create(int nside, int lmax, const double *cls, const double *no
     }
   }
   // inverse noise per pixel and the messenger covariance
-  std::vector<double4> w(npix);
+  std::vector<double4_32a> w(npix);
   double tau = INFINITY;
   long long n_obs = 0;
   for (long long p = 0; p < npix; ++p) {
     const double nt = noise[4 * p], nqq = noise[4 * p + 1], nqu = noise[4 * p + 2], nuu = noise[4 * p + 3];
-    double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
+    double4_32a v = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     if (!mask_t || mask_t[p]) {
       if (!std::isfinite(nt) || !(nt > 0.0)) { set_error("wf_pol_create: T noise must be > 0 where observed"); return WF_EINVAL; }
       v.x = 1.0 / nt;
@@ -651,8 +651,8 @@ wf_status wf_pol_create(int nside, int lmax, const double *cls, const double *no
   Q->df = o.precision == WF_PREC_FP64;
   const size_t nF = (size_t)(lmax + 1) * Q->RP;
   if ((st = Q->dalloc((void **)&Q->d_tab, tab_bytes)) || (st = Q->dalloc((void **)&Q->d_cls, sizeof(double) * 4 * (lmax + 1))) ||
-      (st = Q->dalloc((void **)&Q->d_w, sizeof(double4) * npix)) ||
-      (st = Q->dalloc((void **)&Q->d_gain, sizeof(double4) * npix)) ||
+      (st = Q->dalloc((void **)&Q->d_w, sizeof(double4_32a) * npix)) ||
+      (st = Q->dalloc((void **)&Q->d_gain, sizeof(double4_32a) * npix)) ||
       (st = Q->dalloc((void **)&Q->d_gainlam, sizeof(double) * kPixBlocks)) ||
       (st = Q->dalloc((void **)&Q->d_d, sizeof(double) * 3 * npix)) ||
       (st = Q->dalloc((void **)&Q->d_map, sizeof(double) * 3 * npix)) ||
@@ -671,7 +671,7 @@ wf_status wf_pol_create(int nside, int lmax, const double *cls, const double *no
   Q->hist_cap = o.max_iter + 1;
   cudaStream_t s = Q->stream();
   cudaError_t e = cudaMemcpyAsync(Q->d_cls, cls, sizeof(double) * 4 * (lmax + 1), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_w, w.data(), sizeof(double4) * npix, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Q->d_w, w.data(), sizeof(double4_32a) * npix, cudaMemcpyHostToDevice, s);
   const std::vector<double> no_gains(kPixBlocks, -1.0);   // no gains cached yet: lambda >= 1 never equals -1
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(Q->d_gainlam, no_gains.data(), sizeof(double) * kPixBlocks, cudaMemcpyHostToDevice, s);
