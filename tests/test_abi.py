@@ -79,7 +79,12 @@ def test_bad_sizes_rejected(lib, nside, lmax):
     assert wf.last_error()
 
 
-@pytest.mark.parametrize("bad", ["nan_var", "neg_var", "all_masked", "neg_cl", "bad_opt"])
+BAD_OPTIONS = {"bad_opt": dict(max_iter=0), "synthesis_table_high": dict(synthesis_table=3),
+               "synthesis_table_low": dict(synthesis_table=-2), "slots_high": dict(batch_slots=65),
+               "slots_low": dict(batch_slots=0), "graph_iters": dict(graph_iters=0), "precision": dict(precision=3)}
+
+
+@pytest.mark.parametrize("bad", ["nan_var", "neg_var", "all_masked", "neg_cl"] + list(BAD_OPTIONS))
 def test_bad_values_rejected(lib, bad):
     nside, lmax = 4, 8
     npix = 12 * nside * nside
@@ -94,7 +99,7 @@ def test_bad_values_rejected(lib, bad):
     elif bad == "neg_cl":
         cl[3] = -1.0
     else:
-        opt = wf.options(max_iter=0)
+        opt = wf.options(**BAD_OPTIONS[bad])
     h = ctypes.c_void_p()
     st = lib.wf_plan_create(nside, lmax, cl.ctypes.data_as(ctypes.c_void_p), nv.ctypes.data_as(ctypes.c_void_p),
                             mask.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt) if opt else None,
