@@ -31,10 +31,13 @@
 // synthesis chunk by every tile of ring pairs of its m).
 //
 // Each GEMM CTA is warp-specialised: warp 0 issues the table's TMA loads into a
-// 4-stage ring, warp 2 the data operand's into a 2-stage ring (its chunks come
-// mostly from L2), warp 1 owns the tensor memory and issues the MMAs, warps 3-6
-// split the table tiles (when the table is not split already) and, in the
-// synthesis GEMM, run the epilogue.
+// ring of three stages (two with split tables), warp 2 the data operand's into
+// a ring of three stages and brings the chunks kDAhead ahead into L2 (they come
+// mostly from L2: every tile of an (m, p) or m reads them), warp 1 owns the
+// tensor memory and issues the MMAs, warps 3-6 split the table tiles (when the
+// table is not split already) and, in the synthesis GEMM, run the epilogue; in
+// the analysis GEMM warps 8-15 fold the chunk sums and all sixteen warps run
+// the Eq. 4 epilogue.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
